@@ -1,0 +1,269 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows. None of them compares the oracle
+with itself: they use values printed in the paper, closed forms, exact
+rational geometry and brute force.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import (Oracle, cbt_one_to_bit, cbt_sum_reduction, cbt_zero_to_bit, decode_weights,
+                    halfedges_from_faces, lod_test, splitmix64)
+from workloads.cameras import (MODE_FORCE_MERGE, MODE_FORCE_SPLIT, MODE_LIST, MODE_RANDOM,
+                               forced_params)
+from tests.invariants import check_state, depth_of, symbolic_vertices
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- Fig. 1
+
+def test_fig1_halfedge_table():
+    """Sec. 2.1, Fig. 1: ingest of the three faces gives the printed table."""
+    g = gold("fig1_halfedges.json")
+    he = halfedges_from_faces(W.meshes.fig1_mesh())
+    for k in ("twin", "next", "prev", "vert", "face"):
+        assert he[k].tolist() == g[k], k
+
+
+def test_root_bisector_example():
+    """Sec. 2.2: b7's neighbours are b8 / b11 / b1 and its v2 is the average
+    of Vert(h7..h11); v0 = Vert(h7), v1 = Vert(Next(h7))."""
+    g = gold("worked_examples.json")
+    m = W.meshes.fig1_mesh()
+    o = Oracle(m, D=6, max_depth=4)
+    slots, heap, links = o.leaves()
+    assert slots.tolist() == list(range(12))
+    assert links[7].tolist() == [g["root_neighbours_b7"]["twin"], g["root_neighbours_b7"]["next"],
+                                 g["root_neighbours_b7"]["prev"]]
+    rt = o.root_table()
+    verts = [int(v) for v in np.asarray(o.halfedges["vert"])[g["pentagon_halfedges"]]]
+    s = [0.0, 0.0, 0.0]
+    for v in verts:  # Alg. 1 order: Vert(h7), Vert(h8), ..., Vert(h11)
+        s = [s[c] + m.pos[v][c] for c in range(3)]
+    assert rt[7, 2].tolist() == [x / 5 for x in s]
+    assert rt[7, 0].tolist() == m.pos[1].tolist() and rt[7, 1].tolist() == m.pos[2].tolist()
+
+
+# ---------------------------------------------------------------- CBT
+
+def _cbt_from_bits(D, bits):
+    cbt = np.zeros(2 << D, np.uint32)
+    cbt[1 << D:] = bits
+    return cbt_sum_reduction(D, cbt)
+
+
+def test_cbt_figure_sums_and_search():
+    """Sec. 3.1 CBT figure (D = 4): the printed sum-reduction tree, and Alg. 7
+    returning 0, 3, 10 for the first three set bits (Sec. 3.2)."""
+    g = gold("cbt_figure.json")
+    D = g["D"]
+    cbt = _cbt_from_bits(D, g["bitfield"])
+    k = 1
+    for level in g["levels_root_first"]:
+        assert cbt[k:k + len(level)].tolist() == level
+        k += len(level)
+    ones = [cbt_one_to_bit(D, cbt, i) for i in range(int(cbt[1]))]
+    assert ones[:3] == g["one_to_bit_first_three"]
+    assert ones == [i for i, b in enumerate(g["bitfield"]) if b]
+    zeros = [cbt_zero_to_bit(D, cbt, i) for i in range((1 << D) - int(cbt[1]))]
+    assert zeros == [i for i, b in enumerate(g["bitfield"]) if not b]
+
+
+@pytest.mark.parametrize("D", [1, 2, 5, 9, 12])
+def test_cbt_search_brute_force(D):
+    """Alg. 7/8 against a plain scan of random bitfields."""
+    rng = np.random.default_rng(D)
+    for p in (0.05, 0.5, 0.95):
+        bits = (rng.random(1 << D) < p).astype(np.uint32)
+        cbt = _cbt_from_bits(D, bits)
+        ones = np.nonzero(bits)[0]
+        zeros = np.nonzero(bits == 0)[0]
+        assert int(cbt[1]) == ones.size
+        for i in rng.choice(max(1, ones.size), size=min(50, ones.size), replace=False) if ones.size else []:
+            assert cbt_one_to_bit(D, cbt, int(i)) == ones[i]
+        for i in rng.choice(max(1, zeros.size), size=min(50, zeros.size), replace=False) if zeros.size else []:
+            assert cbt_zero_to_bit(D, cbt, int(i)) == zeros[i]
+
+
+def test_memory_formula_d17():
+    """Sec. 4 'Memory Consumption' with Table 2: D = 17, a pool of 2^D x 9
+    ints, a CBT of 2^(D+1) ints and a pointer buffer of 2^D x 2 ints come to
+    6.5 MiB; the paper rounds the total (with the input buffers) to 7 MiB."""
+    D = 17
+    total = (1 << D) * 9 * 4 + (1 << (D + 1)) * 4 + (1 << D) * 2 * 4 + 4
+    assert total == 6815748
+    assert round(total / 2**20) == 7
+
+
+# --------------------------------------------------------- Eq. 1, Alg. 2
+
+def test_decode_matches_per_level_bisection():
+    """Alg. 2's matrix product (bits read from the low end) against the
+    top-down per-level rule of Eq. 1, in exact rationals."""
+    he = halfedges_from_faces(W.meshes.fig1_mesh())
+    ch = 4
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        h = int(rng.integers(12))
+        d = int(rng.integers(0, 20))
+        path = int(rng.integers(0, 1 << d)) if d else 0
+        j = ((16 + h) << d) + path
+        Wm = decode_weights(j, ch)
+        assert (Wm.sum(axis=1) == 1 << d).all()  # barycentric rows
+        sym = symbolic_vertices(j, ch, he)
+        names = [("v", int(he["vert"][h])), ("v", int(he["vert"][he["next"][h]])), ("c", int(he["face"][h]))]
+        for r in range(3):
+            want = {}
+            for k in range(3):
+                if Wm[r, k]:
+                    want[names[k]] = want.get(names[k], 0) + Fraction(int(Wm[r, k]), 1 << d)
+            assert tuple(sorted(want.items())) == sym[r]
+
+
+def test_decode_eq1_first_level():
+    """Eq. 1 printed: 2 M0 and 2 M1 for the two children of a root."""
+    assert decode_weights(2 * 16, 4).tolist() == [[2, 0, 0], [0, 0, 2], [1, 1, 0]]
+    assert decode_weights(2 * 16 + 1, 4).tolist() == [[0, 0, 2], [0, 2, 0], [1, 1, 0]]
+
+
+def test_decode_deep_exact():
+    """Depth 60 with a known path: all-zero path keeps v0 as vertex 0 and
+    alternating halvings give exact dyadic weights."""
+    ch = 2
+    j = 4 << 60
+    Wm = decode_weights(j, ch)
+    assert int(Wm[0, 0]) == 1 << 60 and int(Wm[0, 1]) == 0 and int(Wm[0, 2]) == 0
+    assert (Wm.astype(object).sum(axis=1) == 1 << 60).all()
+
+
+# ------------------------------------------------------- hash and LOD
+
+def test_splitmix64_published_vector():
+    """SplitMix64 (Steele, Lea & Flood 2014) from state 0: its first three
+    outputs are the published values."""
+    g = 0x9E3779B97F4A7C15
+    outs = [splitmix64((k * g) & 0xFFFFFFFFFFFFFFFF) for k in range(3)]
+    assert outs == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_lod_special_cases():
+    """The LOD reading (split when the projected refinement edge exceeds the
+    threshold, cull when all vertices are behind one plane)."""
+    planes = np.array([[0, 0, 1]], np.float32)  # keep z >= 0
+    tri = np.array([[-1, 0, 10], [1, 0, 10], [0, 1, 10]], np.float32)
+    # |e| = 2 at distance 10: big iff 4 q > 100
+    assert lod_test(tri, planes, 1, 26.0) == 3
+    assert lod_test(tri, planes, 1, 24.0) == 1
+    behind = tri * np.array([1, 1, -1], np.float32)
+    assert lod_test(behind, planes, 1, 26.0) & 1 == 0
+    straddle = tri.copy()
+    straddle[2, 2] = -5.0
+    assert lod_test(straddle, planes, 1, 26.0) & 1 == 1
+    assert lod_test(behind, planes, 0, 26.0) & 1 == 1  # no planes: visible
+
+
+# -------------------------------------------------- worked examples
+
+def _heap(jp, d, ch):
+    return jp + (1 << (ch + d))
+
+
+def _leafset(o):
+    _, heap, _ = o.leaves()
+    return sorted(int(j) for j in heap)
+
+
+def _list_frame(split=(), merge=()):
+    return forced_params(MODE_LIST, split_list=np.array(split, np.uint64),
+                         merge_list=np.array(merge, np.uint64))
+
+
+def test_compatibility_chain_and_decimation_examples():
+    """Fig. 3 / Sec. 2.3 / Sec. 3.3: with b7 split (paired with b1), refining
+    b14 splits b11 into b22, b46, b47; merging the quad b28, b29, b46, b47
+    gives back b14, b23; then b22, b23 merge into b11 and the quad b14, b15,
+    b2, b3 into b7, b1."""
+    g = gold("worked_examples.json")
+    m = W.meshes.fig1_mesh()
+    o = Oracle(m, D=8, max_depth=6)
+    ch = o.ch
+    he = o.halfedges
+
+    def want(key):
+        return sorted(_heap(jp, d, ch) for jp, d in g[key])
+
+    o.update(_list_frame(split=[_heap(7, 0, ch)]))
+    assert _leafset(o) == want("after_split_b7")
+    b14 = _heap(14, 1, ch)
+    assert [2 * b14, 2 * b14 + 1] == [_heap(jp, d, ch) for jp, d in g["children_of_b14"]]
+    slot = {int(j): int(s) for s, j in zip(*o.leaves()[:2])}
+    assert o.chain_cost(slot[b14]) == 2 + 3  # b14 itself, b11 one level up, border end
+    st = o.update(_list_frame(split=[b14]))
+    assert st["split_bisectors"] == 2 and st["allocated"] == 5
+    assert _leafset(o) == want("after_split_b14")
+    for key in ("after_first_merge", "after_second_merge"):
+        st = o.update(forced_params(MODE_FORCE_MERGE))
+        assert st["ab_mismatch"] == 0
+        assert _leafset(o) == want(key)
+        slots, heap, links = o.leaves()
+        check_state(slots, heap, links, he, ch, 6, cbt=o.export()["cbt"])
+
+
+def test_uniform_refinement_closed_form():
+    """Uniform refinement to depth d gives H 2^d leaves, every heap ID
+    (2^ceil(log2 H) + h) 2^d + p, p < 2^d; forced merging returns the roots."""
+    m = W.meshes.cube_mesh()
+    o = Oracle(m, D=16, max_depth=14)
+    for d in range(1, 11):
+        st = o.update(forced_params(MODE_FORCE_SPLIT))
+        assert st["ab_mismatch"] == 0
+        leaves = _leafset(o)
+        assert len(leaves) == 24 * 2**d
+        assert leaves == sorted(((32 + h) << d) + p for h in range(24) for p in range(1 << d))
+    for d in range(9, -1, -1):
+        o.update(forced_params(MODE_FORCE_MERGE))
+        assert o.live_count == 24 * 2**d
+    assert _leafset(o) == [32 + h for h in range(24)]
+
+
+def test_max_allocation_bound():
+    """Sec. 3.3 kernel 4: a split never needs more than 3d + 4 allocations;
+    brute force over every live bisector of random states."""
+    for mesh in (W.meshes.fig1_mesh(), W.meshes.tetra_mesh(), W.meshes.grid_mesh(2, 2, 0.5, seed=7)):
+        o = Oracle(mesh, D=10, max_depth=8)
+        worst = 0
+        for f in range(60):
+            o.update(forced_params(MODE_RANDOM, seed=11))
+            slots, heap, _ = o.leaves()
+            for s, j in zip(slots, heap):
+                c = o.chain_cost(int(s))
+                d = depth_of(int(j), o.ch)
+                assert c <= 3 * d + 4
+                worst = max(worst, c - (3 * d + 4))
+        assert worst == 0  # the bound is reached
+
+
+def test_textbook_order_independence():
+    """The union of compatibility chains does not depend on the order in which
+    the requests are applied: two request orders give the same state."""
+    for mesh in (W.meshes.fig1_mesh(), W.meshes.cube_mesh(), W.meshes.grid_mesh(2, 2, 0.5, seed=7)):
+        a = Oracle(mesh, D=10, max_depth=8)
+        b = Oracle(mesh, D=10, max_depth=8)
+        b.set_order_seed(12345)
+        for f in range(40):
+            sa = a.update(forced_params(MODE_RANDOM, seed=3))
+            sb = b.update(forced_params(MODE_RANDOM, seed=3))
+            assert sa == sb
+            for x, y in zip(a.leaves(), b.leaves()):
+                assert np.array_equal(x, y)

@@ -1,0 +1,156 @@
+"""Seeded camera paths and the per-frame LOD inputs derived from a camera.
+
+The paper leaves the level-of-detail criterion to the application (Sec. 3.3,
+kernel 4, GenerateCommands). The inputs both implementations receive per frame
+are derived here on the host in FP64 and rounded once to FP32:
+
+* ``eye`` (FP64) - the camera position;
+* ``planes`` - 5 inward plane normals through the eye (4 sides + near), FP32;
+* ``q`` - ``((height_px / (2 tan(fovy / 2))) / tau_px)^2`` in FP32.
+
+Nothing here is the method's arithmetic: it is the camera model feeding it.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Wish modes shared by both implementations (frame parameter ``mode``).
+MODE_LOD, MODE_FORCE_SPLIT, MODE_FORCE_MERGE, MODE_RANDOM, MODE_LIST = 0, 1, 2, 3, 4
+# Vertex-evaluation precision (frame parameter ``precision``).
+PREC_FP32, PREC_FIXED, PREC_FP64 = 0, 1, 2
+# Gate (frame parameter ``gate``).
+GATE_CHAIN, GATE_PAPER = 0, 1
+
+
+@dataclass
+class Camera:
+    eye: np.ndarray
+    target: np.ndarray
+    up: np.ndarray
+    fovy_rad: float = np.pi / 2
+    aspect: float = 1920 / 1080
+    width_px: int = 1920
+    height_px: int = 1080
+
+
+@dataclass
+class FrameParams:
+    """One frame's inputs, identical for the oracle and the CUDA library."""
+
+    eye: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    planes: np.ndarray = field(default_factory=lambda: np.zeros((5, 3), np.float32))
+    nplanes: int = 5
+    q: float = 1.0
+    mode: int = MODE_LOD
+    seed: int = 0
+    precision: int = PREC_FP32
+    fixed_shift: int = 20
+    gate: int = GATE_CHAIN
+    split_list: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint64))
+    merge_list: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint64))
+
+
+def camera_basis(cam: Camera):
+    f = np.asarray(cam.target, np.float64) - np.asarray(cam.eye, np.float64)
+    f = f / np.linalg.norm(f)
+    up = np.asarray(cam.up, np.float64)
+    if abs(np.dot(f, up / np.linalg.norm(up))) > 0.999:
+        up = np.array([0.0, 1.0, 0.0]) if abs(f[1]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    r = np.cross(f, up)
+    r = r / np.linalg.norm(r)
+    u = np.cross(r, f)
+    return f, r, u
+
+
+def frame_params(cam: Camera, tau_px: float, frustum: bool = True, **kw) -> FrameParams:
+    f, r, u = camera_basis(cam)
+    ty = np.tan(cam.fovy_rad / 2.0)
+    tx = cam.aspect * ty
+    planes = np.stack([tx * f + r, tx * f - r, ty * f + u, ty * f - u, f]).astype(np.float32)
+    K = cam.height_px / (2.0 * ty)
+    q = np.float32((K / tau_px) ** 2)
+    return FrameParams(eye=np.asarray(cam.eye, np.float64).copy(), planes=planes,
+                       nplanes=5 if frustum else 0, q=float(q), **kw)
+
+
+def forced_params(mode: int, seed: int = 0, **kw) -> FrameParams:
+    """Geometry-free frame (FORCE_SPLIT, FORCE_MERGE, RANDOM or LIST)."""
+    return FrameParams(mode=mode, seed=seed, nplanes=0, q=1.0, **kw)
+
+
+# ----------------------------------------------------------------- paths
+
+def orbit_path(n_frames: int, seed: int, r_min=1.5, r_max=3.0):
+    """Eyes at radius U[r_min, r_max] along uniform directions, looking at
+    the origin, up = +z (the basis falls back when nearly parallel)."""
+    rng = np.random.default_rng(seed)
+    cams = []
+    for _ in range(n_frames):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        rad = rng.uniform(r_min, r_max)
+        cams.append(Camera(eye=d * rad, target=np.zeros(3), up=np.array([0.0, 0.0, 1.0])))
+    return cams
+
+
+def _catmull_rom(P, t):
+    """Uniform Catmull-Rom through control points P (clamped ends), t in [0,1]."""
+    n = len(P)
+    s = t * (n - 1)
+    i = min(int(np.floor(s)), n - 2)
+    u = s - i
+    p0 = P[max(i - 1, 0)]
+    p1, p2 = P[i], P[i + 1]
+    p3 = P[min(i + 2, n - 1)]
+    return 0.5 * ((2 * p1) + (-p0 + p2) * u + (2 * p0 - 5 * p1 + 4 * p2 - p3) * u * u
+                  + (-p0 + 3 * p1 - 3 * p2 + p3) * u * u * u)
+
+
+def flythrough_path(n_frames: int, seed: int, alt_hi=0.5, alt_lo=0.01, pitch_deg=30.0):
+    """Eye on a seeded Catmull-Rom path through 8 points in [0.1, 0.9]^2;
+    altitude log-interpolated alt_hi -> alt_lo -> alt_hi; looking along the
+    path tangent pitched down by ``pitch_deg``; up = +z."""
+    rng = np.random.default_rng(seed)
+    P = rng.uniform(0.1, 0.9, size=(8, 2))
+    cams = []
+    for k in range(n_frames):
+        t = k / max(1, n_frames - 1)
+        xy = _catmull_rom(P, t)
+        xy2 = _catmull_rom(P, min(1.0, t + 1e-3)) if t < 1 else xy + (xy - _catmull_rom(P, t - 1e-3))
+        tang = xy2 - xy
+        nrm = np.linalg.norm(tang)
+        tang = tang / nrm if nrm > 0 else np.array([1.0, 0.0])
+        s = 2 * t if t <= 0.5 else 2 * (1 - t)
+        alt = np.exp(np.log(alt_hi) + (np.log(alt_lo) - np.log(alt_hi)) * s)
+        eye = np.array([xy[0], xy[1], alt])
+        pitch = np.deg2rad(pitch_deg)
+        fwd = np.array([tang[0] * np.cos(pitch), tang[1] * np.cos(pitch), -np.sin(pitch)])
+        cams.append(Camera(eye=eye, target=eye + fwd, up=np.array([0.0, 0.0, 1.0])))
+    return cams
+
+
+def descent_path(mesh, n_frames: int, seed: int, alt_hi=2e7, alt_lo=2.0):
+    """Planet descent: a seeded interior target on one coarse face; altitude
+    above that face's plane log-spaced alt_hi -> alt_lo; looking at
+    target + tangent * 10 * altitude; up = the face normal."""
+    rng = np.random.default_rng(seed)
+    f = int(rng.integers(mesh.F))
+    off = int(mesh.face_sizes[:f].sum())
+    idx = mesh.face_verts[off:off + int(mesh.face_sizes[f])]
+    P = mesh.pos[idx]
+    w = rng.dirichlet(np.ones(len(idx)))
+    target = (w[:, None] * P).sum(0)
+    nrm = np.cross(P[1] - P[0], P[2] - P[0])
+    nrm /= np.linalg.norm(nrm)
+    tang = P[1] - P[0]
+    tang -= nrm * np.dot(tang, nrm)
+    tang /= np.linalg.norm(tang)
+    cams = []
+    for k in range(n_frames):
+        t = k / max(1, n_frames - 1)
+        alt = np.exp(np.log(alt_hi) + (np.log(alt_lo) - np.log(alt_hi)) * t)
+        eye = target + nrm * alt
+        cams.append(Camera(eye=eye, target=target + tang * 10.0 * alt, up=nrm))
+    return cams
