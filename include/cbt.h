@@ -1,0 +1,213 @@
+/* cbt.h - C ABI of the GB300 (sm_103a) adaptive-bisection library.
+ *
+ * Implements the per-frame update of "Concurrent Binary Trees for
+ * Large-Scale Game Components" (Benyoub & Dupuy, 2024): every halfedge of a
+ * polygon mesh is a root bisector (Sec. 2.2); each frame the live bisectors
+ * are classified against a level-of-detail test, split conformingly along
+ * their compatibility chains (Alg. 3, Table 1), merged back (Alg. 4) or kept,
+ * and a concurrent binary tree (CBT, Sec. 3.1-3.2) serves as the memory pool
+ * of 2^D bisector slots.
+ *
+ * Conventions
+ *   - A bisector is identified by its 64-bit heap ID j: the root of halfedge
+ *     h is 2^ceil(log2 H) + h and the children of j are 2j and 2j+1
+ *     (Sec. 2.3 "Notation", Sec. 3.3 "Initialization").
+ *   - Its depth is bitlength(j) - 1 - ceil(log2 H); its vertices are decoded
+ *     from j by Alg. 2 / Eq. 1.
+ *   - Each live bisector holds three neighbour slots Twin, Next, Prev (the
+ *     bisectors across its edges (v0,v1), (v1,v2), (v2,v0)); a missing
+ *     neighbour is CBT_NULL.
+ *   - Slots are indices in [0, 2^D). Live bisectors are always reported in
+ *     ascending slot order, which is the order of Alg. 7 (OneToBitID).
+ *
+ * Memory and streams
+ *   - The caller owns all device memory: the workspace passed to cbt_create
+ *     (size from cbt_workspace_bytes) must stay allocated and unmoved until
+ *     cbt_destroy, and output buffers are caller-allocated device memory.
+ *   - Host arrays passed to cbt_create are read during the call only.
+ *   - A state is used by one host thread at a time. Calls on one state are
+ *     ordered by the stream given to them; the caller orders streams when
+ *     it uses more than one for the same state.
+ *   - Calls marked "asynchronous" only enqueue work; calls marked
+ *     "synchronous" wait for the stream.
+ *
+ * Errors: every entry point returns 0 (CBT_OK) or one of the codes below.
+ * Device-side checks (a non-conforming neighbourhood, a bounded wait that
+ * gave up) set a sticky error word read by cbt_stats().
+ */
+#ifndef CBT_H
+#define CBT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cbt_stream_t; /* a cudaStream_t; NULL = default stream */
+
+#define CBT_NULL 0xFFFFFFFFu
+
+enum {
+    CBT_OK = 0,
+    CBT_EINVAL = 1,     /* bad argument or malformed halfedge mesh */
+    CBT_ECAPACITY = 2,  /* 2^D < H, or D outside [1, 30] */
+    CBT_EDEPTH = 3,     /* ceil(log2 H) + 1 + max_depth > 63 */
+    CBT_ENOMEM = 4,     /* workspace or output buffer too small */
+    CBT_ECUDA = 5,      /* a CUDA launch or runtime call failed */
+    CBT_EDEVICE = 6,    /* the sticky device error word is set */
+    CBT_ETIMEOUT = 7    /* a bounded device wait gave up */
+};
+
+/* Sticky device error bits (cbt_frame_stats.error). */
+enum {
+    CBT_DERR_CHAIN = 1u,    /* compatibility chain not one level coarser */
+    CBT_DERR_LINK = 2u,     /* non-conforming neighbourhood while relinking */
+    CBT_DERR_TIMEOUT = 4u,  /* a look-back wait hit its iteration limit */
+    CBT_DERR_RANGE = 8u,    /* fixed-point root offset outside 62 bits */
+    CBT_DERR_OVERFLOW = 16u /* more allocations than free slots */
+};
+
+/* Wish modes: the LOD test of Sec. 3.3 kernel 4, or test modes. */
+enum { CBT_MODE_LOD = 0, CBT_MODE_FORCE_SPLIT = 1, CBT_MODE_FORCE_MERGE = 2, CBT_MODE_RANDOM = 3,
+       CBT_MODE_LIST = 4 };
+/* Vertex evaluation: FP32, fixed point with exact integer sums, FP64. */
+enum { CBT_PREC_FP32 = 0, CBT_PREC_FIXED = 1, CBT_PREC_FP64 = 2 };
+/* Allocation budget per request: exact chain cost, or the paper's 3d + 4. */
+enum { CBT_GATE_CHAIN = 0, CBT_GATE_PAPER = 1 };
+
+/* One frame's inputs (Sec. 3.3 kernel 4 leaves the LOD criterion to the
+ * application; this library's criterion is described at cbt_update).
+ * planes: inward normals of up to five planes through the eye, FP32.
+ * q: ((viewport height / (2 tan(fovy / 2))) / threshold_px)^2 in FP32.
+ * split_list / merge_list: sorted DEVICE arrays of heap IDs (LIST mode). */
+typedef struct {
+    double eye[3];
+    float planes[5][3];
+    float q;
+    uint32_t nplanes;
+    uint32_t mode;
+    uint32_t seed;
+    uint32_t precision;
+    int32_t fixed_shift;
+    uint32_t gate;
+    const uint64_t* split_list;
+    uint32_t n_split;
+    const uint64_t* merge_list;
+    uint32_t n_merge;
+} cbt_frame;
+
+/* Per-frame counters (read with cbt_stats). */
+typedef struct {
+    uint32_t live_before, live_after, free_before;
+    uint32_t split_wishes, merge_candidates;
+    uint32_t split_granted, merge_granted;
+    uint32_t split_bisectors, merged_bisectors, merge_groups;
+    uint32_t allocated;
+    uint32_t relinked;  /* links of unchanged bisectors rewritten */
+    uint32_t frame;     /* frames completed so far */
+    uint32_t error;     /* sticky CBT_DERR_* bits */
+} cbt_frame_stats;
+
+typedef struct cbt_state cbt_state;
+
+/* Faces -> halfedge arrays (Sec. 2.1, halfedge figure): the halfedges of face
+ * f are consecutive, in face order; Next/Prev go round the face; Twin is the
+ * halfedge running the other way along the same edge, -1 on a border.
+ * Host arrays: face_sizes[F], face_verts[sum of sizes]; outputs [H] each.
+ * Returns CBT_EINVAL for a face with fewer than 3 vertices, a size mismatch
+ * or an edge used twice in the same direction. Synchronous, host only. */
+int cbt_halfedges_from_faces(int32_t F, const int32_t* face_sizes, const int32_t* face_verts,
+                             int32_t H, int32_t* twin, int32_t* next, int32_t* prev,
+                             int32_t* vert, int32_t* face);
+
+/* Bytes of device workspace for a mesh of H halfedges and a pool of 2^D
+ * bisectors (Table 2 and Sec. 4 "Memory Consumption" list the paper's
+ * layout; this one keeps a 64-bit heap ID, three 32-bit links, a 32-bit
+ * command word and a 32-bit destination per slot, the CBT as a bitfield plus
+ * its sum tree, and per-frame scratch). Returns 0 for invalid sizes. */
+size_t cbt_workspace_bytes(int32_t H, int32_t D);
+
+/* Builds the H root bisectors in slots 0..H-1 (Sec. 3.3 "Initialization"):
+ * heap IDs 2^ceil(log2 H) + h, neighbours copied from the halfedge operators,
+ * first H bits of the CBT set, sum reduction done. Root vertices follow
+ * Alg. 1 (v0 = Vert(h), v1 = Vert(Next(h)), v2 = face average, summed in FP64
+ * from the face's smallest halfedge index), kept in FP64.
+ *   twin/next/prev/vert/face: host int32[H] (twin -1 on a border);
+ *   pos: host double[V][3];
+ *   D: pool of 2^D slots, ceil(log2 H) <= D <= 30;
+ *   max_depth: subdivision limit, ceil(log2 H) + 1 + max_depth <= 63;
+ *   workspace/bytes: caller-owned device memory, cbt_workspace_bytes() long,
+ *                    256-byte aligned;
+ *   out: receives the state handle (host memory owned by the library).
+ * Errors: CBT_EINVAL (malformed mesh), CBT_ECAPACITY, CBT_EDEPTH,
+ * CBT_ENOMEM (workspace too small), CBT_ECUDA. Asynchronous on the device
+ * side; the host arrays may be freed when it returns. */
+int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_t* prev,
+               const int32_t* vert, const int32_t* face, int32_t V, const double* pos,
+               int32_t D, int32_t max_depth, void* workspace, size_t bytes,
+               cbt_stream_t stream, cbt_state** out);
+
+/* One frame of the update (Sec. 3.3, the update pipeline; Alg. 9):
+ *   1. the live slots in ascending order (Alg. 7, CachePointers);
+ *   2. classification on the frame-start state (GenerateCommands): split
+ *      wish = visible and big and depth < max_depth; merge wish = no split
+ *      wish, depth >= 1 and the parent is not (visible and big). "Big" means
+ *      |v1 - v0|^2 q > |(v0 + v1) / 2|^2 with camera-relative FP32 vertices;
+ *      "visible" means no plane has all three vertices on its negative side;
+ *   3. the gate: a split costs its compatibility-chain allocation count (or
+ *      3d + 4 with CBT_GATE_PAPER), a mergeable group its parent count at
+ *      its smallest heap ID; merges then splits, each in ascending slot
+ *      order, are granted while the running cost stays within the free slots;
+ *   4. granted splits mark their chains, groups whose members all agree and
+ *      carry no split merge (Alg. 4);
+ *   5. new bisectors take the free slots of the frame-start CBT in that order
+ *      (Alg. 8, ReserveBlocks); records and links are written (Table 1,
+ *      Alg. 5/6; FillNewBlocks, UpdateNeighbors), the bitfield updated and
+ *      the sum tree rebuilt (UpdateBitfield, SumReduction).
+ * Deterministic: the result does not depend on thread scheduling.
+ * Errors: CBT_EINVAL (NULL arguments or bad precision/mode), CBT_ECUDA.
+ * Asynchronous. */
+int cbt_update(cbt_state* st, const cbt_frame* frame, cbt_stream_t stream);
+
+/* Number of live bisectors (CBT root). Synchronous. */
+int cbt_live_count(cbt_state* st, uint32_t* h_count, cbt_stream_t stream);
+
+/* Copies the live bisectors, ascending slot order, into caller device
+ * buffers: d_slots[N], d_heap[N], d_links[N][3] as (Twin, Next, Prev).
+ * Any output may be NULL. cap = capacity of the outputs in bisectors;
+ * *h_count receives N. CBT_ENOMEM when N > cap. Synchronous. */
+int cbt_leaves(cbt_state* st, uint32_t* d_slots, uint64_t* d_heap, uint32_t* d_links,
+               uint32_t cap, uint32_t* h_count, cbt_stream_t stream);
+
+/* Vertices of the live bisectors, ascending slot order, as FP32 [N][3][3]
+ * relative to h_origin (Alg. 2 / Eq. 1 with exact integer weights; FP32,
+ * fixed-point or FP64 evaluation as `precision`; FP64 is used on the device
+ * only to subtract h_origin from the root vertices). d_out: caller device
+ * memory of cap * 9 floats. *h_count receives N. CBT_ENOMEM when N > cap.
+ * Synchronous. */
+int cbt_vertices(cbt_state* st, float* d_out, const double h_origin[3], uint32_t precision,
+                 int32_t fixed_shift, uint32_t cap, uint32_t* h_count, cbt_stream_t stream);
+
+/* The CBT: d_bitfield[max(1, 2^D / 32)] u32 words (bit s%32 of word s/32 is
+ * slot s) and d_sums[2 * words] in heap order: d_sums[1] is the root (live
+ * count), d_sums[words + w] = popcount(word w), d_sums[k] = d_sums[2k] +
+ * d_sums[2k+1]. These equal the paper's CBT heap nodes 1 .. 2*words - 1
+ * (Sec. 3.1). Either may be NULL. Asynchronous. */
+int cbt_cbt(cbt_state* st, uint32_t* d_bitfield, uint32_t* d_sums, cbt_stream_t stream);
+
+/* Counters of the last frame and the sticky device error word. Returns
+ * CBT_EDEVICE when that word is non-zero. Synchronous. */
+int cbt_stats(cbt_state* st, cbt_frame_stats* out, cbt_stream_t stream);
+
+/* Releases the host handle; the workspace stays the caller's. */
+void cbt_destroy(cbt_state* st);
+
+/* Number of kernel launches the last cbt_update enqueued. */
+uint32_t cbt_last_launch_count(const cbt_state* st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,244 @@
+"""Python binding of libcbt.so (argument marshalling only).
+
+Every step of the update runs in the library's CUDA kernels; torch supplies
+device memory (the workspace and output buffers) and the stream. There is no
+CPU path: the CUDA library must be loadable, else importing raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from .build import LIB as _LIB_PATH
+
+_lib = None
+
+CBT_NULL = 0xFFFFFFFF
+ERRORS = {1: "EINVAL", 2: "ECAPACITY", 3: "EDEPTH", 4: "ENOMEM", 5: "ECUDA", 6: "EDEVICE",
+          7: "ETIMEOUT"}
+
+
+class CBTError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: CBT_{ERRORS.get(code, code)}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Loads the CUDA library (built in-tree by ``build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libcbt.so not built ({path}); run paper_2407_02215_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, U32, I32 = C.c_void_p, C.c_uint32, C.c_int32
+    lib.cbt_halfedges_from_faces.argtypes = [I32, P, P, I32, P, P, P, P, P]
+    lib.cbt_workspace_bytes.argtypes = [I32, I32]
+    lib.cbt_workspace_bytes.restype = C.c_size_t
+    lib.cbt_create.argtypes = [I32, P, P, P, P, P, I32, P, I32, I32, P, C.c_size_t, P,
+                               C.POINTER(C.c_void_p)]
+    lib.cbt_update.argtypes = [P, P, P]
+    lib.cbt_live_count.argtypes = [P, C.POINTER(U32), P]
+    lib.cbt_leaves.argtypes = [P, P, P, P, U32, C.POINTER(U32), P]
+    lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
+    lib.cbt_cbt.argtypes = [P, P, P, P]
+    lib.cbt_stats.argtypes = [P, P, P]
+    lib.cbt_destroy.argtypes = [P]
+    lib.cbt_last_launch_count.argtypes = [P]
+    lib.cbt_last_launch_count.restype = U32
+    _lib = lib
+    return lib
+
+
+class Frame(C.Structure):
+    """Mirror of ``cbt_frame`` (include/cbt.h)."""
+
+    _fields_ = [
+        ("eye", C.c_double * 3),
+        ("planes", C.c_float * 15),
+        ("q", C.c_float),
+        ("nplanes", C.c_uint32),
+        ("mode", C.c_uint32),
+        ("seed", C.c_uint32),
+        ("precision", C.c_uint32),
+        ("fixed_shift", C.c_int32),
+        ("gate", C.c_uint32),
+        ("split_list", C.c_void_p),
+        ("n_split", C.c_uint32),
+        ("merge_list", C.c_void_p),
+        ("n_merge", C.c_uint32),
+    ]
+
+
+STAT_FIELDS = ["live_before", "live_after", "free_before", "split_wishes", "merge_candidates",
+               "split_granted", "merge_granted", "split_bisectors", "merged_bisectors",
+               "merge_groups", "allocated", "relinked", "frame", "error"]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_uint32) for n in STAT_FIELDS]
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _t_ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def halfedges_from_faces(mesh) -> dict:
+    """Faces -> halfedge arrays with the library's host ingest."""
+    lib = load()
+    H = int(np.asarray(mesh.face_sizes).sum())
+    out = {k: np.zeros(H, np.int32) for k in ("twin", "next", "prev", "vert", "face")}
+    fs = np.ascontiguousarray(mesh.face_sizes, np.int32)
+    fv = np.ascontiguousarray(mesh.face_verts, np.int32)
+    rc = lib.cbt_halfedges_from_faces(len(fs), _np_ptr(fs), _np_ptr(fv), H, _np_ptr(out["twin"]),
+                                      _np_ptr(out["next"]), _np_ptr(out["prev"]),
+                                      _np_ptr(out["vert"]), _np_ptr(out["face"]))
+    if rc:
+        raise CBTError(rc, "cbt_halfedges_from_faces")
+    return out
+
+
+def workspace_bytes(H: int, D: int) -> int:
+    return int(load().cbt_workspace_bytes(H, D))
+
+
+def frame_struct(fp, device) -> tuple:
+    """Packs a frame-parameter object (fields as in cbt_frame) into the C
+    struct; LIST-mode heap IDs are uploaded to the device."""
+    f = Frame()
+    for i in range(3):
+        f.eye[i] = float(fp.eye[i])
+    pl = np.asarray(fp.planes, np.float32).reshape(-1)
+    for i in range(15):
+        f.planes[i] = float(pl[i]) if i < pl.size else 0.0
+    f.q = float(np.float32(fp.q))
+    f.nplanes = int(fp.nplanes)
+    f.mode = int(fp.mode)
+    f.seed = int(fp.seed)
+    f.precision = int(fp.precision)
+    f.fixed_shift = int(fp.fixed_shift)
+    f.gate = int(fp.gate)
+    keep = []
+    for name, cnt, arr in (("split_list", "n_split", getattr(fp, "split_list", ())),
+                           ("merge_list", "n_merge", getattr(fp, "merge_list", ()))):
+        a = np.sort(np.asarray(arr, np.uint64))
+        if a.size:
+            t = torch.from_numpy(a.view(np.int64)).to(device)
+            keep.append(t)
+            setattr(f, name, t.data_ptr())
+        setattr(f, cnt, int(a.size))
+    return f, keep
+
+
+class CBT:
+    """One instance: a halfedge mesh and a pool of 2^D bisectors on a GPU."""
+
+    def __init__(self, mesh=None, D: int = 16, max_depth: int = 14, halfedges=None, pos=None,
+                 device="cuda", stream=None):
+        lib = load()
+        if halfedges is None:
+            halfedges = halfedges_from_faces(mesh)
+        if pos is None:
+            pos = mesh.pos
+        self.halfedges = halfedges
+        pos = np.ascontiguousarray(pos, np.float64)
+        H = int(halfedges["twin"].shape[0])
+        self.H, self.D, self.max_depth = H, D, max_depth
+        self.cap = 1 << D
+        self.device = torch.device(device)
+        nbytes = lib.cbt_workspace_bytes(H, D)
+        if nbytes == 0:
+            raise CBTError(1, "cbt_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        he = {k: np.ascontiguousarray(v, np.int32) for k, v in halfedges.items()}
+        rc = lib.cbt_create(H, _np_ptr(he["twin"]), _np_ptr(he["next"]), _np_ptr(he["prev"]),
+                            _np_ptr(he["vert"]), _np_ptr(he["face"]), pos.shape[0], _np_ptr(pos),
+                            D, max_depth, _t_ptr(self.workspace), nbytes, _stream_ptr(stream),
+                            C.byref(h))
+        if rc:
+            raise CBTError(rc, "cbt_create")
+        self._h = h
+        self._keep = []
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.cbt_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def update(self, fp, stream=None):
+        f, keep = frame_struct(fp, self.device)
+        self._keep = keep
+        rc = _lib.cbt_update(self._h, C.byref(f), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_update")
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(_lib.cbt_last_launch_count(self._h))
+
+    def live_count(self, stream=None) -> int:
+        n = C.c_uint32()
+        rc = _lib.cbt_live_count(self._h, C.byref(n), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_live_count")
+        return int(n.value)
+
+    def leaves(self, stream=None):
+        n = self.live_count(stream)
+        slots = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        heap = torch.empty(max(n, 1), dtype=torch.int64, device=self.device)
+        links = torch.empty((max(n, 1), 3), dtype=torch.int32, device=self.device)
+        cnt = C.c_uint32()
+        rc = _lib.cbt_leaves(self._h, _t_ptr(slots), _t_ptr(heap), _t_ptr(links), max(n, 1),
+                             C.byref(cnt), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_leaves")
+        n = int(cnt.value)
+        return slots[:n], heap[:n], links[:n]
+
+    def vertices(self, origin, precision=0, fixed_shift=20, out=None, stream=None):
+        n = self.live_count(stream)
+        if out is None:
+            out = torch.empty((max(n, 1), 3, 3), dtype=torch.float32, device=self.device)
+        o = (C.c_double * 3)(*[float(x) for x in origin])
+        cnt = C.c_uint32()
+        rc = _lib.cbt_vertices(self._h, _t_ptr(out), o, precision, fixed_shift, out.shape[0],
+                               C.byref(cnt), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_vertices")
+        return out[:int(cnt.value)]
+
+    def cbt(self, stream=None):
+        W = max(1, self.cap // 32)
+        bits = torch.empty(W, dtype=torch.int32, device=self.device)
+        sums = torch.empty(2 * W, dtype=torch.int32, device=self.device)
+        rc = _lib.cbt_cbt(self._h, _t_ptr(bits), _t_ptr(sums), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_cbt")
+        return bits, sums
+
+    def stats(self, stream=None, check=True) -> dict:
+        s = Stats()
+        rc = _lib.cbt_stats(self._h, C.byref(s), _stream_ptr(stream))
+        if rc and (check or rc != 6):
+            raise CBTError(rc, f"cbt_stats (device error bits {s.error:#x})")
+        return {n: int(getattr(s, n)) for n in STAT_FIELDS}

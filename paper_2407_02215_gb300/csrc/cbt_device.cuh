@@ -1,0 +1,290 @@
+// Device-side data layout and helpers of the CBT bisection update.
+//
+// Per instance (one halfedge mesh, one pool of 2^D slots) the workspace holds:
+//   heap[cap]  u64   bisector heap ID j (Sec. 2.3; root of h = 2^ch + h)
+//   nb[cap]    uint4 {Twin, Next, Prev, rev}: neighbour slots across the edges
+//                    (v0,v1), (v1,v2), (v2,v0); rev holds, per link, which edge
+//                    of the neighbour points back (2 bits each, 3 = none)
+//   cd[cap]    uint2 {cmd, dest}: per-frame command word and the index into
+//                    the free list of the bisector's first new record
+//   bits[W]    u32   CBT bitfield, W = max(1, cap / 32) words
+//   sums[2W]   u32   CBT sum tree above the words in heap order: sums[1] is the
+//                    root, sums[W + w] = popc(bits[w]) (Sec. 3.1)
+//   live[cap]  u32   slots of the live bisectors, ascending (Alg. 7 for all i)
+//   freel[cap] u32   the first A zero bits of the frame-start bitfield (Alg. 8)
+//   scan[cap]  u32   per live index: split cost, then its running total
+//   status[]   u64   look-back tile descriptors of the three scans
+//   root64[H*9], rel[H*9]: root vertices (FP64) and their per-frame offsets
+//                    from the camera (FP32, fixed point or FP64)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cbtgpu {
+
+constexpr uint32_t kNull = 0xFFFFFFFFu;
+
+// cmd word bits.
+constexpr uint32_t kR = 1u, kN = 2u, kP = 4u;  // split bits (R5 reading)
+constexpr uint32_t kSplitMask = 7u;
+constexpr uint32_t kMerged = 1u << 3;
+constexpr uint32_t kSplitWish = 1u << 4;
+constexpr uint32_t kMergeWish = 1u << 5;
+constexpr uint32_t kMergeGrant = 1u << 6;
+constexpr uint32_t kDepthOdd = 1u << 7;
+constexpr uint32_t kHeapOdd = 1u << 8;
+
+// Edge indices of a bisector: Twin (v0,v1), Next (v1,v2), Prev (v2,v0).
+constexpr int kT = 0, kNe = 1, kPe = 2;
+// Portion of an old edge covered by a new edge: whole, the half at the
+// edge's first vertex, the half at its second vertex (in the bisector's own
+// vertex order: Twin v0->v1, Next v1->v2, Prev v2->v0).
+constexpr int kWhole = 0, kFirst = 1, kSecond = 2;
+
+// Device error bits (mirrors CBT_DERR_*).
+constexpr uint32_t kErrChain = 1u, kErrLink = 2u, kErrTimeout = 4u, kErrRange = 8u,
+                   kErrOverflow = 16u;
+
+enum StatIdx {
+    kStLiveBefore = 0, kStLiveAfter, kStFreeBefore, kStSplitWishes, kStMergeCand,
+    kStSplitGranted, kStMergeGranted, kStSplitBis, kStMergedBis, kStMergeGroups,
+    kStAllocated, kStRelinked, kStFrame, kStCount
+};
+
+struct Globals {
+    uint32_t N;         // live bisectors at frame start (CBT root)
+    uint32_t F;         // free slots at frame start
+    uint32_t A;         // allocations of this frame
+    uint32_t Mg;        // granted merge cost of this frame
+    uint32_t err;       // sticky error bits
+    uint32_t done;      // last-block counter of the reduction
+    uint32_t tickets[4];
+    uint32_t stats[kStCount];
+    uint32_t pad[64 - 10 - kStCount];
+};
+static_assert(sizeof(Globals) == 256, "Globals must be 256 bytes");
+
+struct Inst {
+    uint64_t* heap;
+    uint4* nb;
+    uint2* cd;
+    uint32_t* bits;
+    uint32_t* sums;
+    uint32_t* live;
+    uint32_t* freel;
+    uint32_t* scan;
+    unsigned long long* status;  // [3][ntiles_items] then [ntiles_words]
+    double* root64;
+    void* rel;
+    Globals* g;
+    uint32_t cap, W, D, H, ch, max_depth;
+    uint32_t ntiles_items;  // ceil(cap / kTileItems)
+    uint32_t ntiles_words;  // W / tile_words
+    uint32_t tile_words;    // min(W, kTileWords)
+};
+
+struct FrameP {
+    double eye[3];
+    float planes[15];
+    float q;
+    uint32_t nplanes, mode, seed, precision;
+    int32_t shift;
+    uint32_t gate;
+    const uint64_t* split_list;
+    uint32_t n_split;
+    const uint64_t* merge_list;
+    uint32_t n_merge;
+    uint32_t frame;  // frame counter (RANDOM mode key)
+};
+
+constexpr int kThreads = 256;
+constexpr int kItemsPerThread = 4;
+constexpr uint32_t kTileItems = kThreads * kItemsPerThread;  // 1024 live indices
+constexpr uint32_t kTileWords = 1024;                         // 32768 bits
+
+// ------------------------------------------------------------------ bits
+
+__device__ __forceinline__ int bitlen64(uint64_t x) { return 64 - __clzll((long long)x); }
+__device__ __forceinline__ int depth_of(uint64_t j, uint32_t ch) { return bitlen64(j) - 1 - (int)ch; }
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    // SplitMix64 (Steele, Lea & Flood 2014), used as a counter-based hash.
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ double pow2d(int e) {
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+__device__ __forceinline__ void set_err(Globals* g, uint32_t e) { atomicOr(&g->err, e); }
+
+// ------------------------------------------------- Alg. 2 / Eq. 1 decode
+
+// Integer form of Alg. 2 evaluated from the first split down: with W the
+// weights over 2^k after k levels, a 0 bit maps the rows (r0, r1, r2) to
+// (2 r0, 2 r2, r0 + r1) and a 1 bit to (2 r2, 2 r1, r0 + r1) (Eq. 1 times 2).
+// W = 2^d M exactly while entries fit T (T = u32 for d <= 31).
+template <typename T>
+__device__ __forceinline__ void decode_weights(uint64_t j, int d, T W[9], T Wp[9]) {
+    T a[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+#pragma unroll 1
+    for (int lvl = d - 1; lvl >= 0; --lvl) {
+        if (lvl == 0) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Wp[k] = a[k];
+        }
+        const bool b = (j >> lvl) & 1ull;
+        T n[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            n[6 + c] = a[c] + a[3 + c];
+            n[c] = (b ? a[6 + c] : a[c]) << 1;
+            n[3 + c] = (b ? a[3 + c] : a[6 + c]) << 1;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a[k] = n[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) W[k] = a[k];
+    if (d == 0) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Wp[k] = a[k];
+    }
+}
+
+// Correctly rounded signed 128-bit integer -> float: shift down to 63
+// significant bits with a sticky bit (round to odd), then one RN conversion.
+__device__ __forceinline__ float i128_to_float(__int128 s) {
+    const bool neg = s < 0;
+    unsigned __int128 u = neg ? (unsigned __int128)(-s) : (unsigned __int128)s;
+    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    float f;
+    if (hi == 0 && (lo >> 63) == 0) {
+        f = __ull2float_rn(lo);
+    } else {
+        const int bl = hi ? 128 - __clzll((long long)hi) : 64;
+        const int sh = bl - 63;
+        const unsigned __int128 mask = (((unsigned __int128)1) << sh) - 1;
+        const uint64_t m = (uint64_t)(u >> sh) | (uint64_t)((u & mask) != 0);
+        f = __fmul_rn(__ull2float_rn(m), pow2f(sh));
+    }
+    return neg ? -f : f;
+}
+
+// Vertices of a bisector relative to the frame's origin, rounded to FP32:
+//   FP32:  (w0 R0 + w1 R1) + w2 R2, w = float(W) 2^-d (no contraction);
+//   FIXED: float(sum W X) 2^-(d + shift), the sum exact in 128 bits;
+//   FP64:  float((w0 D0 + w1 D1) + w2 D2), w = double(W) 2^-d.
+template <typename T>
+__device__ __forceinline__ void eval_vertices(const T W[9], int d, uint32_t precision, int shift,
+                                              const void* rel, uint32_t h, float r[9]) {
+    if (precision == 1) {
+        const long long* X = static_cast<const long long*>(rel) + 9u * h;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                __int128 s = (__int128)(unsigned long long)W[3 * i + 0] * (__int128)X[c];
+                s += (__int128)(unsigned long long)W[3 * i + 1] * (__int128)X[3 + c];
+                s += (__int128)(unsigned long long)W[3 * i + 2] * (__int128)X[6 + c];
+                r[3 * i + c] = __fmul_rn(i128_to_float(s), pow2f(-(d + shift)));
+            }
+    } else if (precision == 2) {
+        const double* Dp = static_cast<const double*>(rel) + 9u * h;
+        const double sc = pow2d(-d);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double w0 = __dmul_rn(__ull2double_rn(W[3 * i + 0]), sc);
+            const double w1 = __dmul_rn(__ull2double_rn(W[3 * i + 1]), sc);
+            const double w2 = __dmul_rn(__ull2double_rn(W[3 * i + 2]), sc);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double t = __dadd_rn(__dadd_rn(__dmul_rn(w0, Dp[c]), __dmul_rn(w1, Dp[3 + c])),
+                                           __dmul_rn(w2, Dp[6 + c]));
+                r[3 * i + c] = __double2float_rn(t);
+            }
+        }
+    } else {
+        const float* R = static_cast<const float*>(rel) + 9u * h;
+        const float sc = pow2f(-d);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float w0 = __fmul_rn(__ull2float_rn(W[3 * i + 0]), sc);
+            const float w1 = __fmul_rn(__ull2float_rn(W[3 * i + 1]), sc);
+            const float w2 = __fmul_rn(__ull2float_rn(W[3 * i + 2]), sc);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                r[3 * i + c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])),
+                                         __fmul_rn(w2, R[6 + c]));
+        }
+    }
+}
+
+// LOD reading: bit0 visible (no plane has all three vertices strictly on its
+// negative side), bit1 big (|v1 - v0|^2 q > |(v0 + v1)/2|^2).
+__device__ __forceinline__ uint32_t lod_test(const float r[9], const FrameP& fp) {
+    uint32_t vis = 1u;
+    for (uint32_t p = 0; p < fp.nplanes; ++p) {
+        bool all_out = true;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float s = __fadd_rn(__fadd_rn(__fmul_rn(fp.planes[3 * p], r[3 * v]),
+                                                __fmul_rn(fp.planes[3 * p + 1], r[3 * v + 1])),
+                                      __fmul_rn(fp.planes[3 * p + 2], r[3 * v + 2]));
+            all_out = all_out && (s < 0.0f);
+        }
+        if (all_out) vis = 0u;
+    }
+    const float ex = __fsub_rn(r[3], r[0]), ey = __fsub_rn(r[4], r[1]), ez = __fsub_rn(r[5], r[2]);
+    const float mx = __fmul_rn(0.5f, __fadd_rn(r[0], r[3]));
+    const float my = __fmul_rn(0.5f, __fadd_rn(r[1], r[4]));
+    const float mz = __fmul_rn(0.5f, __fadd_rn(r[2], r[5]));
+    const float L2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+    const float R2 = __fadd_rn(__fadd_rn(__fmul_rn(mx, mx), __fmul_rn(my, my)), __fmul_rn(mz, mz));
+    const uint32_t big = __fmul_rn(L2, fp.q) > R2 ? 1u : 0u;
+    return vis | (big << 1);
+}
+
+__device__ __forceinline__ bool in_sorted(const uint64_t* a, uint32_t n, uint64_t x) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2u;
+        if (a[mid] < x)
+            lo = mid + 1u;
+        else
+            hi = mid;
+    }
+    return lo < n && a[lo] == x;
+}
+
+// --------------------------------------------------------- saturating pairs
+
+constexpr uint32_t kSat = 0x7FFFFFFFu;
+
+struct Pair {
+    uint32_t a, b;
+};
+
+__device__ __forceinline__ Pair padd(Pair x, Pair y) {
+    return Pair{min(x.a + y.a, kSat), min(x.b + y.b, kSat)};
+}
+
+constexpr unsigned long long kFlagAgg = 1ull, kFlagIncl = 2ull;
+
+__device__ __forceinline__ unsigned long long pack_status(unsigned long long flag, Pair v) {
+    return (flag << 62) | ((unsigned long long)v.a << 31) | (unsigned long long)v.b;
+}
+__device__ __forceinline__ unsigned long long status_flag(unsigned long long s) { return s >> 62; }
+__device__ __forceinline__ Pair status_val(unsigned long long s) {
+    return Pair{(uint32_t)((s >> 31) & kSat), (uint32_t)(s & kSat)};
+}
+
+}  // namespace cbtgpu

@@ -1,0 +1,104 @@
+"""Parity of the CUDA library with the CPU oracle, frame by frame: the live
+slots, heap IDs, neighbour links, CBT bitfield and every CBT sum must be
+identical (integer state, bit-exact), and so must the per-frame counters."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle
+from workloads.cameras import (GATE_PAPER, MODE_FORCE_MERGE, MODE_FORCE_SPLIT, MODE_LIST,
+                               MODE_RANDOM, PREC_FIXED, PREC_FP32, PREC_FP64, forced_params)
+from tests.gpu_helpers import assert_same_state, run_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def CBT():
+    import paper_2407_02215_gb300 as P
+    P.build_library()
+    return P.CBT
+
+
+TINY = [
+    ("fig1", W.meshes.fig1_mesh, 8, 6),
+    ("tetra", W.meshes.tetra_mesh, 9, 7),
+    ("cube", W.meshes.cube_mesh, 10, 8),
+    ("grid2", lambda: W.meshes.grid_mesh(2, 2, 0.5, seed=7), 9, 7),
+]
+
+
+@pytest.mark.parametrize("name,make,D,md", TINY)
+def test_create(CBT, name, make, D, md):
+    m = make()
+    g, o = CBT(m, D, md), Oracle(m, D, md)
+    assert_same_state(g, o, "create")
+
+
+@pytest.mark.parametrize("name,make,D,md", TINY)
+def test_random_frames(CBT, name, make, D, md):
+    frames = [forced_params(MODE_RANDOM, seed=21) for _ in range(50)]
+    run_pair(make(), D, md, frames, CBT, Oracle)
+
+
+def test_small_pools_and_ragged_words(CBT):
+    """Pools of 2^3..2^6 slots (less than one or a few bitfield words) under
+    random requests: the gate keeps allocations within the free bits."""
+    for D in (4, 5, 6, 7):
+        frames = [forced_params(MODE_RANDOM, seed=D) for _ in range(40)]
+        run_pair(W.meshes.fig1_mesh(), D, 8, frames, CBT, Oracle)
+
+
+def test_paper_gate(CBT):
+    frames = [forced_params(MODE_RANDOM, seed=4, gate=GATE_PAPER) for _ in range(40)]
+    run_pair(W.meshes.cube_mesh(), 9, 8, frames, CBT, Oracle)
+
+
+def test_worked_example_frames(CBT):
+    """The paper's compatibility-chain and decimation example (Fig. 3)."""
+    m = W.meshes.fig1_mesh()
+    ch = 4
+    b7 = 16 + 7
+    b14 = (16 + 7) * 2
+    frames = [forced_params(MODE_LIST, split_list=np.array([b7], np.uint64)),
+              forced_params(MODE_LIST, split_list=np.array([b14], np.uint64)),
+              forced_params(MODE_FORCE_MERGE), forced_params(MODE_FORCE_MERGE)]
+    g, o = run_pair(m, 8, 6, frames, CBT, Oracle)
+    assert g.live_count() == 12
+
+
+def test_uniform_closed_form(CBT):
+    spec = W.configs.config1_uniform(10)
+    g, o = run_pair(spec.mesh, spec.D, spec.max_depth, spec.frames[:10], CBT, Oracle)
+    assert g.live_count() == 24 * 2**10
+    _, heap, _ = g.leaves()
+    want = sorted(((32 + h) << 10) + p for h in range(24) for p in range(1 << 10))
+    assert sorted(heap.cpu().numpy().tolist()) == want
+    for fp in spec.frames[10:]:
+        g.update(fp)
+    assert g.live_count() == 24
+
+
+def test_cube_lod_path(CBT):
+    spec = W.configs.config1()
+    run_pair(spec.mesh, spec.D, spec.max_depth, spec.frames, CBT, Oracle)
+
+
+@pytest.mark.parametrize("prec", [PREC_FP32, PREC_FIXED, PREC_FP64])
+def test_grid_lod_precisions(CBT, prec):
+    """A 24x24 grid flythrough under each vertex-evaluation form."""
+    mesh = W.meshes.grid_mesh(24, 24, 0.1, seed=9)
+    cams = W.cameras.flythrough_path(30, seed=9, alt_lo=0.02)
+    frames = [W.cameras.frame_params(c, 2.0, precision=prec) for c in cams]
+    run_pair(mesh, 17, 22, frames, CBT, Oracle, check_every=5)
+
+
+@pytest.mark.parametrize("prec", [PREC_FP32, PREC_FIXED, PREC_FP64])
+def test_vertices_bit_exact(CBT, prec):
+    spec = W.configs.config1()
+    g, o = run_pair(spec.mesh, spec.D, spec.max_depth, spec.frames[:8], CBT, Oracle, check_every=8)
+    eye = spec.frames[7].eye
+    vg = g.vertices(eye, prec, 20).cpu().numpy()
+    vo = o.vertices(eye, prec, 20)
+    assert vg.shape == vo.shape
+    assert np.array_equal(vg.view(np.uint32), vo.view(np.uint32))
