@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the per-frame CBT adaptive-bisection update on GB300.
+
+One step = one frame of the whole update (classify, chain gate, chain
+scatter, allocation, free-slot decode, fill/relink, CBT reduction + live-slot
+compaction, vertex export) over the grid workload: a 100 x 100 mixed
+quad/triangle mesh (42,034 halfedges), a pool of 2^20 bisectors, max depth
+26, a 120-frame seeded flythrough, LOD threshold 2 px at 1920x1080.
+
+Frames are stateful: the timed run starts from the root bisectors and plays
+frames 0..K-1; the W warm-up frames run on a separate, discarded instance.
+The pool (about 55 MB) fits in L2, so L2 is flushed (a 256 MiB write) before
+every timed frame, outside the frame's CUDA-event interval.
+
+value = bisectors updated per second = sum over frames of the live count at
+frame start / sum of frame times (device time, CUDA events). With --gpus N
+(torchrun) every rank runs its own replica of the workload (the update of one
+instance does not shard); value sums the ranks' bisectors over the slowest
+rank's time.
+
+--impl reference times the CPU oracle (sequential C, one core) on the same
+workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "bisectors updated/sec (per-frame CBT bisection update)"
+UNIT = "bisectors/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def frames_for(spec, K):
+    """K stateful frames: the camera path, continued back and forth."""
+    fr = list(spec.frames)
+    out = []
+    while len(out) < K:
+        out.extend(fr if (len(out) // len(fr)) % 2 == 0 else fr[::-1])
+    return out[:K]
+
+
+def workload_config(spec, K):
+    return {"workload": f"{spec.name}: {spec.mesh.name} ({spec.mesh.H} halfedges), pool 2^{spec.D}, "
+                        f"max depth {spec.max_depth}, {K}-frame flythrough, LOD 2 px at 1920x1080",
+            "halfedges": spec.mesh.H, "pool_log2": spec.D, "max_depth": spec.max_depth,
+            "frames": K, "l2": "flushed before every timed frame (256 MiB write)"}
+
+
+# ------------------------------------------------------------ algorithmic bytes
+
+def algorithmic_bytes(kernel: str, st: dict, cap: int) -> float:
+    """Bytes each kernel must move per frame at minimum, from the frame's
+    counters: N live at frame start, S split and M merged bisectors, A new
+    records, U relinked unchanged neighbours, SW split wishes, MC merge
+    candidates, Wd bitfield words."""
+    N, A, U = st["live_before"], st["allocated"], st["relinked"]
+    S, M = st["split_bisectors"], st["merged_bisectors"]
+    SW, MC = st["split_wishes"], st["merge_candidates"]
+    Wd = max(1, cap // 32)
+    N2 = st["live_after"]
+    return {
+        # live slot, heap ID in; command word and cost out; the twin record
+        # (links + heap) of every split wish
+        "classify": 20.0 * N + 24.0 * SW,
+        # live slot, command, cost in; running total out; group members'
+        # records (3 x links + heap + command) per merge candidate
+        "gate": 16.0 * N + 3 * 28.0 * MC,
+        # live slot, command, running total; command OR on chain members
+        "scatter": 12.0 * N + 28.0 * SW,
+        # live slot and command in, destination out for changed bisectors
+        "alloc": 8.0 * N + 4.0 * (S + M),
+        # bitfield words up to the A-th zero (at most all) and A slots out
+        "free": 4.0 * Wd + 4.0 * A,
+        # live slot + command/destination per live; changed records in; new
+        # records (heap 8 + links 16) out; one neighbour command/destination
+        # and free-list entry per external edge (about 3 per new record);
+        # 8 bytes per relinked neighbour
+        "fill": 12.0 * N + 24.0 * (S + M) + 24.0 * A + 3 * 12.0 * A + 8.0 * U,
+        # bitfield in, sum tree (2 x words) out, live list out
+        "cbt": 4.0 * Wd + 8.0 * Wd + 4.0 * N2,
+        # live slot, heap ID in; 9 floats out
+        "vertices": (4.0 + 8.0 + 36.0) * N2,
+        "prep": 0.0,
+    }.get(kernel, 0.0)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of this GPU's clocks during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.sel = ["-i", uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"]
+        except Exception:
+            self.sel = []
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", *self.sel, f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# -------------------------------------------------------------- CPU oracle
+
+def run_oracle(spec, frames, budget_s):
+    """Times the CPU oracle (one core) on frames until budget_s is spent;
+    returns (bisectors, seconds, frames done)."""
+    from oracle import Oracle
+    o = Oracle(spec.mesh, spec.D, spec.max_depth)
+    bis, secs, done = 0, 0.0, 0
+    for fp in frames:
+        t = time.perf_counter()
+        st = o.update(fp)
+        secs += time.perf_counter() - t
+        bis += st["live_before"]
+        done += 1
+        if secs >= budget_s:
+            break
+    return bis, secs, done
+
+
+def cpu_baseline(spec, frames, budget_s=15.0):
+    bis, secs, done = run_oracle(spec, frames, budget_s)
+    return {"value": bis / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} frames of the same flythrough ({bis} bisector updates, "
+                      f"{secs:.1f} s, sequential C oracle on one host core)"}
+
+
+# -------------------------------------------------------------------- main
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def bench_ours(args):
+    import torch
+
+    from paper_2407_02215_gb300 import CBT
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    spec = W.configs.config2()
+    frames = frames_for(spec, args.steps)
+    warm = frames_for(spec, max(args.warmup, 0))
+
+    # warm-up on a discarded instance
+    g0 = CBT(spec.mesh, spec.D, spec.max_depth, device=dev)
+    vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device=dev)
+    for fp in warm:
+        g0.update(fp, vertices_out=vbuf)
+    torch.cuda.synchronize()
+    g0.stats()
+    del g0
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    g = CBT(spec.mesh, spec.D, spec.max_depth, device=dev)
+    g.set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]
+    clocks = ClockSampler(dev.index or 0) if rank == 0 else None
+    ktimes, kbytes, stats = {}, {}, []
+    launches = 0
+    if clocks:
+        clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    for k, fp in enumerate(frames):
+        flush.zero_()
+        ev[k][0].record()
+        g.update(fp, vertices_out=vbuf)
+        ev[k][1].record()
+        launches += g.last_launch_count
+        kt = g.kernel_times()
+        st = g.stats()
+        stats.append(st)
+        for name, ms in kt.items():
+            ktimes[name] = ktimes.get(name, 0.0) + ms
+            kbytes[name] = kbytes.get(name, 0.0) + algorithmic_bytes(name, st, 1 << spec.D)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    bis = float(sum(s["live_before"] for s in stats))
+    t_local = float(ms.sum()) / 1e3
+    t_max = reduce_max(t_local, world)
+    bis_all = reduce_sum(bis, world)
+    value = bis_all / t_max
+
+    # end to end through the C ABI with host buffers: the frame parameters go
+    # host -> device as launch arguments; the live count and the vertices of
+    # the new triangulation come back to pinned host memory every frame.
+    g2 = CBT(spec.mesh, spec.D, spec.max_depth, device=dev)
+    host_v = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, pin_memory=True)
+    e2e_t, e2e_bis, d2h = 0.0, 0, 0
+    barrier(world)
+    for fp in frames:
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2.update(fp, vertices_out=vbuf)
+        n = g2.live_count()              # cbt_live_count: 4-byte read-back
+        host_v[:n].copy_(vbuf[:n], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        e2e_t += time.perf_counter() - t0
+        d2h += 4 + 36 * n
+    for st in stats:
+        e2e_bis += st["live_before"]
+    e2e_tmax = reduce_max(e2e_t, world)
+    e2e_val = reduce_sum(float(e2e_bis), world) / e2e_tmax
+
+    if rank != 0:
+        return None
+    top = max(ktimes, key=lambda k: ktimes[k])
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    ach = kbytes[top] / (ktimes[top] / 1e3) / 1e9
+    kernel_share = {k: round(v / sum(ktimes.values()), 4) for k, v in sorted(ktimes.items(), key=lambda x: -x[1])}
+    cfg = workload_config(spec, len(frames))
+    cfg["parallelism"] = f"replicas x{world}"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(frames),
+        "warmup": args.warmup, "ms_per_step": float(ms.mean()), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64+fp32",
+        "data": "synthetic (seeded grid mesh and camera path)", "config": cfg,
+        "ms_per_frame_p50": float(np.percentile(ms, 50)), "ms_per_frame_p99": float(np.percentile(ms, 99)),
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": ach, "peak": peak, "unit": "GB/s",
+                     "frac": ach / peak, "peak_source": "measured" if peaks else "fallback",
+                     "traffic": None},
+        "kernel_ms_per_frame": {k: round(v / len(frames), 5) for k, v in ktimes.items()},
+        "kernel_share": kernel_share,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 168,
+                "d2h_bytes_per_step": int(d2h / len(frames))},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, frames, args.cpu_budget)
+    return line
+
+
+def bench_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    spec = W.configs.config2()
+    frames = frames_for(spec, args.steps)
+    warm = frames_for(spec, max(args.warmup, 0))
+    run_oracle(spec, warm, 1e9)
+    bis, secs, done = run_oracle(spec, frames, args.ref_budget)
+    value = bis / secs
+    cfg = workload_config(spec, done)
+    cfg["parallelism"] = "one host core"
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": done,
+        "warmup": args.warmup, "ms_per_step": secs / done * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64+fp32", "impl": "reference",
+        "data": "synthetic (seeded grid mesh and camera path)", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"frames 0..{done - 1} of the flythrough, sequential C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=150.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        line = bench_reference(args)
+    else:
+        import paper_2407_02215_gb300 as P
+        P.build_library()
+        line = bench_ours(args)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -81,7 +81,11 @@ enum { CBT_GATE_CHAIN = 0, CBT_GATE_PAPER = 1 };
  * application; this library's criterion is described at cbt_update).
  * planes: inward normals of up to five planes through the eye, FP32.
  * q: ((viewport height / (2 tan(fovy / 2))) / threshold_px)^2 in FP32.
- * split_list / merge_list: sorted DEVICE arrays of heap IDs (LIST mode). */
+ * split_list / merge_list: sorted DEVICE arrays of heap IDs (LIST mode).
+ * vertices_out: optional DEVICE buffer of vertices_cap * 9 floats; when set,
+ * the frame ends by writing the vertices of the new live bisectors (ascending
+ * slot order) relative to eye in the frame's precision, as cbt_vertices does;
+ * rows beyond vertices_cap are not written (size it 2^D rows to be safe). */
 typedef struct {
     double eye[3];
     float planes[5][3];
@@ -96,6 +100,8 @@ typedef struct {
     uint32_t n_split;
     const uint64_t* merge_list;
     uint32_t n_merge;
+    float* vertices_out;
+    uint32_t vertices_cap;
 } cbt_frame;
 
 /* Per-frame counters (read with cbt_stats). */
@@ -206,6 +212,15 @@ void cbt_destroy(cbt_state* st);
 
 /* Number of kernel launches the last cbt_update enqueued. */
 uint32_t cbt_last_launch_count(const cbt_state* st);
+
+/* Per-kernel timing of cbt_update with CUDA events recorded on the update's
+ * stream between its kernels (off by default). cbt_kernel_times waits for the
+ * last frame and writes up to n durations in ms, in launch order; it returns
+ * how many were written (0 when timing is off). cbt_kernel_name gives the
+ * name of the k-th kernel of a frame. */
+int cbt_set_timing(cbt_state* st, int on);
+uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n);
+const char* cbt_kernel_name(uint32_t k);
 
 #ifdef __cplusplus
 }

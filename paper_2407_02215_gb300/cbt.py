@@ -51,6 +51,11 @@ def load(path: str | None = None):
     lib.cbt_destroy.argtypes = [P]
     lib.cbt_last_launch_count.argtypes = [P]
     lib.cbt_last_launch_count.restype = U32
+    lib.cbt_set_timing.argtypes = [P, C.c_int]
+    lib.cbt_kernel_times.argtypes = [P, P, U32]
+    lib.cbt_kernel_times.restype = U32
+    lib.cbt_kernel_name.argtypes = [U32]
+    lib.cbt_kernel_name.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -72,6 +77,8 @@ class Frame(C.Structure):
         ("n_split", C.c_uint32),
         ("merge_list", C.c_void_p),
         ("n_merge", C.c_uint32),
+        ("vertices_out", C.c_void_p),
+        ("vertices_cap", C.c_uint32),
     ]
 
 
@@ -116,10 +123,14 @@ def workspace_bytes(H: int, D: int) -> int:
     return int(load().cbt_workspace_bytes(H, D))
 
 
-def frame_struct(fp, device) -> tuple:
+def frame_struct(fp, device, vertices_out=None) -> tuple:
     """Packs a frame-parameter object (fields as in cbt_frame) into the C
-    struct; LIST-mode heap IDs are uploaded to the device."""
+    struct; LIST-mode heap IDs are uploaded to the device; vertices_out is an
+    optional float32 [rows, 3, 3] device tensor for the fused export."""
     f = Frame()
+    if vertices_out is not None:
+        f.vertices_out = vertices_out.data_ptr()
+        f.vertices_cap = int(vertices_out.shape[0])
     for i in range(3):
         f.eye[i] = float(fp.eye[i])
     pl = np.asarray(fp.planes, np.float32).reshape(-1)
@@ -184,8 +195,8 @@ class CBT:
     def handle(self):
         return self._h
 
-    def update(self, fp, stream=None):
-        f, keep = frame_struct(fp, self.device)
+    def update(self, fp, stream=None, vertices_out=None):
+        f, keep = frame_struct(fp, self.device, vertices_out)
         self._keep = keep
         rc = _lib.cbt_update(self._h, C.byref(f), _stream_ptr(stream))
         if rc:
@@ -194,6 +205,17 @@ class CBT:
     @property
     def last_launch_count(self) -> int:
         return int(_lib.cbt_last_launch_count(self._h))
+
+    def set_timing(self, on: bool = True):
+        rc = _lib.cbt_set_timing(self._h, 1 if on else 0)
+        if rc:
+            raise CBTError(rc, "cbt_set_timing")
+
+    def kernel_times(self) -> dict:
+        """Per-kernel durations (ms) of the last frame, by kernel name."""
+        buf = (C.c_float * 16)()
+        n = _lib.cbt_kernel_times(self._h, buf, 16)
+        return {_lib.cbt_kernel_name(k).decode(): float(buf[k]) for k in range(n)}
 
     def live_count(self, stream=None) -> int:
         n = C.c_uint32()

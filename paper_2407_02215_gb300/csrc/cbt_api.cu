@@ -13,6 +13,10 @@ int validate_halfedges(int32_t H, const int32_t* twin, const int32_t* next, cons
 
 using namespace cbtgpu;
 
+constexpr int kMaxKernels = 10;
+const char* const kKernelNames[kMaxKernels] = {"prep", "classify", "gate", "scatter", "alloc",
+                                                "free", "fill", "cbt", "vertices", ""};
+
 struct cbt_state {
     Inst inst;
     void* workspace;
@@ -20,6 +24,9 @@ struct cbt_state {
     int sms;
     uint32_t frame;
     uint32_t launches;
+    bool timing;
+    uint32_t timed;  // kernels timed in the last frame
+    cudaEvent_t ev[kMaxKernels + 1];
 };
 
 namespace {
@@ -107,6 +114,7 @@ bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
     fp.merge_list = f->merge_list;
     fp.n_merge = f->n_merge;
     fp.frame = frame;
+    if (f->vertices_out && f->vertices_cap == 0) return false;
     return true;
 }
 
@@ -203,15 +211,34 @@ extern "C" int cbt_update(cbt_state* st, const cbt_frame* frame, cbt_stream_t st
     if (!frame_from_api(frame, st->frame, fp)) return CBT_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const Inst& I = st->inst;
+    uint32_t k = 0;
+    auto mark = [&]() {
+        if (st->timing) cudaEventRecord(st->ev[k], s);
+        ++k;
+    };
+    mark();
     launch_prep(I, fp, true, grid_prep(st, true), s);
+    mark();
     launch_classify(I, fp, grid_items(st), s);
+    mark();
     launch_gate(I, fp, grid_tiles(st), s);
+    mark();
     launch_scatter(I, grid_items(st), s);
+    mark();
     launch_alloc(I, grid_tiles(st), s);
+    mark();
     launch_free(I, grid_words(st), s);
+    mark();
     launch_fill(I, grid_items(st), s);
+    mark();
     launch_cbt(I, grid_words(st), s);
-    st->launches = 8;
+    mark();
+    if (frame->vertices_out) {
+        launch_vertices(I, fp, frame->vertices_out, frame->vertices_cap, grid_items(st), s);
+        mark();
+    }
+    st->launches = k - 1u;
+    st->timed = st->timing ? k - 1u : 0u;
     st->frame += 1u;
     return check_launch();
 }
@@ -254,7 +281,7 @@ extern "C" int cbt_vertices(cbt_state* st, float* d_out, const double h_origin[3
     fp.shift = fixed_shift;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     launch_prep(st->inst, fp, false, grid_prep(st, false), s);
-    launch_vertices(st->inst, fp, d_out, grid_items(st), s);
+    launch_vertices(st->inst, fp, d_out, cap, grid_items(st), s);
     rc = check_launch();
     if (rc) return rc;
     return cudaStreamSynchronize(s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
@@ -296,6 +323,38 @@ extern "C" int cbt_stats(cbt_state* st, cbt_frame_stats* out, cbt_stream_t strea
     return g.err ? CBT_EDEVICE : CBT_OK;
 }
 
-extern "C" void cbt_destroy(cbt_state* st) { delete st; }
+extern "C" void cbt_destroy(cbt_state* st) {
+    if (!st) return;
+    if (st->timing)
+        for (auto& e : st->ev) cudaEventDestroy(e);
+    delete st;
+}
+
+extern "C" int cbt_set_timing(cbt_state* st, int on) {
+    if (!st) return CBT_EINVAL;
+    if (on && !st->timing) {
+        for (auto& e : st->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return CBT_ECUDA;
+        st->timing = true;
+    } else if (!on && st->timing) {
+        for (auto& e : st->ev) cudaEventDestroy(e);
+        st->timing = false;
+        st->timed = 0;
+    }
+    return CBT_OK;
+}
+
+extern "C" uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n) {
+    if (!st || !st->timing || st->timed == 0 || !ms) return 0u;
+    if (cudaEventSynchronize(st->ev[st->timed]) != cudaSuccess) return 0u;
+    const uint32_t m = std::min(n, st->timed);
+    for (uint32_t k = 0; k < m; ++k) {
+        ms[k] = 0.0f;
+        cudaEventElapsedTime(&ms[k], st->ev[k], st->ev[k + 1]);
+    }
+    return m;
+}
+
+extern "C" const char* cbt_kernel_name(uint32_t k) { return k < kMaxKernels ? kKernelNames[k] : ""; }
 
 extern "C" uint32_t cbt_last_launch_count(const cbt_state* st) { return st ? st->launches : 0u; }

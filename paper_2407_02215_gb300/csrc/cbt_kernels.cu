@@ -926,8 +926,8 @@ __global__ void __launch_bounds__(kThreads) k_leaves(Inst I, uint32_t* slots, ui
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_vertices(Inst I, FrameP fp, float* out) {
-    const uint32_t N = I.sums[1];
+__global__ void __launch_bounds__(kThreads) k_vertices(Inst I, FrameP fp, float* out, uint32_t cap) {
+    const uint32_t N = min(I.sums[1], cap);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const uint32_t s = I.live[i];
         const uint64_t j = I.heap[s];
@@ -977,8 +977,8 @@ void launch_leaves(const Inst& I, uint32_t* slots, uint64_t* heap, uint32_t* lin
                    cudaStream_t s) {
     k_leaves<<<grid, kThreads, 0, s>>>(I, slots, heap, links);
 }
-void launch_vertices(const Inst& I, const FrameP& fp, float* out, int grid, cudaStream_t s) {
-    k_vertices<<<grid, kThreads, 0, s>>>(I, fp, out);
+void launch_vertices(const Inst& I, const FrameP& fp, float* out, uint32_t cap, int grid, cudaStream_t s) {
+    k_vertices<<<grid, kThreads, 0, s>>>(I, fp, out, cap);
 }
 
 }  // namespace cbtgpu

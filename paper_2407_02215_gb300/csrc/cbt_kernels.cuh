@@ -20,6 +20,6 @@ void launch_init(const Inst& I, const int32_t* twin, const int32_t* next, const 
                  const int32_t* face, const double* hpos, int grid, cudaStream_t s);
 void launch_leaves(const Inst& I, uint32_t* slots, uint64_t* heap, uint32_t* links, int grid,
                    cudaStream_t s);
-void launch_vertices(const Inst& I, const FrameP& fp, float* out, int grid, cudaStream_t s);
+void launch_vertices(const Inst& I, const FrameP& fp, float* out, uint32_t cap, int grid, cudaStream_t s);
 
 }  // namespace cbtgpu

@@ -1,0 +1,87 @@
+"""Planet-scale precision form: cube-sphere of radius 6.371e6 m (1536
+halfedges), max depth 48, descent from 2e7 m to 2 m, fixed-point vertex
+evaluation (exact integer weights times integer root offsets)."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle
+from workloads.cameras import PREC_FIXED, PREC_FP32, PREC_FP64
+from tests.gpu_helpers import run_pair
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "planet_oracle.json")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2407_02215_gb300 as P
+    P.build_library()
+    return P
+
+
+def test_planet_reduced_pool_live_oracle(P):
+    """Pool 2^16, every 4th frame of the descent, compared with the oracle
+    frame by frame (the pool saturates, so the gate is exercised)."""
+    spec = W.configs.config3(n_frames=600, D=16)
+    run_pair(spec.mesh, 16, 48, spec.frames[::4], P.CBT, Oracle, check_every=15)
+
+
+def _digest(g):
+    """Same byte layout as tests/golden/make_planet_golden.py."""
+    slots, heap, links = g.leaves()
+    bits, _ = g.cbt()
+    h = hashlib.sha256()
+    for t, dt in ((slots, "<u4"), (heap, "<u8"), (links, "<u4"), (bits, "<u4")):
+        h.update(np.ascontiguousarray(t.cpu().numpy()).view(dt).tobytes())
+    return h.hexdigest()
+
+
+def test_planet_full_size_against_stored_oracle(P):
+    """Pool 2^22 over the whole 600-frame descent: the live count after
+    every frame, the state digests and the final fixed-point vertices equal
+    the oracle's stored results (tests/golden/make_planet_golden.py)."""
+    if not os.path.exists(GOLD):
+        pytest.skip("planet_oracle.json not generated")
+    gold = json.load(open(GOLD))
+    spec = W.configs.config3(n_frames=gold["frames"], D=gold["D"])
+    g = P.CBT(spec.mesh, spec.D, spec.max_depth)
+    for k, fp in enumerate(spec.frames):
+        g.update(fp)
+        assert g.live_count() == gold["live_after"][k], f"frame {k}"
+        if str(k) in gold["state_digest"]:
+            assert g.stats()["error"] == 0
+            assert _digest(g) == gold["state_digest"][str(k)], f"frame {k}"
+    last = spec.frames[-1]
+    v = g.vertices(last.eye, last.precision, last.fixed_shift).cpu().numpy()
+    assert hashlib.sha256(np.ascontiguousarray(v, "<f4").tobytes()).hexdigest() == gold["vertices_digest"]
+
+
+def test_planet_precision_report(P):
+    """Camera 2 m above the surface after the descent on a 2^18 pool:
+    near the camera, fixed-point vertices stay within a micrometre (plus the
+    final FP32 rounding) of the FP64 decode; the FP64-everywhere form is as
+    good; the FP32 form is off by centimetres or more. Errors in mm."""
+    spec = W.configs.config3(n_frames=600, D=18)
+    g = P.CBT(spec.mesh, spec.D, spec.max_depth)
+    o = Oracle(spec.mesh, spec.D, spec.max_depth)
+    for fp in spec.frames[::3]:
+        g.update(fp)
+        o.update(fp)
+    eye = spec.frames[-1].eye
+    exact = o.vertices_f64() - eye[None, None, :]
+    dist = np.linalg.norm(exact, axis=2).min(axis=1)
+    near = np.argsort(dist)[:512]                    # the 512 bisectors closest to the camera
+    assert dist[near].max() < 1e4
+    errs = {}
+    for name, prec in (("fixed", PREC_FIXED), ("fp64", PREC_FP64), ("fp32", PREC_FP32)):
+        v = g.vertices(eye, prec, 20).cpu().numpy().astype(np.float64)
+        errs[name] = float(np.abs(v - exact)[near].max() * 1e3)
+    print("planet vertex error of the 512 bisectors nearest the camera (mm):", errs)
+    assert errs["fixed"] <= 1e-3 * 2 + 1e4 * 2**-24 * 1e3
+    assert errs["fp64"] <= 1e-3 * 2 + 1e4 * 2**-24 * 1e3
+    assert errs["fp32"] > 10.0
