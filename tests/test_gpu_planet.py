@@ -62,10 +62,11 @@ def test_planet_full_size_against_stored_oracle(P):
 
 
 def test_planet_precision_report(P):
-    """Camera 2 m above the surface after the descent on a 2^18 pool:
-    near the camera, fixed-point vertices stay within a micrometre (plus the
-    final FP32 rounding) of the FP64 decode; the FP64-everywhere form is as
-    good; the FP32 form is off by centimetres or more. Errors in mm."""
+    """After the descent (camera 2 m above the surface) on a 2^18 pool:
+    fixed-point vertices are within 2^-19 m plus the final FP32 rounding
+    (2^-24 relative) of the FP64 decode, vertex by vertex; the FP64-everywhere
+    form meets the same bound; the FP32 form is off by centimetres or more
+    (root offsets of ~1e6 m rounded to FP32). Errors printed in mm."""
     spec = W.configs.config3(n_frames=600, D=18)
     g = P.CBT(spec.mesh, spec.D, spec.max_depth)
     o = Oracle(spec.mesh, spec.D, spec.max_depth)
@@ -74,14 +75,15 @@ def test_planet_precision_report(P):
         o.update(fp)
     eye = spec.frames[-1].eye
     exact = o.vertices_f64() - eye[None, None, :]
+    bound = 2.0**-19 + 2.0**-24 * np.abs(exact)
     dist = np.linalg.norm(exact, axis=2).min(axis=1)
-    near = np.argsort(dist)[:512]                    # the 512 bisectors closest to the camera
-    assert dist[near].max() < 1e4
+    near = np.argsort(dist)[:512]
     errs = {}
     for name, prec in (("fixed", PREC_FIXED), ("fp64", PREC_FP64), ("fp32", PREC_FP32)):
         v = g.vertices(eye, prec, 20).cpu().numpy().astype(np.float64)
-        errs[name] = float(np.abs(v - exact)[near].max() * 1e3)
-    print("planet vertex error of the 512 bisectors nearest the camera (mm):", errs)
-    assert errs["fixed"] <= 1e-3 * 2 + 1e4 * 2**-24 * 1e3
-    assert errs["fp64"] <= 1e-3 * 2 + 1e4 * 2**-24 * 1e3
-    assert errs["fp32"] > 10.0
+        e = np.abs(v - exact)
+        errs[name] = {"max_mm": float(e.max() * 1e3), "near512_max_mm": float(e[near].max() * 1e3)}
+        if name != "fp32":
+            assert (e <= bound).all(), name
+    print(f"planet vertex error (mm); nearest bisector {dist.min():.0f} m away:", errs)
+    assert errs["fp32"]["max_mm"] > 10.0
