@@ -222,6 +222,31 @@ int cbt_set_timing(cbt_state* st, int on);
 uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n);
 const char* cbt_kernel_name(uint32_t k);
 
+/* The reduction and live-slot compaction step of cbt_update (the CBT sum
+ * tree and the ascending list of set bits) over a caller's bitfield, for
+ * callers that cannot allocate device memory: a real-time frame loop in which
+ * cudaMalloc/cudaFree would synchronize the device and stall the frame, or a
+ * host application whose device memory all comes from its own allocator or a
+ * graphics interop pool. This entry point allocates nothing; its scratch (a
+ * tile ticket, a finished-tile counter and the look-back descriptors) is one
+ * static device array of 33,024 bytes in this library, held by every GPU that
+ * loads the library until the process exits. The paper has no counterpart to
+ * this entry point.
+ *   d_bitfield: DEVICE u32[max(1, 2^D / 32)], bit s % 32 of word s / 32 is slot
+ *               s (bits at or above 2^D are ignored);
+ *   D: 1 <= D <= 27 (the static scratch covers 4096 tiles of 1024 words);
+ *   d_sums: DEVICE u32[2 * words], written in the layout of cbt_cbt;
+ *   d_live: DEVICE u32[2^D], receives the slots of the set bits, ascending;
+ *   d_count: DEVICE u32, receives the number of set bits.
+ * The first call on a device looks up the scratch's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call clears the part of the scratch it uses before its kernel runs;
+ * calls whose work overlaps on the GPU (other streams, other threads) share
+ * the scratch and race. Errors: CBT_EINVAL (NULL pointer, D < 1),
+ * CBT_ECAPACITY (D > 27), CBT_ECUDA. Asynchronous. */
+int cbt_reduce_compact_static(const uint32_t* d_bitfield, int32_t D, uint32_t* d_sums,
+                              uint32_t* d_live, uint32_t* d_count, cbt_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
