@@ -148,8 +148,8 @@ size_t cbt_workspace_bytes(int32_t H, int32_t D);
  *                    256-byte aligned;
  *   out: receives the state handle (host memory owned by the library).
  * Errors: CBT_EINVAL (malformed mesh), CBT_ECAPACITY, CBT_EDEPTH,
- * CBT_ENOMEM (workspace too small), CBT_ECUDA. Asynchronous on the device
- * side; the host arrays may be freed when it returns. */
+ * CBT_ENOMEM (workspace too small), CBT_ECUDA. Synchronous: the roots and
+ * their CBT are built when it returns; the host arrays may then be freed. */
 int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_t* prev,
                const int32_t* vert, const int32_t* face, int32_t V, const double* pos,
                int32_t D, int32_t max_depth, void* workspace, size_t bytes,
@@ -221,6 +221,97 @@ uint32_t cbt_last_launch_count(const cbt_state* st);
 int cbt_set_timing(cbt_state* st, int on);
 uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n);
 const char* cbt_kernel_name(uint32_t k);
+
+/* Update through a CUDA graph (on: the frame's launches are captured once
+ * and replayed; the frame parameters reach the device through a copy from
+ * pinned host memory that the graph performs). Results are identical either
+ * way. Host only. */
+int cbt_set_graph(cbt_state* st, int on);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent instances updated together: every kernel of the frame is
+ * launched once for the whole batch, whose work items are (instance, tile of
+ * live bisectors) pairs laid out from a device-side prefix over the
+ * instances' live counts. Each instance's result is exactly the one
+ * cbt_update would give it. The states keep their own workspaces; the batch
+ * needs a further caller-owned device workspace for its instance table,
+ * per-instance frame parameters and scan descriptors. A state may belong to
+ * several batches but must not be updated by two of them (or by cbt_update)
+ * concurrently. */
+typedef struct cbt_batch cbt_batch;
+
+/* Bytes of device workspace for a batch of the given states (0 if invalid). */
+size_t cbt_batch_workspace_bytes(cbt_state* const* states, int32_t n);
+
+/* Builds a batch of n distinct states; workspace is caller-owned device
+ * memory of cbt_batch_workspace_bytes(), 256-byte aligned, kept until
+ * cbt_batch_destroy. Errors: CBT_EINVAL, CBT_ENOMEM, CBT_ECUDA. Synchronous. */
+int cbt_batch_create(cbt_state* const* states, int32_t n, void* workspace, size_t bytes,
+                     cbt_stream_t stream, cbt_batch** out);
+
+/* One frame for every instance: frames[b] is instance b's cbt_frame (as for
+ * cbt_update). Asynchronous, except that it waits for the previous frame's
+ * parameter copy before reusing its pinned staging buffer. */
+int cbt_batch_update(cbt_batch* b, const cbt_frame* frames, cbt_stream_t stream);
+
+/* Replay the batch frame as a CUDA graph (see cbt_set_graph). Host only. */
+int cbt_batch_set_graph(cbt_batch* b, int on);
+
+/* Online autotuner: the next 9 * rounds frames try the 9 combinations of
+ * reduction / rank-to-bit tile width (64, 128 or 256 words) and blocks per SM
+ * of the item kernels (4, 8 or 16), one per frame, and then keep the one
+ * with the smallest median frame time. The configuration never changes the
+ * results. cbt_batch_config reads the current choice (tuning = 1 while
+ * trying); cbt_batch_set_config sets it directly. */
+int cbt_batch_autotune(cbt_batch* b, uint32_t rounds);
+int cbt_batch_config(const cbt_batch* b, uint32_t* tile_words, uint32_t* blocks_per_sm, int* tuning);
+int cbt_batch_set_config(cbt_batch* b, uint32_t tile_words, uint32_t blocks_per_sm, cbt_stream_t stream);
+
+/* Per-kernel timing of cbt_batch_update (as cbt_set_timing / cbt_kernel_times). */
+int cbt_batch_set_timing(cbt_batch* b, int on);
+uint32_t cbt_batch_kernel_times(cbt_batch* b, float* ms, uint32_t n);
+uint32_t cbt_batch_last_launch_count(const cbt_batch* b);
+
+/* Releases the batch handle; the workspaces stay the caller's. */
+void cbt_batch_destroy(cbt_batch* b);
+
+/* ------------------------------------------------------------------ serving
+ * A set of resident instances served by ticks: each tick updates, with one
+ * launch per kernel, the subset of instances named in it (each with its own
+ * frame), so requests that arrive while other ticks are on the GPU start in
+ * the next tick. Up to `inflight` ticks can be outstanding, each with its
+ * own device region (so ticks on different streams overlap); an instance may
+ * be in at most one outstanding tick, which keeps its frames in order, and
+ * its result is exactly the one cbt_update would give. */
+typedef struct cbt_server cbt_server;
+
+/* Bytes of device workspace for a server over these states (0 if invalid);
+ * 1 <= inflight <= 16. */
+size_t cbt_server_workspace_bytes(cbt_state* const* states, int32_t n, int32_t inflight);
+
+/* Builds a server; workspace is caller-owned device memory, 256-byte aligned,
+ * kept until cbt_server_destroy. Errors: CBT_EINVAL, CBT_ENOMEM, CBT_ECUDA. */
+int cbt_server_create(cbt_state* const* states, int32_t n, int32_t inflight, void* workspace,
+                      size_t bytes, cbt_server** out);
+
+/* Enqueues one tick on `stream`: instance idx[i] (an index into the server's
+ * states) takes frames[i]. *ticket receives the tick's slot. CBT_EINVAL if an
+ * instance is repeated or already in an outstanding tick, or if the next
+ * slot's previous tick has not been polled yet. Asynchronous. */
+int cbt_server_submit(cbt_server* sv, const int32_t* idx, const cbt_frame* frames, int32_t k,
+                      cbt_stream_t stream, int32_t* ticket);
+
+/* Completion of a tick: 1 when done (live_before[i], if given, receives the
+ * live count of idx[i] at the start of its frame), 0 while pending (wait = 0),
+ * a negative CBT_* code on error. wait != 0 blocks until done. */
+int cbt_server_poll(cbt_server* sv, int32_t ticket, int wait, uint32_t* live_before);
+
+/* 1 if the slot the next submit will use is free. */
+int32_t cbt_server_next_slot_free(const cbt_server* sv);
+
+/* Releases the server (waiting for outstanding ticks); workspaces stay the
+ * caller's. */
+void cbt_server_destroy(cbt_server* sv);
 
 /* The reduction and live-slot compaction step of cbt_update (the CBT sum
  * tree and the ascending list of set bits) over a caller's bitfield, for

@@ -51,6 +51,29 @@ def load(path: str | None = None):
     lib.cbt_destroy.argtypes = [P]
     lib.cbt_last_launch_count.argtypes = [P]
     lib.cbt_last_launch_count.restype = U32
+    lib.cbt_set_graph.argtypes = [P, C.c_int]
+    lib.cbt_batch_workspace_bytes.argtypes = [P, I32]
+    lib.cbt_batch_workspace_bytes.restype = C.c_size_t
+    lib.cbt_batch_create.argtypes = [P, I32, P, C.c_size_t, P, C.POINTER(C.c_void_p)]
+    lib.cbt_batch_update.argtypes = [P, P, P]
+    lib.cbt_batch_set_graph.argtypes = [P, C.c_int]
+    lib.cbt_batch_autotune.argtypes = [P, U32]
+    lib.cbt_batch_config.argtypes = [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(C.c_int)]
+    lib.cbt_batch_set_config.argtypes = [P, U32, U32, P]
+    lib.cbt_batch_set_timing.argtypes = [P, C.c_int]
+    lib.cbt_batch_kernel_times.argtypes = [P, P, U32]
+    lib.cbt_batch_kernel_times.restype = U32
+    lib.cbt_batch_last_launch_count.argtypes = [P]
+    lib.cbt_batch_last_launch_count.restype = U32
+    lib.cbt_batch_destroy.argtypes = [P]
+    lib.cbt_server_workspace_bytes.argtypes = [P, I32, I32]
+    lib.cbt_server_workspace_bytes.restype = C.c_size_t
+    lib.cbt_server_create.argtypes = [P, I32, I32, P, C.c_size_t, C.POINTER(C.c_void_p)]
+    lib.cbt_server_submit.argtypes = [P, P, P, I32, P, C.POINTER(I32)]
+    lib.cbt_server_poll.argtypes = [P, I32, C.c_int, P]
+    lib.cbt_server_next_slot_free.argtypes = [P]
+    lib.cbt_server_next_slot_free.restype = I32
+    lib.cbt_server_destroy.argtypes = [P]
     lib.cbt_set_timing.argtypes = [P, C.c_int]
     lib.cbt_kernel_times.argtypes = [P, P, U32]
     lib.cbt_kernel_times.restype = U32
@@ -206,6 +229,11 @@ class CBT:
     def last_launch_count(self) -> int:
         return int(_lib.cbt_last_launch_count(self._h))
 
+    def set_graph(self, on: bool = True):
+        rc = _lib.cbt_set_graph(self._h, 1 if on else 0)
+        if rc:
+            raise CBTError(rc, "cbt_set_graph")
+
     def set_timing(self, on: bool = True):
         rc = _lib.cbt_set_timing(self._h, 1 if on else 0)
         if rc:
@@ -264,3 +292,133 @@ class CBT:
         if rc and (check or rc != 6):
             raise CBTError(rc, f"cbt_stats (device error bits {s.error:#x})")
         return {n: int(getattr(s, n)) for n in STAT_FIELDS}
+
+
+class Batch:
+    """Several CBT instances updated by one launch per kernel and frame."""
+
+    def __init__(self, instances, stream=None):
+        lib = load()
+        self.instances = list(instances)
+        n = len(self.instances)
+        handles = (C.c_void_p * n)(*[g.handle.value for g in self.instances])
+        self._handles = handles
+        nbytes = lib.cbt_batch_workspace_bytes(handles, n)
+        if nbytes == 0:
+            raise CBTError(1, "cbt_batch_workspace_bytes")
+        self.device = self.instances[0].device
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        rc = lib.cbt_batch_create(handles, n, _t_ptr(self.workspace), nbytes, _stream_ptr(stream), C.byref(h))
+        if rc:
+            raise CBTError(rc, "cbt_batch_create")
+        self._h = h
+        self._keep = []
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.cbt_batch_destroy(self._h)
+            self._h = None
+
+    def update(self, fps, stream=None, vertices_out=None):
+        n = len(self.instances)
+        arr = (Frame * n)()
+        keep = []
+        for b, fp in enumerate(fps):
+            vo = vertices_out[b] if vertices_out is not None else None
+            f, k = frame_struct(fp, self.device, vo)
+            arr[b] = f
+            keep.extend(k)
+        self._keep = keep
+        rc = _lib.cbt_batch_update(self._h, arr, _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_batch_update")
+
+    def set_graph(self, on: bool = True):
+        _lib.cbt_batch_set_graph(self._h, 1 if on else 0)
+
+    def autotune(self, rounds: int = 2):
+        rc = _lib.cbt_batch_autotune(self._h, rounds)
+        if rc:
+            raise CBTError(rc, "cbt_batch_autotune")
+
+    def config(self):
+        tw, bm, tun = C.c_uint32(), C.c_uint32(), C.c_int()
+        _lib.cbt_batch_config(self._h, C.byref(tw), C.byref(bm), C.byref(tun))
+        return {"tile_words": tw.value, "blocks_per_sm": bm.value, "tuning": bool(tun.value)}
+
+    def set_config(self, tile_words: int, blocks_per_sm: int, stream=None):
+        rc = _lib.cbt_batch_set_config(self._h, tile_words, blocks_per_sm, _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_batch_set_config")
+
+    def set_timing(self, on: bool = True):
+        _lib.cbt_batch_set_timing(self._h, 1 if on else 0)
+
+    def kernel_times(self) -> dict:
+        buf = (C.c_float * 16)()
+        n = _lib.cbt_batch_kernel_times(self._h, buf, 16)
+        return {_lib.cbt_kernel_name(k).decode(): float(buf[k]) for k in range(n)}
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(_lib.cbt_batch_last_launch_count(self._h))
+
+
+class Server:
+    """Resident instances served by ticks (see cbt_server in include/cbt.h)."""
+
+    def __init__(self, instances, inflight: int = 2):
+        lib = load()
+        self.instances = list(instances)
+        n = len(self.instances)
+        self._handles = (C.c_void_p * n)(*[g.handle.value for g in self.instances])
+        nbytes = lib.cbt_server_workspace_bytes(self._handles, n, inflight)
+        if nbytes == 0:
+            raise CBTError(1, "cbt_server_workspace_bytes")
+        self.device = self.instances[0].device
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        rc = lib.cbt_server_create(self._handles, n, inflight, _t_ptr(self.workspace), nbytes, C.byref(h))
+        if rc:
+            raise CBTError(rc, "cbt_server_create")
+        self._h = h
+        self.inflight = inflight
+        self._pending = {}
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.cbt_server_destroy(self._h)
+            self._h = None
+
+    def next_slot_free(self) -> bool:
+        return bool(_lib.cbt_server_next_slot_free(self._h))
+
+    def submit(self, idx, fps, stream=None, vertices_out=None) -> int:
+        k = len(idx)
+        arr = (Frame * k)()
+        keep = []
+        for i, fp in enumerate(fps):
+            vo = vertices_out[i] if vertices_out is not None else None
+            f, kp = frame_struct(fp, self.device, vo)
+            arr[i] = f
+            keep.extend(kp)
+        ids = (C.c_int32 * k)(*idx)
+        t = C.c_int32()
+        rc = _lib.cbt_server_submit(self._h, ids, arr, k, _stream_ptr(stream), C.byref(t))
+        if rc:
+            raise CBTError(rc, "cbt_server_submit")
+        self._pending[t.value] = (list(idx), keep)
+        return t.value
+
+    def poll(self, ticket: int, wait: bool = False):
+        """None while pending, else the live counts at frame start."""
+        idx, _ = self._pending[ticket]
+        out = (C.c_uint32 * len(idx))()
+        r = _lib.cbt_server_poll(self._h, ticket, 1 if wait else 0, out)
+        if r < 0:
+            raise CBTError(-r, "cbt_server_poll")
+        if r == 0:
+            return None
+        del self._pending[ticket]
+        return list(out)

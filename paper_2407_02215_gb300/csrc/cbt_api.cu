@@ -1,4 +1,10 @@
 // C ABI of the CBT bisection library (declared in include/cbt.h).
+//
+// A single instance is updated as a batch of one: its workspace holds, after
+// its own arrays, a small batch region (instance table, frame parameters,
+// tile prefixes, look-back descriptors). cbt_batch_* build the same region
+// for many instances in a caller-provided workspace, so that one launch per
+// kernel updates them all.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -13,33 +19,58 @@ int validate_halfedges(int32_t H, const int32_t* twin, const int32_t* next, cons
 
 using namespace cbtgpu;
 
-constexpr int kMaxKernels = 10;
-const char* const kKernelNames[kMaxKernels] = {"prep", "classify", "gate", "scatter", "alloc",
-                                                "free", "fill", "cbt", "vertices", ""};
-
-struct cbt_state {
-    Inst inst;
-    void* workspace;
-    size_t bytes;
-    int sms;
-    uint32_t frame;
-    uint32_t launches;
-    bool timing;
-    uint32_t timed;  // kernels timed in the last frame
-    cudaEvent_t ev[kMaxKernels + 1];
-};
-
 namespace {
 
-struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, status, root64, rel, total;
-    uint32_t cap, W, ntiles_items, ntiles_words, tile_words, ch;
-};
+constexpr int kNumKernels = 9;
+const char* const kKernelNames[kNumKernels] = {"prep", "classify", "gate", "scatter", "alloc",
+                                               "free", "fill", "cbt", "vertices"};
+
+size_t align256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
 
 uint32_t ceil_log2(uint32_t x) {
     uint32_t c = 0;
     while ((1ull << c) < static_cast<uint64_t>(x)) ++c;
     return c;
+}
+
+uint32_t word_tiles(uint32_t W, uint32_t tw) { return W / std::min(W, tw); }
+uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems; }
+
+// Per-instance arrays.
+struct Layout {
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, root64, rel, batch, total;
+    uint32_t cap, W, ch;
+};
+
+// A batch region for instances with the given pool sizes and halfedge counts.
+struct BatchLayout {
+    size_t inst, fps, bg, tile_base, wtile_base, vtile_base, rel_base, status, total;
+    uint32_t Titems, TwordsMax, Trel;
+};
+
+BatchLayout batch_layout(uint32_t n, const uint32_t* cap, const uint32_t* W, const uint32_t* H) {
+    BatchLayout L{};
+    for (uint32_t b = 0; b < n; ++b) {
+        L.Titems += item_tiles(cap[b]);
+        L.TwordsMax += word_tiles(W[b], kMinTileWords);
+        L.Trel += 9u * H[b];
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.inst = take(sizeof(Inst) * n);
+    L.fps = take(sizeof(FrameP) * n);
+    L.bg = take(sizeof(BatchGlobals));
+    L.tile_base = take(4u * (n + 1u));
+    L.wtile_base = take(4u * (n + 1u));
+    L.vtile_base = take(4u * (n + 1u));
+    L.rel_base = take(4u * (n + 1u));
+    L.status = take(8u * (2u * static_cast<size_t>(L.Titems) + L.TwordsMax));
+    L.total = off;
+    return L;
 }
 
 bool make_layout(int32_t H, int32_t D, Layout& L) {
@@ -48,13 +79,10 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     if (static_cast<uint32_t>(D) < L.ch) return false;
     L.cap = 1u << D;
     L.W = std::max(1u, L.cap / 32u);
-    L.tile_words = std::min(L.W, kTileWords);
-    L.ntiles_words = L.W / L.tile_words;
-    L.ntiles_items = (L.cap + kTileItems - 1u) / kTileItems;
     size_t off = 0;
     auto take = [&](size_t n) {
         const size_t o = off;
-        off = (off + n + 255u) & ~static_cast<size_t>(255u);
+        off = align256(off + n);
         return o;
     };
     const size_t cap = L.cap, h = static_cast<size_t>(H);
@@ -67,28 +95,14 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.live = take(4u * cap);
     L.freel = take(4u * cap);
     L.scan = take(4u * cap);
-    L.status = take(8u * (3u * static_cast<size_t>(L.ntiles_items) + L.ntiles_words));
+    L.grp = take(16u * cap);
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
+    const uint32_t Hh = static_cast<uint32_t>(H);
+    const BatchLayout B = batch_layout(1, &L.cap, &L.W, &Hh);
+    L.batch = take(B.total);
     L.total = off;
     return true;
-}
-
-int grid_items(const cbt_state* st) {
-    const uint32_t want = (st->inst.cap + kThreads - 1u) / kThreads;
-    return static_cast<int>(std::max(1u, std::min<uint32_t>(want, static_cast<uint32_t>(st->sms) * 8u)));
-}
-int grid_tiles(const cbt_state* st) {
-    return static_cast<int>(std::max(1u, std::min<uint32_t>(st->inst.ntiles_items, static_cast<uint32_t>(st->sms) * 2u)));
-}
-int grid_words(const cbt_state* st) {
-    return static_cast<int>(std::max(1u, std::min<uint32_t>(st->inst.ntiles_words, static_cast<uint32_t>(st->sms) * 2u)));
-}
-int grid_prep(const cbt_state* st, bool frame_start) {
-    uint32_t n = 9u * st->inst.H;
-    if (frame_start) n = std::max(n, 3u * st->inst.ntiles_items + st->inst.ntiles_words);
-    const uint32_t want = (n + kThreads - 1u) / kThreads;
-    return static_cast<int>(std::max(1u, std::min<uint32_t>(want, static_cast<uint32_t>(st->sms) * 4u)));
 }
 
 int check_launch() { return cudaGetLastError() == cudaSuccess ? CBT_OK : CBT_ECUDA; }
@@ -98,6 +112,7 @@ bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
     if (f->fixed_shift < 0 || f->fixed_shift > 62) return false;
     if (f->mode == CBT_MODE_LIST && ((f->n_split && !f->split_list) || (f->n_merge && !f->merge_list)))
         return false;
+    if (f->vertices_out && f->vertices_cap == 0) return false;
     std::memset(&fp, 0, sizeof(fp));
     for (int c = 0; c < 3; ++c) fp.eye[c] = f->eye[c];
     for (int p = 0; p < 5; ++p)
@@ -114,8 +129,282 @@ bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
     fp.merge_list = f->merge_list;
     fp.n_merge = f->n_merge;
     fp.frame = frame;
-    if (f->vertices_out && f->vertices_cap == 0) return false;
+    fp.vout = f->vertices_out;
+    fp.vcap = f->vertices_cap;
     return true;
+}
+
+}  // namespace
+
+// Host side of a batch (also the batch of one inside every state).
+struct cbt_batch {
+    std::vector<cbt_state*> st;
+    uint32_t n = 0;
+    int sms = 1;
+    char* region = nullptr;
+    BatchLayout L{};
+    BatchDev dev{};
+    std::vector<uint32_t> cap, W, H;
+    FrameP* h_fps = nullptr;  // pinned staging for the per-instance frame parameters
+    cudaEvent_t staged = nullptr;
+    bool staged_pending = false;
+    uint32_t tw = 256;
+    uint32_t grid_mult = 8;
+    bool use_graph = false;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t exec_tw = 0, exec_mult = 0;
+    bool exec_vertices = false;
+    bool timing = false;
+    cudaEvent_t ev[kNumKernels + 1] = {};
+    uint32_t timed = 0, launches = 0;
+    // online autotuner over (tile words, blocks per SM)
+    bool tuning = false;
+    uint32_t tune_k = 0, tune_rounds = 0;
+    std::vector<float> tune_ms;
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+    bool tune_pending = false;
+    uint32_t tune_cfg = 0;
+};
+
+struct cbt_state {
+    Inst inst;
+    void* workspace;
+    size_t bytes;
+    int sms;
+    uint32_t frame;
+    cbt_batch* self;
+};
+
+namespace {
+
+const uint32_t kTuneTw[3] = {64, 128, 256};
+const uint32_t kTuneMult[3] = {4, 8, 16};
+
+int upload_static_prefixes(cbt_batch* B, cudaStream_t s) {
+    std::vector<uint32_t> w(B->n + 1), v(B->n + 1), r(B->n + 1);
+    w[0] = v[0] = r[0] = 0;
+    for (uint32_t b = 0; b < B->n; ++b) {
+        w[b + 1] = w[b] + word_tiles(B->W[b], B->tw);
+        v[b + 1] = v[b] + item_tiles(B->cap[b]);
+        r[b + 1] = r[b] + 9u * B->H[b];
+    }
+    B->dev.Twords = w[B->n];
+    B->dev.Titems = v[B->n];
+    B->dev.Trel = r[B->n];
+    B->dev.tw = B->tw;
+    const size_t bytes = 4u * (B->n + 1u);
+    if (cudaMemcpyAsync(const_cast<uint32_t*>(B->dev.wtile_base), w.data(), bytes, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(const_cast<uint32_t*>(B->dev.vtile_base), v.data(), bytes, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(const_cast<uint32_t*>(B->dev.rel_base), r.data(), bytes, cudaMemcpyHostToDevice, s))
+        return CBT_ECUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
+}
+
+// Builds a batch over `n` states in `region` (L.total bytes of device memory).
+int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t s, cbt_batch** out) {
+    cbt_batch* B = new cbt_batch();
+    B->n = n;
+    B->st.assign(states, states + n);
+    B->sms = states[0]->sms;
+    for (uint32_t b = 0; b < n; ++b) {
+        B->cap.push_back(states[b]->inst.cap);
+        B->W.push_back(states[b]->inst.W);
+        B->H.push_back(states[b]->inst.H);
+    }
+    B->L = batch_layout(n, B->cap.data(), B->W.data(), B->H.data());
+    B->region = region;
+    BatchDev& d = B->dev;
+    d.inst = reinterpret_cast<const Inst*>(region + B->L.inst);
+    d.fps = nullptr;
+    d.B = n;
+    d.tile_base = reinterpret_cast<uint32_t*>(region + B->L.tile_base);
+    d.wtile_base = reinterpret_cast<const uint32_t*>(region + B->L.wtile_base);
+    d.vtile_base = reinterpret_cast<const uint32_t*>(region + B->L.vtile_base);
+    d.rel_base = reinterpret_cast<const uint32_t*>(region + B->L.rel_base);
+    d.bg = reinterpret_cast<BatchGlobals*>(region + B->L.bg);
+    d.status = reinterpret_cast<unsigned long long*>(region + B->L.status);
+    std::vector<Inst> insts(n);
+    for (uint32_t b = 0; b < n; ++b) insts[b] = states[b]->inst;
+    int rc = CBT_OK;
+    if (cudaMemcpyAsync(region + B->L.inst, insts.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, s) ||
+        cudaMemsetAsync(d.bg, 0, sizeof(BatchGlobals), s) ||
+        cudaMallocHost(reinterpret_cast<void**>(&B->h_fps), sizeof(FrameP) * n) ||
+        cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming))
+        rc = CBT_ECUDA;
+    if (!rc) rc = upload_static_prefixes(B, s);
+    if (rc) {
+        if (B->h_fps) cudaFreeHost(B->h_fps);
+        delete B;
+        return rc;
+    }
+    *out = B;
+    return CBT_OK;
+}
+
+void batch_free(cbt_batch* B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->timing)
+        for (auto& e : B->ev) cudaEventDestroy(e);
+    for (auto& e : B->tune_ev)
+        if (e) cudaEventDestroy(e);
+    if (B->staged) cudaEventDestroy(B->staged);
+    if (B->h_fps) cudaFreeHost(B->h_fps);
+    delete B;
+}
+
+int grid_prep(const cbt_batch* B) {
+    const uint32_t n = std::max(B->dev.Trel, 2u * B->dev.Titems + B->dev.Twords);
+    const uint32_t want = (n + kThreads - 1u) / kThreads;
+    return static_cast<int>(std::max(1u, std::min<uint32_t>(want, static_cast<uint32_t>(B->sms) * 4u)));
+}
+
+// The kernels of one frame of a batch descriptor; ev (optional) receives an
+// event before and after every kernel. Returns the number of launches.
+uint32_t enqueue_kernels(const BatchDev& bt, int sms, uint32_t grid_mult, bool vertices, cudaStream_t s,
+                         cudaEvent_t* ev) {
+    const uint32_t prep_n = std::max(bt.Trel, 2u * bt.Titems + bt.Twords);
+    const int prep = static_cast<int>(std::max(1u, std::min<uint32_t>((prep_n + kThreads - 1u) / kThreads,
+                                                                     static_cast<uint32_t>(sms) * 4u)));
+    const int items = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * grid_mult)));
+    const int scans = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * 2u)));
+    const int words = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Twords, static_cast<uint32_t>(sms) * 4u)));
+    uint32_t k = 0;
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(ev[k], s);
+        ++k;
+    };
+    mark();
+    launch_prep(bt, true, prep, s);
+    mark();
+    launch_classify(bt, items, s);
+    mark();
+    launch_gate(bt, scans, s);
+    mark();
+    launch_scatter(bt, items, s);
+    mark();
+    launch_alloc(bt, scans, s);
+    mark();
+    launch_free(bt, words, s);
+    mark();
+    launch_fill(bt, items, s);
+    mark();
+    launch_cbt(bt, words, s);
+    mark();
+    if (vertices) {
+        launch_vertices(bt, items, s);
+        mark();
+    }
+    return k - 1u;
+}
+
+// The kernels of one frame. `timed`: record events between the kernels.
+void enqueue_frame(cbt_batch* B, cudaStream_t s, bool vertices, bool timed) {
+    B->launches = enqueue_kernels(B->dev, B->sms, B->grid_mult, vertices, s, timed ? B->ev : nullptr);
+    B->timed = timed ? B->launches : 0u;
+}
+
+int apply_config(cbt_batch* B, uint32_t tw, uint32_t mult, cudaStream_t s) {
+    B->grid_mult = mult;
+    if (tw == B->tw) return CBT_OK;
+    B->tw = tw;
+    return upload_static_prefixes(B, s);
+}
+
+int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
+    const uint32_t n = B->n;
+    std::vector<FrameP> fps(n);
+    bool vertices = false;
+    for (uint32_t b = 0; b < n; ++b) {
+        if (!frame_from_api(frames + b, B->st[b]->frame, fps[b])) return CBT_EINVAL;
+        vertices = vertices || fps[b].vout != nullptr;
+    }
+    // online autotuner: one candidate configuration per frame, round robin,
+    // then the fastest by median frame time (results do not depend on it)
+    if (B->tuning) {
+        if (B->tune_pending) {
+            float ms = 0.0f;
+            cudaEventSynchronize(B->tune_ev[1]);
+            cudaEventElapsedTime(&ms, B->tune_ev[0], B->tune_ev[1]);
+            B->tune_ms.push_back(ms);
+            B->tune_pending = false;
+        }
+        const uint32_t ncfg = 9;
+        if (B->tune_ms.size() >= ncfg * B->tune_rounds) {
+            uint32_t best = 0;
+            float best_ms = 1e30f;
+            for (uint32_t c = 0; c < ncfg; ++c) {
+                std::vector<float> v;
+                for (size_t k = c; k < B->tune_ms.size(); k += ncfg) v.push_back(B->tune_ms[k]);
+                std::sort(v.begin(), v.end());
+                const float med = v[v.size() / 2];
+                if (med < best_ms) {
+                    best_ms = med;
+                    best = c;
+                }
+            }
+            B->tuning = false;
+            B->tune_cfg = best;
+            int rc = apply_config(B, kTuneTw[best / 3], kTuneMult[best % 3], s);
+            if (rc) return rc;
+        } else {
+            const uint32_t c = static_cast<uint32_t>(B->tune_ms.size()) % ncfg;
+            int rc = apply_config(B, kTuneTw[c / 3], kTuneMult[c % 3], s);
+            if (rc) return rc;
+        }
+    }
+    const bool tune_now = B->tuning;
+    if (tune_now) cudaEventRecord(B->tune_ev[0], s);
+    if (B->use_graph) {
+        // the graph copies the frame parameters from pinned staging
+        if (B->staged_pending) cudaEventSynchronize(B->staged);
+        std::memcpy(B->h_fps, fps.data(), sizeof(FrameP) * n);
+        if (!B->exec || B->exec_tw != B->tw || B->exec_mult != B->grid_mult || B->exec_vertices != vertices) {
+            if (B->exec) {
+                cudaGraphExecDestroy(B->exec);
+                B->exec = nullptr;
+            }
+            cudaStream_t cs;
+            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) return CBT_ECUDA;
+            cudaGraph_t g = nullptr;
+            B->dev.fps = reinterpret_cast<const FrameP*>(B->region + B->L.fps);
+            cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            cudaMemcpyAsync(B->region + B->L.fps, B->h_fps, sizeof(FrameP) * n, cudaMemcpyHostToDevice, cs);
+            enqueue_frame(B, cs, vertices, false);
+            const cudaError_t e1 = cudaStreamEndCapture(cs, &g);
+            cudaStreamDestroy(cs);
+            if (e1 != cudaSuccess || !g) return CBT_ECUDA;
+            const cudaError_t e2 = cudaGraphInstantiate(&B->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e2 != cudaSuccess) return CBT_ECUDA;
+            B->exec_tw = B->tw;
+            B->exec_mult = B->grid_mult;
+            B->exec_vertices = vertices;
+        }
+        if (cudaGraphLaunch(B->exec, s) != cudaSuccess) return CBT_ECUDA;
+        cudaEventRecord(B->staged, s);
+        B->staged_pending = true;
+        B->timed = 0;
+    } else if (n == 1) {
+        B->dev.fps = nullptr;
+        B->dev.fp0 = fps[0];
+        enqueue_frame(B, s, vertices, B->timing);
+    } else {
+        if (B->staged_pending) cudaEventSynchronize(B->staged);
+        std::memcpy(B->h_fps, fps.data(), sizeof(FrameP) * n);
+        if (cudaMemcpyAsync(B->region + B->L.fps, B->h_fps, sizeof(FrameP) * n, cudaMemcpyHostToDevice, s))
+            return CBT_ECUDA;
+        cudaEventRecord(B->staged, s);
+        B->staged_pending = true;
+        B->dev.fps = reinterpret_cast<const FrameP*>(B->region + B->L.fps);
+        enqueue_frame(B, s, vertices, B->timing);
+    }
+    if (tune_now) {
+        cudaEventRecord(B->tune_ev[1], s);
+        B->tune_pending = true;
+    }
+    for (uint32_t b = 0; b < n; ++b) B->st[b]->frame += 1u;
+    return check_launch();
 }
 
 }  // namespace
@@ -144,12 +433,14 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     cbt_state* st = new cbt_state();
     st->workspace = workspace;
     st->bytes = bytes;
+    st->frame = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&st->sms, cudaDevAttrMultiProcessorCount, dev);
     if (st->sms <= 0) st->sms = 1;
     char* b = static_cast<char*>(workspace);
     Inst& I = st->inst;
+    std::memset(&I, 0, sizeof(I));
     I.g = reinterpret_cast<Globals*>(b + L.globals);
     I.heap = reinterpret_cast<uint64_t*>(b + L.heap);
     I.nb = reinterpret_cast<uint4*>(b + L.nb);
@@ -159,7 +450,7 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     I.live = reinterpret_cast<uint32_t*>(b + L.live);
     I.freel = reinterpret_cast<uint32_t*>(b + L.freel);
     I.scan = reinterpret_cast<uint32_t*>(b + L.scan);
-    I.status = reinterpret_cast<unsigned long long*>(b + L.status);
+    I.grp = reinterpret_cast<uint4*>(b + L.grp);
     I.root64 = reinterpret_cast<double*>(b + L.root64);
     I.rel = b + L.rel;
     I.cap = L.cap;
@@ -168,36 +459,47 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     I.H = static_cast<uint32_t>(H);
     I.ch = ch;
     I.max_depth = static_cast<uint32_t>(max_depth);
-    I.ntiles_items = L.ntiles_items;
-    I.ntiles_words = L.ntiles_words;
-    I.tile_words = L.tile_words;
+    I.ntiles_items = item_tiles(L.cap);
 
     // Stage the halfedge operators and the position of Vert(h) per halfedge
     // in the (not yet used) relative-vertex region.
     const size_t h = static_cast<size_t>(H);
-    std::vector<int32_t> ints(4u * h);
+    std::vector<int32_t> ints(3u * h);
     std::vector<double> hpos(3u * h);
     for (size_t k = 0; k < h; ++k) {
         ints[k] = twin[k];
         ints[h + k] = next[k];
         ints[2u * h + k] = prev[k];
-        ints[3u * h + k] = face[k];
         for (int c = 0; c < 3; ++c) hpos[3u * k + c] = pos[3u * static_cast<size_t>(vert[k]) + c];
     }
     int32_t* d_ints = reinterpret_cast<int32_t*>(b + L.rel);
-    double* d_hpos = reinterpret_cast<double*>(b + L.rel + 16u * h);
+    double* d_hpos = reinterpret_cast<double*>(b + L.rel + align256(12u * h));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaMemsetAsync(I.g, 0, sizeof(Globals), s);
-    cudaMemsetAsync(I.status, 0, 8u * (3u * static_cast<size_t>(L.ntiles_items) + L.ntiles_words), s);
-    cudaMemcpyAsync(d_ints, ints.data(), 16u * h, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_ints, ints.data(), 12u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_hpos, hpos.data(), 24u * h, cudaMemcpyHostToDevice, s);
     const int grid = static_cast<int>(std::min<uint32_t>((std::max(L.W, static_cast<uint32_t>(H)) + 255u) / 256u,
                                                          static_cast<uint32_t>(st->sms) * 4u));
-    launch_init(I, d_ints, d_ints + h, d_ints + 2u * h, d_ints + 3u * h, d_hpos, std::max(1, grid), s);
-    launch_cbt(I, grid_words(st), s);
+    launch_init(I, d_ints, d_ints + h, d_ints + 2u * h, d_hpos, std::max(1, grid), s);
     rc = check_launch();
-    if (rc == CBT_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = CBT_ECUDA;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = CBT_ECUDA;
+    if (!rc) {
+        cbt_state* self[1] = {st};
+        rc = batch_build(self, 1, b + L.batch, s, &st->self);
+    }
+    if (!rc) {
+        // the reduction and live list of the roots
+        cbt_batch* B = st->self;
+        cudaMemsetAsync(B->dev.status, 0, 8u * (2u * static_cast<size_t>(B->dev.Titems) + B->dev.Twords), s);
+        cudaMemsetAsync(B->dev.bg, 0, sizeof(BatchGlobals), s);
+        B->dev.fps = nullptr;
+        std::memset(&B->dev.fp0, 0, sizeof(FrameP));
+        launch_cbt(B->dev, std::max(1, static_cast<int>(std::min<uint32_t>(B->dev.Twords, static_cast<uint32_t>(st->sms) * 4u))), s);
+        rc = check_launch();
+        if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = CBT_ECUDA;
+    }
     if (rc) {
+        batch_free(st->self);
         delete st;
         return rc;
     }
@@ -206,41 +508,8 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
 }
 
 extern "C" int cbt_update(cbt_state* st, const cbt_frame* frame, cbt_stream_t stream) {
-    if (!st) return CBT_EINVAL;
-    FrameP fp;
-    if (!frame_from_api(frame, st->frame, fp)) return CBT_EINVAL;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const Inst& I = st->inst;
-    uint32_t k = 0;
-    auto mark = [&]() {
-        if (st->timing) cudaEventRecord(st->ev[k], s);
-        ++k;
-    };
-    mark();
-    launch_prep(I, fp, true, grid_prep(st, true), s);
-    mark();
-    launch_classify(I, fp, grid_items(st), s);
-    mark();
-    launch_gate(I, fp, grid_tiles(st), s);
-    mark();
-    launch_scatter(I, grid_items(st), s);
-    mark();
-    launch_alloc(I, grid_tiles(st), s);
-    mark();
-    launch_free(I, grid_words(st), s);
-    mark();
-    launch_fill(I, grid_items(st), s);
-    mark();
-    launch_cbt(I, grid_words(st), s);
-    mark();
-    if (frame->vertices_out) {
-        launch_vertices(I, fp, frame->vertices_out, frame->vertices_cap, grid_items(st), s);
-        mark();
-    }
-    st->launches = k - 1u;
-    st->timed = st->timing ? k - 1u : 0u;
-    st->frame += 1u;
-    return check_launch();
+    if (!st || !frame) return CBT_EINVAL;
+    return batch_update(st->self, frame, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int cbt_live_count(cbt_state* st, uint32_t* h_count, cbt_stream_t stream) {
@@ -259,7 +528,8 @@ extern "C" int cbt_leaves(cbt_state* st, uint32_t* d_slots, uint64_t* d_heap, ui
     if (h_count) *h_count = n;
     if (n > cap) return CBT_ENOMEM;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    launch_leaves(st->inst, d_slots, d_heap, d_links, grid_items(st), s);
+    const int grid = static_cast<int>(std::max(1u, std::min<uint32_t>((n + 255u) / 256u, static_cast<uint32_t>(st->sms) * 8u)));
+    launch_leaves(st->inst, d_slots, d_heap, d_links, grid, s);
     rc = check_launch();
     if (rc) return rc;
     return cudaStreamSynchronize(s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
@@ -274,14 +544,20 @@ extern "C" int cbt_vertices(cbt_state* st, float* d_out, const double h_origin[3
     if (rc) return rc;
     if (h_count) *h_count = n;
     if (n > cap) return CBT_ENOMEM;
+    cbt_batch* B = st->self;
     FrameP fp;
     std::memset(&fp, 0, sizeof(fp));
     for (int c = 0; c < 3; ++c) fp.eye[c] = h_origin[c];
     fp.precision = precision;
     fp.shift = fixed_shift;
+    fp.vout = d_out;
+    fp.vcap = cap;
+    BatchDev bt = B->dev;
+    bt.fps = nullptr;
+    bt.fp0 = fp;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    launch_prep(st->inst, fp, false, grid_prep(st, false), s);
-    launch_vertices(st->inst, fp, d_out, cap, grid_items(st), s);
+    launch_prep(bt, false, grid_prep(B), s);
+    launch_vertices(bt, std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(st->sms) * 8u))), s);
     rc = check_launch();
     if (rc) return rc;
     return cudaStreamSynchronize(s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
@@ -325,36 +601,338 @@ extern "C" int cbt_stats(cbt_state* st, cbt_frame_stats* out, cbt_stream_t strea
 
 extern "C" void cbt_destroy(cbt_state* st) {
     if (!st) return;
-    if (st->timing)
-        for (auto& e : st->ev) cudaEventDestroy(e);
+    batch_free(st->self);
     delete st;
 }
 
-extern "C" int cbt_set_timing(cbt_state* st, int on) {
-    if (!st) return CBT_EINVAL;
-    if (on && !st->timing) {
-        for (auto& e : st->ev)
+extern "C" uint32_t cbt_last_launch_count(const cbt_state* st) { return st ? st->self->launches : 0u; }
+
+namespace {
+int set_timing(cbt_batch* B, int on) {
+    if (on && !B->timing) {
+        for (auto& e : B->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return CBT_ECUDA;
-        st->timing = true;
-    } else if (!on && st->timing) {
-        for (auto& e : st->ev) cudaEventDestroy(e);
-        st->timing = false;
-        st->timed = 0;
+        B->timing = true;
+    } else if (!on && B->timing) {
+        for (auto& e : B->ev) cudaEventDestroy(e);
+        B->timing = false;
+        B->timed = 0;
     }
     return CBT_OK;
 }
-
-extern "C" uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n) {
-    if (!st || !st->timing || st->timed == 0 || !ms) return 0u;
-    if (cudaEventSynchronize(st->ev[st->timed]) != cudaSuccess) return 0u;
-    const uint32_t m = std::min(n, st->timed);
+uint32_t kernel_times(cbt_batch* B, float* ms, uint32_t n) {
+    if (!B->timing || B->timed == 0 || !ms) return 0u;
+    if (cudaEventSynchronize(B->ev[B->timed]) != cudaSuccess) return 0u;
+    const uint32_t m = std::min(n, B->timed);
     for (uint32_t k = 0; k < m; ++k) {
         ms[k] = 0.0f;
-        cudaEventElapsedTime(&ms[k], st->ev[k], st->ev[k + 1]);
+        cudaEventElapsedTime(&ms[k], B->ev[k], B->ev[k + 1]);
     }
     return m;
 }
+}  // namespace
 
-extern "C" const char* cbt_kernel_name(uint32_t k) { return k < kMaxKernels ? kKernelNames[k] : ""; }
+extern "C" int cbt_set_timing(cbt_state* st, int on) { return st ? set_timing(st->self, on) : CBT_EINVAL; }
 
-extern "C" uint32_t cbt_last_launch_count(const cbt_state* st) { return st ? st->launches : 0u; }
+extern "C" uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n) {
+    return st ? kernel_times(st->self, ms, n) : 0u;
+}
+
+extern "C" const char* cbt_kernel_name(uint32_t k) { return k < kNumKernels ? kKernelNames[k] : ""; }
+
+extern "C" int cbt_set_graph(cbt_state* st, int on) {
+    if (!st) return CBT_EINVAL;
+    st->self->use_graph = on != 0;
+    return CBT_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+extern "C" size_t cbt_batch_workspace_bytes(cbt_state* const* states, int32_t n) {
+    if (!states || n < 1) return 0u;
+    std::vector<uint32_t> cap(n), W(n), H(n);
+    for (int32_t b = 0; b < n; ++b) {
+        if (!states[b]) return 0u;
+        cap[b] = states[b]->inst.cap;
+        W[b] = states[b]->inst.W;
+        H[b] = states[b]->inst.H;
+    }
+    return batch_layout(static_cast<uint32_t>(n), cap.data(), W.data(), H.data()).total;
+}
+
+extern "C" int cbt_batch_create(cbt_state* const* states, int32_t n, void* workspace, size_t bytes,
+                                cbt_stream_t stream, cbt_batch** out) {
+    if (!out || !states || n < 1 || !workspace) return CBT_EINVAL;
+    *out = nullptr;
+    for (int32_t b = 0; b < n; ++b) {
+        if (!states[b]) return CBT_EINVAL;
+        for (int32_t c = 0; c < b; ++c)
+            if (states[c] == states[b]) return CBT_EINVAL;
+    }
+    if (bytes < cbt_batch_workspace_bytes(states, n) || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return CBT_ENOMEM;
+    return batch_build(states, static_cast<uint32_t>(n), static_cast<char*>(workspace),
+                       reinterpret_cast<cudaStream_t>(stream), out);
+}
+
+extern "C" int cbt_batch_update(cbt_batch* b, const cbt_frame* frames, cbt_stream_t stream) {
+    if (!b || !frames) return CBT_EINVAL;
+    return batch_update(b, frames, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cbt_batch_set_graph(cbt_batch* b, int on) {
+    if (!b) return CBT_EINVAL;
+    b->use_graph = on != 0;
+    return CBT_OK;
+}
+
+extern "C" int cbt_batch_autotune(cbt_batch* b, uint32_t rounds) {
+    if (!b || rounds == 0) return CBT_EINVAL;
+    for (auto& e : b->tune_ev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) return CBT_ECUDA;
+    b->tuning = true;
+    b->tune_rounds = rounds;
+    b->tune_ms.clear();
+    b->tune_pending = false;
+    return CBT_OK;
+}
+
+extern "C" int cbt_batch_config(const cbt_batch* b, uint32_t* tile_words, uint32_t* blocks_per_sm,
+                                int* tuning) {
+    if (!b) return CBT_EINVAL;
+    if (tile_words) *tile_words = b->tw;
+    if (blocks_per_sm) *blocks_per_sm = b->grid_mult;
+    if (tuning) *tuning = b->tuning ? 1 : 0;
+    return CBT_OK;
+}
+
+extern "C" int cbt_batch_set_config(cbt_batch* b, uint32_t tile_words, uint32_t blocks_per_sm,
+                                    cbt_stream_t stream) {
+    if (!b || (tile_words != 64 && tile_words != 128 && tile_words != 256) || blocks_per_sm < 1 ||
+        blocks_per_sm > 64)
+        return CBT_EINVAL;
+    return apply_config(b, tile_words, blocks_per_sm, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cbt_batch_set_timing(cbt_batch* b, int on) { return b ? set_timing(b, on) : CBT_EINVAL; }
+
+extern "C" uint32_t cbt_batch_kernel_times(cbt_batch* b, float* ms, uint32_t n) {
+    return b ? kernel_times(b, ms, n) : 0u;
+}
+
+extern "C" uint32_t cbt_batch_last_launch_count(const cbt_batch* b) { return b ? b->launches : 0u; }
+
+extern "C" void cbt_batch_destroy(cbt_batch* b) { batch_free(b); }
+
+// ------------------------------------------------------------------ server
+
+namespace {
+
+// One in-flight tick: a device region holding the tick's packed instance
+// table, frame parameters and prefixes, the launch counters, the tile
+// prefix, live-count output and look-back descriptors; its pinned host twin.
+struct ServerSlot {
+    char* dev = nullptr;
+    char* host = nullptr;  // pinned: packed tick block, then live counts
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<int32_t> idx;
+};
+
+struct TickLayout {
+    size_t inst, fps, wbase, vbase, rbase, block;  // packed block (copied per tick)
+    size_t bg, tile_base, nout, status, total;      // rest of the device region
+};
+
+TickLayout tick_layout(uint32_t k, uint32_t n_max, uint32_t status_words) {
+    TickLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.inst = take(sizeof(Inst) * k);
+    L.fps = take(sizeof(FrameP) * k);
+    L.wbase = take(4u * (k + 1u));
+    L.vbase = take(4u * (k + 1u));
+    L.rbase = take(4u * (k + 1u));
+    L.block = off;
+    // the fixed part is laid out for the largest tick so that its offsets
+    // do not move between ticks
+    size_t moff = 0;
+    auto mtake = [&](size_t bytes) {
+        const size_t o = moff;
+        moff = align256(moff + bytes);
+        return o;
+    };
+    mtake(sizeof(Inst) * n_max);
+    mtake(sizeof(FrameP) * n_max);
+    mtake(4u * (n_max + 1u));
+    mtake(4u * (n_max + 1u));
+    mtake(4u * (n_max + 1u));
+    L.bg = mtake(sizeof(BatchGlobals));
+    L.tile_base = mtake(4u * (n_max + 1u));
+    L.nout = mtake(4u * n_max);
+    L.status = mtake(8u * static_cast<size_t>(status_words));
+    L.total = moff;
+    return L;
+}
+
+}  // namespace
+
+struct cbt_server {
+    std::vector<cbt_state*> st;
+    std::vector<int32_t> inflight;  // slot of each instance's pending tick, or -1
+    uint32_t n = 0;
+    int sms = 1;
+    uint32_t status_words = 0;
+    size_t slot_bytes = 0;
+    uint32_t tw = 256, grid_mult = 8;
+    std::vector<ServerSlot> slots;
+    uint32_t next = 0;
+};
+
+extern "C" size_t cbt_server_workspace_bytes(cbt_state* const* states, int32_t n, int32_t inflight) {
+    if (!states || n < 1 || inflight < 1 || inflight > 16) return 0u;
+    uint64_t titems = 0, twords = 0;
+    for (int32_t b = 0; b < n; ++b) {
+        if (!states[b]) return 0u;
+        titems += item_tiles(states[b]->inst.cap);
+        twords += word_tiles(states[b]->inst.W, kMinTileWords);
+    }
+    const TickLayout L = tick_layout(static_cast<uint32_t>(n), static_cast<uint32_t>(n),
+                                     static_cast<uint32_t>(2u * titems + twords));
+    return L.total * static_cast<size_t>(inflight);
+}
+
+extern "C" int cbt_server_create(cbt_state* const* states, int32_t n, int32_t inflight, void* workspace,
+                                 size_t bytes, cbt_server** out) {
+    if (!out || !states || n < 1 || inflight < 1 || inflight > 16 || !workspace) return CBT_EINVAL;
+    *out = nullptr;
+    const size_t need = cbt_server_workspace_bytes(states, n, inflight);
+    if (need == 0u) return CBT_EINVAL;
+    if (bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return CBT_ENOMEM;
+    cbt_server* sv = new cbt_server();
+    sv->st.assign(states, states + n);
+    sv->inflight.assign(static_cast<size_t>(n), -1);
+    sv->n = static_cast<uint32_t>(n);
+    sv->sms = states[0]->sms;
+    uint64_t titems = 0, twords = 0;
+    for (int32_t b = 0; b < n; ++b) {
+        titems += item_tiles(states[b]->inst.cap);
+        twords += word_tiles(states[b]->inst.W, kMinTileWords);
+    }
+    sv->status_words = static_cast<uint32_t>(2u * titems + twords);
+    const TickLayout L = tick_layout(sv->n, sv->n, sv->status_words);
+    sv->slot_bytes = L.total;
+    sv->slots.resize(static_cast<size_t>(inflight));
+    int rc = CBT_OK;
+    for (int32_t r = 0; r < inflight && !rc; ++r) {
+        ServerSlot& S = sv->slots[r];
+        S.dev = static_cast<char*>(workspace) + L.total * static_cast<size_t>(r);
+        if (cudaMallocHost(reinterpret_cast<void**>(&S.host), L.block + 4u * sv->n) != cudaSuccess ||
+            cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess)
+            rc = CBT_ECUDA;
+    }
+    if (rc) {
+        for (auto& S : sv->slots) {
+            if (S.host) cudaFreeHost(S.host);
+            if (S.done) cudaEventDestroy(S.done);
+        }
+        delete sv;
+        return rc;
+    }
+    *out = sv;
+    return CBT_OK;
+}
+
+extern "C" int cbt_server_submit(cbt_server* sv, const int32_t* idx, const cbt_frame* frames, int32_t k,
+                                 cbt_stream_t stream, int32_t* ticket) {
+    if (!sv || !idx || !frames || k < 1 || static_cast<uint32_t>(k) > sv->n || !ticket) return CBT_EINVAL;
+    for (int32_t i = 0; i < k; ++i) {
+        if (idx[i] < 0 || static_cast<uint32_t>(idx[i]) >= sv->n) return CBT_EINVAL;
+        if (sv->inflight[idx[i]] >= 0) return CBT_EINVAL;  // one pending tick per instance
+        for (int32_t j = 0; j < i; ++j)
+            if (idx[j] == idx[i]) return CBT_EINVAL;
+    }
+    const uint32_t r = sv->next;
+    ServerSlot& S = sv->slots[r];
+    if (S.busy) return CBT_EINVAL;  // poll the slot's previous ticket first
+    const uint32_t kk = static_cast<uint32_t>(k);
+    const TickLayout L = tick_layout(kk, sv->n, sv->status_words);
+    Inst* hi = reinterpret_cast<Inst*>(S.host + L.inst);
+    FrameP* hf = reinterpret_cast<FrameP*>(S.host + L.fps);
+    uint32_t* hw = reinterpret_cast<uint32_t*>(S.host + L.wbase);
+    uint32_t* hv = reinterpret_cast<uint32_t*>(S.host + L.vbase);
+    uint32_t* hr = reinterpret_cast<uint32_t*>(S.host + L.rbase);
+    hw[0] = hv[0] = hr[0] = 0;
+    bool vertices = false;
+    for (uint32_t i = 0; i < kk; ++i) {
+        cbt_state* st = sv->st[idx[i]];
+        hi[i] = st->inst;
+        if (!frame_from_api(frames + i, st->frame, hf[i])) return CBT_EINVAL;
+        vertices = vertices || hf[i].vout != nullptr;
+        hw[i + 1] = hw[i] + word_tiles(st->inst.W, sv->tw);
+        hv[i + 1] = hv[i] + item_tiles(st->inst.cap);
+        hr[i + 1] = hr[i] + 9u * st->inst.H;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(S.dev, S.host, L.block, cudaMemcpyHostToDevice, s) != cudaSuccess) return CBT_ECUDA;
+    BatchDev bt{};
+    bt.inst = reinterpret_cast<const Inst*>(S.dev + L.inst);
+    bt.fps = reinterpret_cast<const FrameP*>(S.dev + L.fps);
+    bt.B = kk;
+    bt.tw = sv->tw;
+    bt.tile_base = reinterpret_cast<uint32_t*>(S.dev + L.tile_base);
+    bt.wtile_base = reinterpret_cast<const uint32_t*>(S.dev + L.wbase);
+    bt.vtile_base = reinterpret_cast<const uint32_t*>(S.dev + L.vbase);
+    bt.rel_base = reinterpret_cast<const uint32_t*>(S.dev + L.rbase);
+    bt.bg = reinterpret_cast<BatchGlobals*>(S.dev + L.bg);
+    bt.status = reinterpret_cast<unsigned long long*>(S.dev + L.status);
+    bt.Titems = hv[kk];
+    bt.Twords = hw[kk];
+    bt.Trel = hr[kk];
+    bt.nout = reinterpret_cast<uint32_t*>(S.dev + L.nout);
+    enqueue_kernels(bt, sv->sms, sv->grid_mult, vertices, s, nullptr);
+    cudaMemcpyAsync(S.host + L.block, bt.nout, 4u * kk, cudaMemcpyDeviceToHost, s);
+    if (cudaEventRecord(S.done, s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return CBT_ECUDA;
+    S.busy = true;
+    S.idx.assign(idx, idx + k);
+    for (uint32_t i = 0; i < kk; ++i) {
+        sv->inflight[idx[i]] = static_cast<int32_t>(r);
+        sv->st[idx[i]]->frame += 1u;
+    }
+    sv->next = (r + 1u) % static_cast<uint32_t>(sv->slots.size());
+    *ticket = static_cast<int32_t>(r);
+    return CBT_OK;
+}
+
+extern "C" int cbt_server_poll(cbt_server* sv, int32_t ticket, int wait, uint32_t* live_before) {
+    if (!sv || ticket < 0 || static_cast<size_t>(ticket) >= sv->slots.size()) return -CBT_EINVAL;
+    ServerSlot& S = sv->slots[ticket];
+    if (!S.busy) return -CBT_EINVAL;
+    const cudaError_t e = wait ? cudaEventSynchronize(S.done) : cudaEventQuery(S.done);
+    if (e == cudaErrorNotReady) return 0;
+    if (e != cudaSuccess) return -CBT_ECUDA;
+    const TickLayout L = tick_layout(static_cast<uint32_t>(S.idx.size()), sv->n, sv->status_words);
+    if (live_before) std::memcpy(live_before, S.host + L.block, 4u * S.idx.size());
+    for (int32_t b : S.idx) sv->inflight[b] = -1;
+    S.idx.clear();
+    S.busy = false;
+    return 1;
+}
+
+extern "C" int32_t cbt_server_next_slot_free(const cbt_server* sv) {
+    return sv && !sv->slots[sv->next].busy ? 1 : 0;
+}
+
+extern "C" void cbt_server_destroy(cbt_server* sv) {
+    if (!sv) return;
+    for (auto& S : sv->slots) {
+        if (S.busy) cudaEventSynchronize(S.done);
+        if (S.host) cudaFreeHost(S.host);
+        if (S.done) cudaEventDestroy(S.done);
+    }
+    delete sv;
+}

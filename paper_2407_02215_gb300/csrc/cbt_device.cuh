@@ -13,9 +13,13 @@
 //   live[cap]  u32   slots of the live bisectors, ascending (Alg. 7 for all i)
 //   freel[cap] u32   the first A zero bits of the frame-start bitfield (Alg. 8)
 //   scan[cap]  u32   per live index: split cost, then its running total
-//   status[]   u64   look-back tile descriptors of the three scans
+//   grp[cap]   uint4 per live index: the members of the merge group whose
+//                    smallest member it is (written by the gate)
 //   root64[H*9], rel[H*9]: root vertices (FP64) and their per-frame offsets
 //                    from the camera (FP32, fixed point or FP64)
+// and, per batch (a single instance carries a batch of one), the instance
+// table, per-instance frame parameters, tile prefixes and the look-back
+// tile descriptors of the two scans and the reduction.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -33,6 +37,7 @@ constexpr uint32_t kMergeWish = 1u << 5;
 constexpr uint32_t kMergeGrant = 1u << 6;
 constexpr uint32_t kDepthOdd = 1u << 7;
 constexpr uint32_t kHeapOdd = 1u << 8;
+constexpr uint32_t kCand = 1u << 9;  // smallest member of a mergeable group (members in grp[i])
 
 // Edge indices of a bisector: Twin (v0,v1), Next (v1,v2), Prev (v2,v0).
 constexpr int kT = 0, kNe = 1, kPe = 2;
@@ -51,19 +56,22 @@ enum StatIdx {
     kStAllocated, kStRelinked, kStFrame, kStCount
 };
 
+// Per-instance counters (256 bytes at the start of the instance workspace).
 struct Globals {
     uint32_t N;         // live bisectors at frame start (CBT root)
     uint32_t F;         // free slots at frame start
     uint32_t A;         // allocations of this frame
     uint32_t Mg;        // granted merge cost of this frame
     uint32_t err;       // sticky error bits
-    uint32_t done;      // last-block counter of the reduction
-    uint32_t tickets[4];
+    uint32_t done;      // finished word tiles of the reduction
+    uint32_t ntiles;    // item tiles of this frame: ceil(N / kTileItems)
+    uint32_t reserved[3];
     uint32_t stats[kStCount];
     uint32_t pad[64 - 10 - kStCount];
 };
 static_assert(sizeof(Globals) == 256, "Globals must be 256 bytes");
 
+// Per-instance device arrays and sizes.
 struct Inst {
     uint64_t* heap;
     uint4* nb;
@@ -73,14 +81,13 @@ struct Inst {
     uint32_t* live;
     uint32_t* freel;
     uint32_t* scan;
-    unsigned long long* status;  // [3][ntiles_items] then [ntiles_words]
+    uint4* grp;  // per live index: members of the group whose smallest member it is
     double* root64;
     void* rel;
     Globals* g;
     uint32_t cap, W, D, H, ch, max_depth;
     uint32_t ntiles_items;  // ceil(cap / kTileItems)
-    uint32_t ntiles_words;  // W / tile_words
-    uint32_t tile_words;    // min(W, kTileWords)
+    uint32_t pad_;
 };
 
 struct FrameP {
@@ -95,12 +102,43 @@ struct FrameP {
     const uint64_t* merge_list;
     uint32_t n_merge;
     uint32_t frame;  // frame counter (RANDOM mode key)
+    float* vout;     // optional vertex export, vcap rows of 9 floats
+    uint32_t vcap;
+};
+
+// Launch-wide counters of one batch (256 bytes).
+struct BatchGlobals {
+    uint32_t tickets[8];
+    uint32_t total_tiles;  // item tiles of this frame over all instances
+    uint32_t pad[64 - 9];
+};
+static_assert(sizeof(BatchGlobals) == 256, "BatchGlobals must be 256 bytes");
+
+// A batch of independent instances updated by one launch per kernel. Item
+// tiles of instance b are the global tiles [tile_base[b], tile_base[b+1])
+// (recomputed on the device every frame from the live counts); word tiles
+// and vertex tiles use static prefixes. A single instance is a batch of one.
+struct BatchDev {
+    const Inst* inst;     // [B]
+    const FrameP* fps;    // [B] in device memory, or null: fp0 for every instance
+    FrameP fp0;
+    uint32_t B;
+    uint32_t tw;          // word-tile size of the reduction and free-list kernels
+    uint32_t* tile_base;  // [B+1]
+    const uint32_t* wtile_base;  // [B+1] word tiles, min(W_b, tw) words each
+    const uint32_t* vtile_base;  // [B+1] ceil(cap_b / kTileItems)
+    const uint32_t* rel_base;    // [B+1] 9 * H_b
+    BatchGlobals* bg;
+    unsigned long long* status;  // [2 * Titems + Twords] look-back descriptors
+    uint32_t Titems, Twords, Trel;
+    uint32_t* nout;              // optional [B]: live count at frame start per instance
 };
 
 constexpr int kThreads = 256;
 constexpr int kItemsPerThread = 4;
 constexpr uint32_t kTileItems = kThreads * kItemsPerThread;  // 1024 live indices
-constexpr uint32_t kTileWords = 1024;                         // 32768 bits
+constexpr uint32_t kMaxTileWords = 256;                       // up to 8192 bits per tile
+constexpr uint32_t kMinTileWords = 64;
 
 // ------------------------------------------------------------------ bits
 

@@ -1,12 +1,15 @@
 // Kernels of one frame of the CBT bisection update for sm_103a.
 //
 // Frame = k_prep, k_classify, k_gate, k_scatter, k_alloc, k_free, k_fill,
-// k_cbt. Every per-bisector kernel reads the live count from device memory
-// (the CBT root) and walks a grid-stride loop, which replaces the paper's
-// DispatchIndirect. The two prefix scans are single-pass decoupled look-back
-// scans over tiles handed out by an atomic ticket, so a tile only ever waits
-// for tiles already owned by running blocks; every wait is bounded and sets
-// kErrTimeout instead of hanging.
+// k_cbt [, k_vertices], each launched once for a whole batch of independent
+// instances (a single instance is a batch of one). Item kernels walk global
+// tiles of 1024 live indices; tile t belongs to the instance b with
+// tile_base[b] <= t < tile_base[b+1], recomputed on the device each frame
+// from the CBT roots (this replaces the paper's DispatchIndirect). The two
+// prefix scans and the reduction are single-pass decoupled look-back scans
+// over tiles handed out by an atomic ticket, so a tile only waits for tiles
+// owned by running blocks; the first tile of each instance starts its own
+// chain. Every wait is bounded and sets kErrTimeout instead of hanging.
 #include "cbt_kernels.cuh"
 
 namespace cbtgpu {
@@ -26,7 +29,6 @@ __device__ __forceinline__ bool bad_slot(const Inst& I, uint32_t s, uint32_t err
     set_err(I.g, err);
     return true;
 }
-
 __device__ __forceinline__ uint32_t link_of(const uint4& r, int e) {
     return e == 0 ? r.x : (e == 1 ? r.y : r.z);
 }
@@ -35,6 +37,23 @@ __device__ __forceinline__ unsigned long long ld_status(const unsigned long long
 }
 __device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
     *reinterpret_cast<volatile unsigned long long*>(p) = v;
+}
+__device__ __forceinline__ const FrameP& frame_of(const BatchDev& bt, uint32_t b) {
+    return bt.fps ? bt.fps[b] : bt.fp0;
+}
+
+// Largest b in [0, B) with base[b] <= t (base is non-decreasing, base[B] is
+// the total): the instance owning global tile t.
+__device__ __forceinline__ uint32_t find_inst(const uint32_t* base, uint32_t B, uint32_t t) {
+    uint32_t lo = 0, hi = B;
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (base[mid] <= t)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
 }
 
 // ------------------------------------------------------------ block scans
@@ -74,8 +93,8 @@ __device__ __forceinline__ Pair block_scan(Pair x, Pair& total, Pair* s_warp) {
     return r;
 }
 
-// Exclusive prefix of tile `tile` (called by all lanes of warp 0 after the
-// tile's aggregate has been published). Bounded waits.
+// Exclusive prefix of global tile `tile` (local tile > 0), by all lanes of
+// warp 0 after the tile's aggregate has been published. Bounded waits.
 __device__ Pair lookback(unsigned long long* status, uint32_t tile, Globals* g) {
     const int lane = threadIdx.x & 31;
     Pair excl{0, 0};
@@ -110,14 +129,14 @@ __device__ Pair lookback(unsigned long long* status, uint32_t tile, Globals* g) 
     return excl;
 }
 
-// Publishes the tile aggregate, looks back, publishes the inclusive prefix;
-// returns the tile's exclusive prefix to every thread.
-__device__ __forceinline__ Pair tile_prefix(unsigned long long* status, uint32_t tile, Pair agg,
-                                            Globals* g, Pair* s_excl) {
+// Publishes the tile aggregate, looks back (unless it is the instance's
+// first tile), publishes the inclusive prefix; returns the exclusive prefix.
+__device__ __forceinline__ Pair tile_prefix(unsigned long long* status, uint32_t tile, bool first,
+                                            Pair agg, Globals* g, Pair* s_excl) {
     if (threadIdx.x < 32) {
         Pair ex{0, 0};
-        if (tile == 0) {
-            if (threadIdx.x == 0) st_status(status, pack_status(kFlagIncl, agg));
+        if (first) {
+            if (threadIdx.x == 0) st_status(status + tile, pack_status(kFlagIncl, agg));
         } else {
             if (threadIdx.x == 0) st_status(status + tile, pack_status(kFlagAgg, agg));
             ex = lookback(status, tile, g);
@@ -131,48 +150,117 @@ __device__ __forceinline__ Pair tile_prefix(unsigned long long* status, uint32_t
     return r;
 }
 
-__device__ __forceinline__ uint32_t next_tile(Globals* g, int which, uint32_t* s_tile) {
-    if (threadIdx.x == 0) *s_tile = atomicAdd(&g->tickets[which], 1u);
+__device__ __forceinline__ uint32_t next_ticket(BatchGlobals* bg, int which, uint32_t* s_tile) {
+    if (threadIdx.x == 0) *s_tile = atomicAdd(&bg->tickets[which], 1u);
     __syncthreads();
     const uint32_t t = *s_tile;
     __syncthreads();
     return t;
 }
 
-// Warp-aggregated statistics counter.
-__device__ __forceinline__ void count_stat(Globals* g, int idx, bool pred) {
+// Statistics: warp-aggregated adds into per-block shared counters, flushed
+// to the instance's counters once per tile (block-uniform points), so that a
+// frame costs one global atomic per counter and tile.
+constexpr int kBlockStats = 4;
+__device__ __forceinline__ void count_stat(uint32_t* s_cnt, int k, bool pred) {
     const unsigned act = __activemask();
     const unsigned m = __ballot_sync(act, pred);
-    if (m && (int)(threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(&g->stats[idx], (uint32_t)__popc(m));
+    if (m && (int)(threadIdx.x & 31) == __ffs(act) - 1) atomicAdd(&s_cnt[k], (uint32_t)__popc(m));
+}
+__device__ __forceinline__ void stats_reset(uint32_t* s_cnt) {
+    if (threadIdx.x < kBlockStats) s_cnt[threadIdx.x] = 0;
+}
+// Call between __syncthreads with every thread of the block.
+__device__ __forceinline__ void stats_flush(uint32_t* s_cnt, Globals* g, int i0, int i1 = -1, int i2 = -1,
+                                            int i3 = -1) {
+    const int idx[kBlockStats] = {i0, i1, i2, i3};
+    if (threadIdx.x < kBlockStats && idx[threadIdx.x] >= 0 && s_cnt[threadIdx.x])
+        atomicAdd(&g->stats[idx[threadIdx.x]], s_cnt[threadIdx.x]);
+}
+
+// Per-tile copies of the instance descriptor and frame parameters in shared
+// memory: their fields are then read without reloads after global stores.
+__device__ __forceinline__ void load_tile_ctx(const BatchDev& bt, uint32_t b, Inst* s_inst, FrameP* s_fp) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(bt.inst + b);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_inst);
+    for (uint32_t k = threadIdx.x; k < sizeof(Inst) / 4; k += blockDim.x) dst[k] = src[k];
+    if (s_fp) {
+        const uint32_t* fs = reinterpret_cast<const uint32_t*>(bt.fps ? bt.fps + b : &bt.fp0);
+        uint32_t* fd = reinterpret_cast<uint32_t*>(s_fp);
+        for (uint32_t k = threadIdx.x; k < sizeof(FrameP) / 4; k += blockDim.x) fd[k] = fs[k];
+    }
+}
+
+// Start of a tile: its instance and local index, the instance descriptor
+// and frame parameters copied to shared memory, the block counters cleared.
+__device__ __forceinline__ void tile_begin(const BatchDev& bt, const uint32_t* base, uint32_t t, uint32_t* s_b,
+                                           Inst* s_inst, FrameP* s_fp, uint32_t* s_cnt, uint32_t& b,
+                                           uint32_t& lt) {
+    if (threadIdx.x == 0) *s_b = find_inst(base, bt.B, t);
+    if (s_cnt) stats_reset(s_cnt);
+    __syncthreads();
+    b = *s_b;
+    lt = t - base[b];
+    load_tile_ctx(bt, b, s_inst, s_fp);
+    __syncthreads();
 }
 
 // ------------------------------------------------------------------ prep
 
-// Per-frame reset and camera-relative root table. FP64 is used here only to
-// subtract the origin from the FP64 root vertices.
-__global__ void __launch_bounds__(kThreads) k_prep(Inst I, FrameP fp, int frame_start) {
+// Frame start: per-instance counters, the item-tile prefix over the batch
+// (block 0), the look-back descriptors zeroed, and the camera-relative root
+// tables. FP64 is used here only to subtract the eye from the root vertices.
+__global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start) {
+    __shared__ uint32_t s_carry;
+    __shared__ Pair s_warp[kThreads / 32 + 1];
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nth = gridDim.x * blockDim.x;
     if (frame_start) {
-        if (tid == 0) {
-            const uint32_t N = I.sums[1];
-            I.g->N = N;
-            I.g->F = I.cap - N;
-            I.g->A = 0;
-            I.g->Mg = 0;
-            I.g->done = 0;
-            for (int k = 0; k < 4; ++k) I.g->tickets[k] = 0;
-            for (int k = 0; k < kStCount; ++k) I.g->stats[k] = 0;
-            I.g->stats[kStLiveBefore] = N;
-            I.g->stats[kStFreeBefore] = I.cap - N;
-            I.g->stats[kStFrame] = fp.frame;
+        if (blockIdx.x == 0) {
+            if (threadIdx.x == 0) s_carry = 0;
+            __syncthreads();
+            for (uint32_t b0 = 0; b0 < bt.B; b0 += kThreads) {
+                const uint32_t b = b0 + threadIdx.x;
+                uint32_t tiles = 0;
+                if (b < bt.B) {
+                    const Inst& I = bt.inst[b];
+                    const uint32_t N = I.sums[1];
+                    Globals* g = I.g;
+                    g->N = N;
+                    g->F = I.cap - N;
+                    g->A = 0;
+                    g->Mg = 0;
+                    g->done = 0;
+                    tiles = (N + kTileItems - 1u) / kTileItems;
+                    g->ntiles = tiles;
+                    for (int k = 0; k < kStCount; ++k) g->stats[k] = 0;
+                    g->stats[kStLiveBefore] = N;
+                    g->stats[kStFreeBefore] = I.cap - N;
+                    g->stats[kStFrame] = frame_of(bt, b).frame;
+                    if (bt.nout) bt.nout[b] = N;
+                }
+                Pair tot;
+                const Pair ex = block_scan(Pair{0, tiles}, tot, s_warp);
+                if (b < bt.B) bt.tile_base[b] = s_carry + ex.b;
+                __syncthreads();
+                if (threadIdx.x == 0) s_carry += tot.b;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                bt.tile_base[bt.B] = s_carry;
+                bt.bg->total_tiles = s_carry;
+                for (int k = 0; k < 8; ++k) bt.bg->tickets[k] = 0;
+            }
         }
-        const uint32_t nstat = 3u * I.ntiles_items + I.ntiles_words;
-        for (uint32_t k = tid; k < nstat; k += nth) I.status[k] = 0ull;
+        const uint32_t nstat = 2u * bt.Titems + bt.Twords;
+        for (uint32_t k = tid; k < nstat; k += nth) bt.status[k] = 0ull;
     }
-    const uint32_t n = 9u * I.H;
-    for (uint32_t e = tid; e < n; e += nth) {
-        const double diff = __dsub_rn(I.root64[e], fp.eye[e % 3u]);
+    for (uint32_t e = tid; e < bt.Trel; e += nth) {
+        const uint32_t b = find_inst(bt.rel_base, bt.B, e);
+        const Inst& I = bt.inst[b];
+        const FrameP& fp = frame_of(bt, b);
+        const uint32_t le = e - bt.rel_base[b];
+        const double diff = __dsub_rn(I.root64[le], fp.eye[le % 3u]);
         if (fp.precision == 1) {
             const double sc = __dmul_rn(diff, pow2d(fp.shift));
             long long x = 0;
@@ -180,11 +268,11 @@ __global__ void __launch_bounds__(kThreads) k_prep(Inst I, FrameP fp, int frame_
                 x = __double2ll_rn(sc);
             else
                 set_err(I.g, kErrRange);
-            static_cast<long long*>(I.rel)[e] = x;
+            static_cast<long long*>(I.rel)[le] = x;
         } else if (fp.precision == 2) {
-            static_cast<double*>(I.rel)[e] = diff;
+            static_cast<double*>(I.rel)[le] = diff;
         } else {
-            static_cast<float*>(I.rel)[e] = __double2float_rn(diff);
+            static_cast<float*>(I.rel)[le] = __double2float_rn(diff);
         }
     }
 }
@@ -245,50 +333,71 @@ __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool scatter) {
     return cost;
 }
 
-__global__ void __launch_bounds__(kThreads) k_classify(Inst I, FrameP fp) {
-    const uint32_t N = ld_volatile(&I.g->N);
-    const uint64_t key = splitmix64(((uint64_t)fp.seed << 32) | (uint64_t)fp.frame);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const uint32_t s = I.live[i];
-        const uint64_t j = I.heap[s];
-        const int d = depth_of(j, I.ch);
-        const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
-        bool split = false, merge = false;
-        if (d < 0 || h >= I.H) {
-            set_err(I.g, kErrLink);
-            *cmd_ptr(I, s) = 0u;
-            I.scan[i] = 0u;
-            continue;
+__device__ __forceinline__ void classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
+                                              uint32_t* s_cnt) {
+    const uint32_t s = I.live[i];
+    const uint64_t j = I.heap[s];
+    const int d = depth_of(j, I.ch);
+    const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
+    bool split = false, merge = false;
+    if (d < 0 || h >= I.H) {
+        set_err(I.g, kErrLink);
+        *cmd_ptr(I, s) = 0u;
+        I.scan[i] = 0u;
+        return;
+    }
+    switch (fp.mode) {
+        case 0:
+            if (d <= 31)
+                lod_wishes<uint32_t>(I, fp, j, d, h, split, merge);
+            else
+                lod_wishes<unsigned long long>(I, fp, j, d, h, split, merge);
+            break;
+        case 1:
+            split = d < (int)I.max_depth;
+            break;
+        case 2:
+            merge = d >= 1;
+            break;
+        case 3:
+            split = d < (int)I.max_depth && (splitmix64(j ^ key) & 7ull) == 0ull;
+            merge = !split && d >= 1 && (splitmix64((j >> 1) ^ key) & 1ull);
+            break;
+        default:
+            split = d < (int)I.max_depth && in_sorted(fp.split_list, fp.n_split, j);
+            merge = !split && d >= 1 && in_sorted(fp.merge_list, fp.n_merge, j);
+            break;
+    }
+    const uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
+                         ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
+    *cmd_ptr(I, s) = cmd;
+    uint32_t cost = 0;
+    if (split) cost = fp.gate == 1 ? 3u * (uint32_t)d + 4u : chain_walk(I, s, d, false);
+    I.scan[i] = cost;
+    count_stat(s_cnt, 0, split);
+}
+
+__global__ void __launch_bounds__(kThreads) k_classify(BatchDev bt) {
+    __shared__ uint32_t s_b;
+    __shared__ Inst s_I;
+    __shared__ FrameP s_fp;
+    __shared__ uint32_t s_cnt[kBlockStats];
+    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        uint32_t b, lt;
+        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, &s_fp, s_cnt, b, lt);
+        const Inst& I = s_I;
+        const FrameP& fp = s_fp;
+        const uint32_t N = I.g->N;
+        const uint64_t key = splitmix64(((uint64_t)fp.seed << 32) | (uint64_t)fp.frame);
+#pragma unroll 1
+        for (int k = 0; k < kItemsPerThread; ++k) {
+            const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+            if (i < N) classify_item(I, fp, key, i, s_cnt);
         }
-        switch (fp.mode) {
-            case 0:
-                if (d <= 31)
-                    lod_wishes<uint32_t>(I, fp, j, d, h, split, merge);
-                else
-                    lod_wishes<unsigned long long>(I, fp, j, d, h, split, merge);
-                break;
-            case 1:
-                split = d < (int)I.max_depth;
-                break;
-            case 2:
-                merge = d >= 1;
-                break;
-            case 3:
-                split = d < (int)I.max_depth && (splitmix64(j ^ key) & 7ull) == 0ull;
-                merge = !split && d >= 1 && (splitmix64((j >> 1) ^ key) & 1ull);
-                break;
-            default:
-                split = d < (int)I.max_depth && in_sorted(fp.split_list, fp.n_split, j);
-                merge = !split && d >= 1 && in_sorted(fp.merge_list, fp.n_merge, j);
-                break;
-        }
-        const uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
-                             ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
-        *cmd_ptr(I, s) = cmd;
-        uint32_t cost = 0;
-        if (split) cost = fp.gate == 1 ? 3u * (uint32_t)d + 4u : chain_walk(I, s, d, false);
-        I.scan[i] = cost;
-        count_stat(I.g, kStSplitWishes, split);
+        __syncthreads();
+        stats_flush(s_cnt, I.g, kStSplitWishes);
+        __syncthreads();
     }
 }
 
@@ -298,10 +407,11 @@ struct Group {
     uint32_t m[4];
     uint64_t j[4];
     int n, imin, np;
-    uint64_t p[2];
 };
 
-// Alg. 4 on the frame-start state.
+// Alg. 4 on the frame-start state. Members: m[0] = s1, m[1] its sibling,
+// m[2] the bisector across the outer half of the refinement edge, m[3] its
+// sibling.
 __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
     const uint64_t j1 = I.heap[s1];
     if (depth_of(j1, I.ch) < 1) return false;
@@ -315,7 +425,9 @@ __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
     if ((j2 >> 1) != (j1 >> 1)) return false;
     g.m[0] = s1; g.j[0] = j1;
     g.m[1] = s2; g.j[1] = j2;
+    g.m[2] = g.m[3] = kNull;
     g.n = 2;
+    g.np = 1;
     if (s3 != kNull) {
         const uint64_t j3 = I.heap[s3];
         if (bitlen64(j3) != bitlen64(j1) || (j3 >> 1) == (j1 >> 1)) return false;
@@ -327,47 +439,42 @@ __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
         g.m[2] = s3; g.j[2] = j3;
         g.m[3] = s4; g.j[3] = j4;
         g.n = 4;
+        g.np = 2;
     }
     g.imin = 0;
     for (int k = 1; k < g.n; ++k)
         if (g.j[k] < g.j[g.imin]) g.imin = k;
-    g.p[0] = g.j[0] >> 1;
-    g.np = 1;
-    if (g.n == 4) {
-        const uint64_t q = g.j[2] >> 1;
-        if (q < g.p[0]) {
-            g.p[1] = g.p[0];
-            g.p[0] = q;
-        } else {
-            g.p[1] = q;
-        }
-        g.np = 2;
-    }
     return true;
-}
-
-__device__ __forceinline__ int parent_index(const Group& g, int k) {
-    return (g.np == 2 && (g.j[k] >> 1) == g.p[1]) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------ gate
 
 // Scan of (merge cost at the group's smallest member, split chain cost) in
-// ascending slot order; merges are granted while their running total fits
-// the free slots, then splits while (granted merges + their running total)
-// fits (deterministic form of the allocation-counter test of Sec. 3.3).
-__global__ void __launch_bounds__(kThreads) k_gate(Inst I, FrameP fp) {
-    __shared__ uint32_t s_tile;
+// ascending slot order per instance; merges are granted while their running
+// total fits the free slots, then splits while (granted merges + their
+// running total) fits (deterministic form of the allocation-counter test of
+// Sec. 3.3). The smallest member (always an even heap ID) walks its group
+// once and records the members for k_alloc and k_fill: m0, m1 are the
+// children of the smaller parent, m2, m3 those of the larger one.
+__global__ void __launch_bounds__(kThreads) k_gate(BatchDev bt) {
+    __shared__ uint32_t s_tile, s_b, s_mg;
     __shared__ Pair s_warp[kThreads / 32 + 1];
     __shared__ Pair s_excl;
-    const uint32_t N = ld_volatile(&I.g->N);
-    const uint32_t F = ld_volatile(&I.g->F);
-    const uint32_t ntiles = (N + kTileItems - 1) / kTileItems;
-    unsigned long long* status = I.status;
+    __shared__ Inst s_I;
+    __shared__ uint32_t s_cnt[kBlockStats];
+    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    unsigned long long* status = bt.status;
     for (;;) {
-        const uint32_t tile = next_tile(I.g, 0, &s_tile);
-        if (tile >= ntiles) break;
-        const uint32_t base = tile * kTileItems + threadIdx.x * kItemsPerThread;
+        const uint32_t t = next_ticket(bt.bg, 0, &s_tile);
+        if (t >= T) break;
+        uint32_t b, lt;
+        if (threadIdx.x == 0) s_mg = 0;
+        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
+        const Inst& I = s_I;
+        const FrameP& fp = frame_of(bt, b);
+        const uint32_t gate = fp.gate;
+        const uint32_t N = I.g->N, F = I.g->F;
+        const uint32_t base = lt * kTileItems + threadIdx.x * kItemsPerThread;
         Pair v[kItemsPerThread];
         uint32_t slot[kItemsPerThread];
         Pair loc{0, 0};
@@ -381,12 +488,15 @@ __global__ void __launch_bounds__(kThreads) k_gate(Inst I, FrameP fp) {
                 slot[k] = s;
                 const uint32_t cmd = *cmd_ptr(I, s);
                 uint32_t mc = 0;
-                if (cmd & kMergeWish) {
+                if ((cmd & kMergeWish) && !(cmd & kHeapOdd)) {
                     Group g;
                     if (find_group(I, s, g) && g.imin == 0) {
                         bool all = true;
                         for (int m = 1; m < g.n; ++m) all = all && (*cmd_ptr(I, g.m[m]) & kMergeWish);
-                        if (all) mc = fp.gate == 1 ? 2u : (uint32_t)g.np;
+                        if (all) {
+                            mc = gate == 1 ? 2u : (uint32_t)g.np;
+                            I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
+                        }
                     }
                 }
                 v[k] = Pair{mc, I.scan[i]};
@@ -395,7 +505,7 @@ __global__ void __launch_bounds__(kThreads) k_gate(Inst I, FrameP fp) {
         }
         Pair tot;
         const Pair tex = block_scan(loc, tot, s_warp);
-        const Pair ex = tile_prefix(status, tile, tot, I.g, &s_excl);
+        const Pair ex = tile_prefix(status, t, lt == 0, tot, I.g, &s_excl);
         Pair run = padd(ex, tex);
 #pragma unroll
         for (int k = 0; k < kItemsPerThread; ++k) {
@@ -404,53 +514,87 @@ __global__ void __launch_bounds__(kThreads) k_gate(Inst I, FrameP fp) {
             if (i >= N) continue;
             const bool cand = v[k].a > 0;
             const bool granted = cand && run.a <= F;
-            if (granted) {
-                atomicOr(cmd_ptr(I, slot[k]), kMergeGrant);
-                atomicMax(&I.g->Mg, run.a);
-            }
+            if (cand) atomicOr(cmd_ptr(I, slot[k]), granted ? (kCand | kMergeGrant) : kCand);
+            if (granted) atomicMax(&s_mg, run.a);
             I.scan[i] = run.b;
-            count_stat(I.g, kStMergeCand, cand);
-            count_stat(I.g, kStMergeGranted, granted);
+            count_stat(s_cnt, 0, cand);
+            count_stat(s_cnt, 1, granted);
         }
+        __syncthreads();
+        stats_flush(s_cnt, I.g, kStMergeCand, kStMergeGranted);
+        if (threadIdx.x == 0 && s_mg) atomicMax(&I.g->Mg, s_mg);
+        __syncthreads();
     }
 }
 
 // --------------------------------------------------------------- scatter
 
-__global__ void __launch_bounds__(kThreads) k_scatter(Inst I) {
-    const uint32_t N = ld_volatile(&I.g->N);
-    const uint64_t F = ld_volatile(&I.g->F);
-    const uint64_t Mg = ld_volatile(&I.g->Mg);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const uint32_t s = I.live[i];
-        const uint32_t cmd = *cmd_ptr(I, s);
-        bool granted = false;
-        if (cmd & kSplitWish) {
-            granted = Mg + (uint64_t)I.scan[i] <= F;
-            if (granted) chain_walk(I, s, 0, true);
+// Granted split requests mark their chains. The requests of a tile are first
+// packed in shared memory so that whole warps walk chains.
+__global__ void __launch_bounds__(kThreads) k_scatter(BatchDev bt) {
+    __shared__ uint32_t s_b, s_n;
+    __shared__ uint32_t s_list[kTileItems];
+    __shared__ Inst s_I;
+    __shared__ uint32_t s_cnt[kBlockStats];
+    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        uint32_t b, lt;
+        if (threadIdx.x == 0) s_n = 0;
+        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
+        const Inst& I = s_I;
+        const uint32_t N = I.g->N;
+        const uint64_t F = I.g->F, Mg = ld_volatile(&I.g->Mg);
+#pragma unroll
+        for (int k = 0; k < kItemsPerThread; ++k) {
+            const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+            bool granted = false;
+            if (i < N) {
+                const uint32_t s = I.live[i];
+                if (*cmd_ptr(I, s) & kSplitWish) {
+                    granted = Mg + (uint64_t)I.scan[i] <= F;
+                    if (granted) s_list[atomicAdd(&s_n, 1u)] = s;
+                }
+            }
+            count_stat(s_cnt, 0, granted);
         }
-        count_stat(I.g, kStSplitGranted, granted);
+        __syncthreads();
+        const uint32_t n = s_n;
+        for (uint32_t k = threadIdx.x; k < n; k += kThreads) chain_walk(I, s_list[k], 0, true);
+        __syncthreads();
+        stats_flush(s_cnt, I.g, kStSplitGranted);
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------ allocation
 
+__device__ __forceinline__ uint32_t leaves_of(uint32_t sb) {
+    return sb ? 2u + ((sb >> 1) & 1u) + ((sb >> 2) & 1u) : 0u;
+}
+
 // Fates and the exclusive scan of allocation counts in ascending slot order
 // (ReserveBlocks): a split bisector takes 2-4 leaves, a valid merge group
-// its parents at its smallest member. dest = index into the free list.
-__global__ void __launch_bounds__(kThreads) k_alloc(Inst I) {
-    __shared__ uint32_t s_tile;
+// its parents at its smallest member, which also marks every member merged
+// and gives each the free-list index of its parent.
+__global__ void __launch_bounds__(kThreads) k_alloc(BatchDev bt) {
+    __shared__ uint32_t s_tile, s_b;
     __shared__ Pair s_warp[kThreads / 32 + 1];
     __shared__ Pair s_excl;
-    const uint32_t N = ld_volatile(&I.g->N);
-    const uint32_t ntiles = (N + kTileItems - 1) / kTileItems;
-    unsigned long long* status = I.status + I.ntiles_items;
+    __shared__ Inst s_I;
+    __shared__ uint32_t s_cnt[kBlockStats];
+    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    unsigned long long* status = bt.status + bt.Titems;
     for (;;) {
-        const uint32_t tile = next_tile(I.g, 1, &s_tile);
-        if (tile >= ntiles) break;
-        const uint32_t base = tile * kTileItems + threadIdx.x * kItemsPerThread;
+        const uint32_t t = next_ticket(bt.bg, 1, &s_tile);
+        if (t >= T) break;
+        uint32_t b, lt;
+        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
+        const Inst& I = s_I;
+        const uint32_t N = I.g->N;
+        const uint32_t base = lt * kTileItems + threadIdx.x * kItemsPerThread;
         uint32_t na[kItemsPerThread], slot[kItemsPerThread];
-        uint8_t fate[kItemsPerThread];  // 0 keep, 1 split, 2 merged, 3 merged min
+        uint32_t fate[kItemsPerThread];  // 0 keep (or merged, not smallest), 1 split, 3 merge at smallest
+        uint4 mem[kItemsPerThread];
         Pair loc{0, 0};
 #pragma unroll
         for (int k = 0; k < kItemsPerThread; ++k) {
@@ -458,33 +602,40 @@ __global__ void __launch_bounds__(kThreads) k_alloc(Inst I) {
             na[k] = 0;
             fate[k] = 0;
             slot[k] = kNull;
+            mem[k] = make_uint4(kNull, kNull, kNull, kNull);
             if (i >= N) continue;
             const uint32_t s = I.live[i];
             slot[k] = s;
             const uint32_t cmd = *cmd_ptr(I, s);
             const uint32_t sb = cmd & kSplitMask;
             if (sb) {
-                na[k] = 2u + ((sb >> 1) & 1u) + ((sb >> 2) & 1u);
+                na[k] = leaves_of(sb);
                 fate[k] = 1;
-            } else if (cmd & kMergeWish) {
-                Group g;
-                if (find_group(I, s, g)) {
-                    bool ok = (*cmd_ptr(I, g.m[g.imin]) & kMergeGrant) != 0u;
-                    for (int m = 0; m < g.n; ++m) {
-                        const uint32_t c = *cmd_ptr(I, g.m[m]);
-                        ok = ok && (c & kMergeWish) && !(c & kSplitMask);
+            } else if ((cmd & kCand) && (cmd & kMergeGrant)) {
+                const uint4 m = I.grp[i];
+                const uint32_t ms[3] = {m.y, m.z, m.w};
+                bool ok = true;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (ms[q] == kNull) continue;
+                    if (bad_slot(I, ms[q], kErrLink)) {
+                        ok = false;
+                        continue;
                     }
-                    if (ok) {
-                        fate[k] = g.imin == 0 ? 3 : 2;
-                        if (g.imin == 0) na[k] = (uint32_t)g.np;
-                    }
+                    const uint32_t c = *cmd_ptr(I, ms[q]);
+                    ok = ok && (c & kMergeWish) && !(c & kSplitMask);
+                }
+                if (ok) {
+                    fate[k] = 3;
+                    mem[k] = m;
+                    na[k] = m.z == kNull ? 1u : 2u;
                 }
             }
             loc = padd(loc, Pair{0, na[k]});
         }
         Pair tot;
         const Pair tex = block_scan(loc, tot, s_warp);
-        const Pair ex = tile_prefix(status, tile, tot, I.g, &s_excl);
+        const Pair ex = tile_prefix(status, t, lt == 0, tot, I.g, &s_excl);
         uint32_t run = ex.b + tex.b;
 #pragma unroll
         for (int k = 0; k < kItemsPerThread; ++k) {
@@ -493,70 +644,88 @@ __global__ void __launch_bounds__(kThreads) k_alloc(Inst I) {
             const uint32_t s = slot[k];
             if (fate[k] == 1) {
                 *dest_ptr(I, s) = run;
-            } else if (fate[k] >= 2) {
-                atomicOr(cmd_ptr(I, s), kMerged);
-                if (fate[k] == 3) {
-                    Group g;
-                    find_group(I, s, g);
-                    for (int m = 0; m < g.n; ++m) *dest_ptr(I, g.m[m]) = run + (uint32_t)parent_index(g, m);
+            } else if (fate[k] == 3) {
+                const uint32_t ms[4] = {mem[k].x, mem[k].y, mem[k].z, mem[k].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (ms[q] == kNull) continue;
+                    atomicOr(cmd_ptr(I, ms[q]), kMerged);
+                    *dest_ptr(I, ms[q]) = run + (q < 2 ? 0u : 1u);
                 }
+                atomicAdd(&s_cnt[2], mem[k].z == kNull ? 2u : 4u);
             }
             run += na[k];
-            count_stat(I.g, kStSplitBis, fate[k] == 1);
-            count_stat(I.g, kStMergedBis, fate[k] >= 2);
-            count_stat(I.g, kStMergeGroups, fate[k] == 3);
+            count_stat(s_cnt, 0, fate[k] == 1);
+            count_stat(s_cnt, 1, fate[k] == 3);
         }
-        if (tile == ntiles - 1 && threadIdx.x == kThreads - 1) {
+        if (lt == I.g->ntiles - 1u && threadIdx.x == kThreads - 1) {
             I.g->A = run;
             I.g->stats[kStAllocated] = run;
             if (run > I.g->F) set_err(I.g, kErrOverflow);
         }
+        __syncthreads();
+        stats_flush(s_cnt, I.g, kStSplitBis, kStMergeGroups, kStMergedBis);
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------- free list
 
 // freel[k] = slot of the k-th zero bit of the frame-start bitfield, k < A
-// (Alg. 8 for the first A ranks at once): tiles of words find their zero
-// offset from the sum tree and emit their zeros in order.
-__global__ void __launch_bounds__(kThreads) k_free(Inst I) {
-    __shared__ Pair s_warp[kThreads / 32 + 1];
-    const uint32_t A = min(ld_volatile(&I.g->A), ld_volatile(&I.g->F));
-    if (A == 0) return;
-    const uint32_t TW = I.tile_words;
-    for (uint32_t t = blockIdx.x; t < I.ntiles_words; t += gridDim.x) {
+// (Alg. 8 for the first A ranks at once): each tile of words (one word per
+// thread) finds its zero offset from the sum tree and emits its zeros.
+__global__ void __launch_bounds__(kMaxTileWords) k_free(BatchDev bt) {
+    __shared__ uint32_t s_b;
+    __shared__ uint32_t s_w[kMaxTileWords / 32 + 1];
+    __shared__ Inst s_I;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t t = blockIdx.x; t < bt.Twords; t += gridDim.x) {
+        uint32_t b, lt;
+        tile_begin(bt, bt.wtile_base, t, &s_b, &s_I, nullptr, nullptr, b, lt);
+        const Inst& I = s_I;
+        const uint32_t A = min(ld_volatile(&I.g->A), I.g->F);
+        const uint32_t TW = min(I.W, bt.tw);
+        const uint32_t nt = I.W / TW;
         uint32_t ones_before = 0;
-        for (uint32_t n = I.ntiles_words + t; n > 1; n >>= 1)
+        for (uint32_t n = nt + lt; n > 1; n >>= 1)
             if (n & 1u) ones_before += I.sums[n - 1];
-        const uint64_t zeros_before = (uint64_t)t * TW * 32u - ones_before;
-        if (zeros_before >= A) break;
-        uint32_t words[4] = {0, 0, 0, 0}, zc[4] = {0, 0, 0, 0};
-        uint32_t total = 0;
-        const uint32_t w0 = t * TW + threadIdx.x * 4u;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t w = w0 + k;
-            if (threadIdx.x * 4u + k < TW) {
-                uint32_t valid = 0xFFFFFFFFu;
-                if (I.cap < 32u) valid = (1u << I.cap) - 1u;
-                words[k] = ~I.bits[w] & valid;
-                zc[k] = __popc(words[k]);
-                total += zc[k];
+        const uint64_t zeros_before = (uint64_t)lt * TW * 32u - ones_before;
+        if (zeros_before < A) {  // block-uniform
+            const uint32_t w = lt * TW + threadIdx.x;
+            uint32_t z = 0;
+            if (threadIdx.x < TW) {
+                const uint32_t valid = I.cap < 32u ? (1u << I.cap) - 1u : 0xFFFFFFFFu;
+                z = ~I.bits[w] & valid;
             }
-        }
-        Pair tot;
-        const Pair ex = block_scan(Pair{0, total}, tot, s_warp);
-        uint64_t r = zeros_before + ex.b;
+            const uint32_t mine = __popc(z);
+            uint32_t inc = mine;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t m = words[k];
-            while (m && r < A) {
-                const int b = __ffs(m) - 1;
-                I.freel[r] = (w0 + k) * 32u + (uint32_t)b;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_w[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t x = lane < nw ? s_w[lane] : 0u;
+                uint32_t xi = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+                    if (lane >= o) xi += y;
+                }
+                __syncwarp();
+                if (lane < nw) s_w[lane] = xi - x;
+            }
+            __syncthreads();
+            uint64_t r = zeros_before + s_w[warp] + (inc - mine);
+            while (z && r < A) {
+                I.freel[r] = w * 32u + (uint32_t)(__ffs(z) - 1);
                 ++r;
-                m &= m - 1u;
+                z &= z - 1u;
             }
         }
+        __syncthreads();
     }
 }
 
@@ -607,58 +776,107 @@ __constant__ FamDesc c_fam[4] = {
 
 __device__ __forceinline__ int fam_case(uint32_t sb) { return (int)((sb >> 1) & 3u); }
 
-// Neighbour across the portion `portion` of old edge E of old bisector x
-// (record rx, depth parity xodd) for a new bisector at `newslot` whose edge
-// `newedge` covers it. Returns the new neighbour slot and the neighbour's
-// edge that faces it; an unchanged neighbour gets its own link rewritten
-// (it has exactly one writer: the bisector across that edge).
-__device__ uint32_t resolve(const Inst& I, const uint4& rx, bool xodd, int E, int portion,
-                            uint32_t newslot, int newedge, uint32_t& rev) {
-    const uint32_t y = link_of(rx, E);
-    rev = 3u;
-    if (y == kNull) return kNull;
-    if (bad_slot(I, y, kErrLink)) return kNull;
-    const int Ep = (int)((rx.w >> (2 * E)) & 3u);
+// Does a family with split bits sb cover old edge E by halves?
+__device__ __forceinline__ bool halves(uint32_t sb, int E) {
+    return E == kT || (E == kNe && (sb & kN)) || (E == kPe && (sb & kP));
+}
+
+// Leaf of family `sb` covering portion p of old edge Ep, and that leaf's edge.
+__device__ __forceinline__ bool family_leaf(uint32_t sb, int Ep, int p, uint32_t& leaf, uint32_t& edge) {
+    const FamDesc& f = c_fam[fam_case(sb)];
+    for (int l = 0; l < f.n; ++l)
+        for (int e = 0; e < 3; ++e)
+            if (f.e[l][e].ext && f.e[l][e].a == Ep && f.e[l][e].b == p) {
+                leaf = (uint32_t)l;
+                edge = (uint32_t)e;
+                return true;
+            }
+    return false;
+}
+
+// What lies across the old edges of a changed bisector x on the new mesh:
+// per old edge E its old neighbour y (and y's edge facing x, command word and
+// destination), then the new neighbour per portion used ([0] whole or first
+// half, [1] second half) and that neighbour's edge facing the new bisector.
+struct Across {
+    uint32_t y[3];
+    uint32_t ep[3];
+    uint2 yc[3];
+    uint32_t slot[3][2];
+    uint32_t rev[3][2];
+};
+
+// The three neighbour loads are independent, so they overlap.
+__device__ __forceinline__ void across_load(const Inst& I, const uint4& rx, Across& a) {
+#pragma unroll
+    for (int E = 0; E < 3; ++E) {
+        a.y[E] = link_of(rx, E);
+        a.ep[E] = (rx.w >> (2 * E)) & 3u;
+        a.yc[E] = make_uint2(0u, 0u);
+        if (a.y[E] != kNull && !bad_slot(I, a.y[E], kErrLink))
+            a.yc[E] = I.cd[a.y[E]];
+        else
+            a.y[E] = kNull;
+    }
+}
+
+// Resolves old edge E of x (depth parity xodd), whole (hv = false) or by
+// halves: a split neighbour gives the leaf of its family on the same
+// portion, a merged one its parent, an unchanged one itself (R11 reading).
+__device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, bool xodd) {
+    const uint32_t y = a.y[E];
+    a.slot[E][0] = a.slot[E][1] = kNull;
+    a.rev[E][0] = a.rev[E][1] = 3u;
+    if (y == kNull) return;
+    const int Ep = (int)a.ep[E];
+    const uint2 yc = a.yc[E];
+    const uint32_t ysb = yc.x & kSplitMask;
+    const uint32_t A = I.g->A;
     if (Ep > 2) {
         set_err(I.g, kErrLink);
-        return kNull;
+        return;
     }
-    const uint2 yc = I.cd[y];
-    const uint32_t A = I.g->A;
-    const uint32_t ysb = yc.x & kSplitMask;
     if (ysb) {
-        int py = portion;
-        if (portion != kWhole && (((yc.x & kDepthOdd) != 0u) == xodd)) py = portion == kFirst ? kSecond : kFirst;
-        const FamDesc& f = c_fam[fam_case(ysb)];
-        for (int l = 0; l < f.n; ++l)
-            for (int e = 0; e < 3; ++e)
-                if (f.e[l][e].ext && f.e[l][e].a == Ep && f.e[l][e].b == py) {
-                    if (yc.y + (uint32_t)l >= A) {
-                        set_err(I.g, kErrLink);
-                        return kNull;
-                    }
-                    rev = (uint32_t)e;
-                    return I.freel[yc.y + (uint32_t)l];
-                }
-        set_err(I.g, kErrLink);
-        return kNull;
-    }
-    if (yc.x & kMerged) {
-        if (portion != kWhole || Ep != kT) set_err(I.g, kErrLink);
-        if (yc.y >= A) {
-            set_err(I.g, kErrLink);
-            return kNull;
+        const bool same = ((yc.x & kDepthOdd) != 0u) == xodd;
+        for (int h = 0; h < (hv ? 2 : 1); ++h) {
+            int p = hv ? (h == 0 ? kFirst : kSecond) : kWhole;
+            if (p != kWhole && same) p = p == kFirst ? kSecond : kFirst;
+            uint32_t leaf, edge;
+            if (!family_leaf(ysb, Ep, p, leaf, edge) || yc.y + leaf >= A) {
+                set_err(I.g, kErrLink);
+                continue;
+            }
+            a.slot[E][h] = I.freel[yc.y + leaf];
+            a.rev[E][h] = edge;
         }
-        rev = (yc.x & kHeapOdd) ? (uint32_t)kNe : (uint32_t)kPe;
-        return I.freel[yc.y];
+    } else if (yc.x & kMerged) {
+        if (hv || Ep != kT || yc.y >= A) {
+            set_err(I.g, kErrLink);
+            return;
+        }
+        a.slot[E][0] = I.freel[yc.y];
+        a.rev[E][0] = (yc.x & kHeapOdd) ? (uint32_t)kNe : (uint32_t)kPe;
+    } else {
+        if (hv) {
+            set_err(I.g, kErrLink);
+            return;
+        }
+        a.slot[E][0] = y;
+        a.rev[E][0] = (uint32_t)Ep;
     }
-    if (portion != kWhole) set_err(I.g, kErrLink);
+}
+
+// An unchanged neighbour across old edge E of x now faces new bisector ns
+// through ns's edge ne; that neighbour link has exactly one writer, this one.
+__device__ __forceinline__ void push_keep(const Inst& I, const Across& a, int E, uint32_t ns, uint32_t ne,
+                                          uint32_t* s_cnt) {
+    const uint32_t y = a.y[E];
+    if (y == kNull || (a.yc[E].x & (kSplitMask | kMerged))) return;
     uint32_t* yr = reinterpret_cast<uint32_t*>(I.nb + y);
-    yr[Ep] = newslot;
-    atomicXor(yr + 3, ((uint32_t)(E ^ newedge)) << (2 * Ep));
-    atomicAdd(&I.g->stats[kStRelinked], 1u);
-    rev = (uint32_t)Ep;
-    return y;
+    const int Ep = (int)a.ep[E];
+    yr[Ep] = ns;
+    atomicXor(yr + 3, ((uint32_t)E ^ ne) << (2 * Ep));
+    atomicAdd(&s_cnt[0], 1u);
 }
 
 __device__ __forceinline__ void set_bit(const Inst& I, uint32_t s) {
@@ -668,20 +886,24 @@ __device__ __forceinline__ void clear_bit(const Inst& I, uint32_t s) {
     atomicAnd(I.bits + (s >> 5), ~(1u << (s & 31u)));
 }
 
-__device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t dest) {
-    const uint64_t j = I.heap[s];
-    const uint4 rx = I.nb[s];
-    const bool xodd = (cmd & kDepthOdd) != 0u;
-    const FamDesc& f = c_fam[fam_case(cmd & kSplitMask)];
+__device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t dest, uint32_t* s_cnt) {
+    const uint32_t sb = cmd & kSplitMask;
+    const FamDesc& f = c_fam[fam_case(sb)];
     if (dest + f.n > I.g->A) {
         set_err(I.g, kErrOverflow);
         return;
     }
+    const uint64_t j = I.heap[s];
+    const uint4 rx = I.nb[s];
     uint32_t slots[4];
-    for (int l = 0; l < f.n; ++l) {
-        slots[l] = I.freel[dest + (uint32_t)l];
+    for (int l = 0; l < f.n; ++l) slots[l] = I.freel[dest + (uint32_t)l];
+    Across a;
+    across_load(I, rx, a);
+    const bool xodd = (cmd & kDepthOdd) != 0u;
+#pragma unroll
+    for (int E = 0; E < 3; ++E) across_resolve(I, a, E, halves(sb, E), xodd);
+    for (int l = 0; l < f.n; ++l)
         if (bad_slot(I, slots[l], kErrOverflow)) return;
-    }
     for (int l = 0; l < f.n; ++l) {
         uint32_t lk[3], rv = 0;
         for (int e = 0; e < 3; ++e) {
@@ -691,7 +913,10 @@ __device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t des
                 lk[e] = slots[ed.a];
                 r = ed.b;
             } else {
-                lk[e] = resolve(I, rx, xodd, ed.a, ed.b, slots[l], e, r);
+                const int h = ed.b == kSecond ? 1 : 0;
+                lk[e] = a.slot[ed.a][h];
+                r = a.rev[ed.a][h];
+                if (ed.b == kWhole) push_keep(I, a, ed.a, slots[l], (uint32_t)e, s_cnt);
             }
             rv |= r << (2 * e);
         }
@@ -701,160 +926,184 @@ __device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t des
     }
 }
 
-// Parents of a valid merge group (Alg. 4) written by its smallest member:
+// Parents of a valid merge group (Alg. 4), written by its smallest member:
 // Next = across child 2p+1's Twin edge, Prev = across child 2p's Twin edge,
-// Twin = the other parent (Table 1 read backwards, Alg. 6).
-__device__ void fill_merge(const Inst& I, uint32_t s, uint32_t dest) {
-    Group g;
-    if (!find_group(I, s, g)) {
-        set_err(I.g, kErrLink);
-        return;
-    }
-    const uint32_t base = dest - (uint32_t)parent_index(g, 0);
-    if (base + (uint32_t)g.np > I.g->A) {
+// Twin = the other parent (Table 1 read backwards, Alg. 6). Members m0, m1
+// are the children of the smaller parent, m2, m3 of the other one.
+__device__ void fill_merge(const Inst& I, uint32_t dest, const uint4 m, uint32_t* s_cnt) {
+    const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
+    const int np = m.z == kNull ? 1 : 2;
+    if (dest + (uint32_t)np > I.g->A) {
         set_err(I.g, kErrOverflow);
         return;
     }
-    for (int pk = 0; pk < g.np; ++pk) {
-        const uint64_t p = g.p[pk];
-        uint32_t a = kNull, b = kNull;
-        for (int m = 0; m < g.n; ++m) {
-            if (g.j[m] == 2 * p) a = g.m[m];
-            if (g.j[m] == 2 * p + 1) b = g.m[m];
-        }
-        const uint32_t ps = I.freel[base + (uint32_t)pk];
-        const uint32_t tw = g.np == 2 ? I.freel[base + (uint32_t)(1 - pk)] : kNull;
-        if (a == kNull || b == kNull || bad_slot(I, ps, kErrOverflow) || (tw != kNull && bad_slot(I, tw, kErrOverflow))) {
-            set_err(I.g, kErrLink);
-            return;
-        }
-        const uint32_t rvT = g.np == 2 ? (uint32_t)kT : 3u;
-        uint32_t rvN, rvP;
-        const uint4 rb = I.nb[b], ra = I.nb[a];
+    uint32_t ps[2] = {kNull, kNull};
+    for (int k = 0; k < np; ++k) {
+        ps[k] = I.freel[dest + (uint32_t)k];
+        if (bad_slot(I, ps[k], kErrOverflow)) return;
+    }
+    for (int pk = 0; pk < np; ++pk) {
+        const uint32_t u = ms[2 * pk], v = ms[2 * pk + 1];
+        if (bad_slot(I, u, kErrLink) || bad_slot(I, v, kErrLink)) return;
+        const uint64_t ju = I.heap[u];
+        const uint32_t a = (ju & 1ull) ? v : u;   // child 2p
+        const uint32_t c1 = (ju & 1ull) ? u : v;  // child 2p+1
         const bool modd = (*cmd_ptr(I, a) & kDepthOdd) != 0u;
-        const uint32_t nx = resolve(I, rb, modd, kT, kWhole, ps, kNe, rvN);
-        const uint32_t pv = resolve(I, ra, modd, kT, kWhole, ps, kPe, rvP);
-        I.nb[ps] = make_uint4(tw, nx, pv, rvT | (rvN << 2) | (rvP << 4));
-        I.heap[ps] = p;
-        set_bit(I, ps);
+        Across xa, xb;
+        const uint4 ra = I.nb[a], rb = I.nb[c1];
+        across_load(I, rb, xb);
+        across_load(I, ra, xa);
+        across_resolve(I, xb, kT, false, modd);
+        across_resolve(I, xa, kT, false, modd);
+        push_keep(I, xb, kT, ps[pk], (uint32_t)kNe, s_cnt);
+        push_keep(I, xa, kT, ps[pk], (uint32_t)kPe, s_cnt);
+        const uint32_t tw = np == 2 ? ps[1 - pk] : kNull;
+        const uint32_t rvT = np == 2 ? (uint32_t)kT : 3u;
+        I.nb[ps[pk]] = make_uint4(tw, xb.slot[kT][0], xa.slot[kT][0],
+                                  rvT | (xb.rev[kT][0] << 2) | (xa.rev[kT][0] << 4));
+        I.heap[ps[pk]] = ju >> 1;
+        set_bit(I, ps[pk]);
     }
 }
 
-// FillNewBlocks + UpdateNeighbors + UpdateBitfield for the changed bisectors.
-__global__ void __launch_bounds__(kThreads) k_fill(Inst I) {
-    const uint32_t N = ld_volatile(&I.g->N);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const uint32_t s = I.live[i];
-        const uint2 c = I.cd[s];
-        const uint32_t sb = c.x & kSplitMask;
-        if (!sb && !(c.x & kMerged)) continue;
-        clear_bit(I, s);
-        if (sb) {
-            fill_split(I, s, c.x, c.y);
-        } else {
-            // The smallest member writes the parents; it is the member whose
-            // dest is its own parent's first index with parent index 0 ...
-            Group g;
-            if (find_group(I, s, g) && g.imin == 0) fill_merge(I, s, c.y);
+// FillNewBlocks + UpdateNeighbors + UpdateBitfield for the changed
+// bisectors. The changed bisectors of a tile are packed in shared memory
+// first, so that whole warps build families.
+__global__ void __launch_bounds__(kThreads) k_fill(BatchDev bt) {
+    __shared__ uint32_t s_b, s_n;
+    __shared__ uint32_t s_item[kTileItems];
+    __shared__ Inst s_I;
+    __shared__ uint32_t s_cnt[kBlockStats];
+    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        uint32_t b, lt;
+        if (threadIdx.x == 0) s_n = 0;
+        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
+        const Inst& I = s_I;
+        const uint32_t N = I.g->N;
+#pragma unroll
+        for (int k = 0; k < kItemsPerThread; ++k) {
+            const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+            if (i >= N) continue;
+            const uint32_t s = I.live[i];
+            const uint32_t cmd = *cmd_ptr(I, s);
+            if (!(cmd & (kSplitMask | kMerged))) continue;
+            clear_bit(I, s);
+            if ((cmd & kSplitMask) || ((cmd & kCand) && (cmd & kMerged))) s_item[atomicAdd(&s_n, 1u)] = i;
         }
+        __syncthreads();
+        const uint32_t n = s_n;
+        for (uint32_t k = threadIdx.x; k < n; k += kThreads) {
+            const uint32_t i = s_item[k];
+            const uint32_t s = I.live[i];
+            const uint2 c = I.cd[s];
+            if (c.x & kSplitMask)
+                fill_split(I, s, c.x, c.y, s_cnt);
+            else
+                fill_merge(I, c.y, I.grp[i], s_cnt);
+        }
+        __syncthreads();
+        stats_flush(s_cnt, I.g, kStRelinked);
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------ reduce + compact
 
 // SumReduction over the updated bitfield fused with CachePointers' live list:
-// each tile of words writes its part of the sum tree, finds its live-count
-// prefix by look-back and writes the slots of its set bits; the last tile to
-// finish builds the levels above the tiles.
-__global__ void __launch_bounds__(kThreads) k_cbt(Inst I) {
-    __shared__ uint32_t s_tile;
-    __shared__ Pair s_warp[kThreads / 32 + 1];
+// each tile of words (one word per thread) writes its part of the sum tree,
+// finds its live-count prefix by look-back and writes the slots of its set
+// bits, staged in shared memory so that the stores are coalesced; the last
+// tile of an instance to finish builds the levels above its tiles.
+__global__ void __launch_bounds__(kMaxTileWords) k_cbt(BatchDev bt) {
+    __shared__ uint32_t s_tile, s_b, s_last;
+    __shared__ uint32_t s_w[kMaxTileWords / 32 + 1];
     __shared__ Pair s_excl;
-    __shared__ uint32_t s_lvl[2][kThreads];
-    __shared__ uint32_t s_last;
-    const uint32_t TW = I.tile_words, W = I.W;
-    unsigned long long* status = I.status + 3u * I.ntiles_items;
+    __shared__ uint32_t s_lvl[kMaxTileWords];
+    __shared__ uint32_t s_live[kMaxTileWords * 32];
+    __shared__ Inst s_I;
+    unsigned long long* status = bt.status + 2u * bt.Titems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (;;) {
-        const uint32_t tile = next_tile(I.g, 2, &s_tile);
-        if (tile >= I.ntiles_words) break;
-        const uint32_t w0 = tile * TW + threadIdx.x * 4u;
-        uint32_t wv[4] = {0, 0, 0, 0}, pc[4] = {0, 0, 0, 0};
-        const bool mine = threadIdx.x * 4u < TW;
-        if (mine) {
-            if (TW >= 4u) {
-                const uint4 q = *reinterpret_cast<const uint4*>(I.bits + w0);
-                wv[0] = q.x; wv[1] = q.y; wv[2] = q.z; wv[3] = q.w;
-            } else {
-                for (uint32_t k = 0; k < TW; ++k) wv[k] = I.bits[w0 + k];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) pc[k] = __popc(wv[k]);
-        // word level and the two levels above it, from registers
-        if (mine) {
-            for (uint32_t k = 0; k < 4u && threadIdx.x * 4u + k < TW; ++k) I.sums[W + w0 + k] = pc[k];
-            if (TW >= 2u) {
-                I.sums[(W + w0) >> 1] = pc[0] + pc[1];
-                if (TW >= 4u) {
-                    I.sums[((W + w0) >> 1) + 1] = pc[2] + pc[3];
-                    I.sums[(W + w0) >> 2] = pc[0] + pc[1] + pc[2] + pc[3];
-                }
-            }
-        }
-        const uint32_t tsum = pc[0] + pc[1] + pc[2] + pc[3];
-        // remaining levels of the tile in shared memory
-        uint32_t cnt = TW >= 4u ? TW / 4u : 1u;  // nodes at the current level
-        int lvl = TW >= 4u ? 2 : (TW >= 2u ? 1 : 0);
-        s_lvl[0][threadIdx.x] = mine ? tsum : 0u;
+        const uint32_t t = next_ticket(bt.bg, 2, &s_tile);
+        if (t >= bt.Twords) break;
+        uint32_t b, lt;
+        tile_begin(bt, bt.wtile_base, t, &s_b, &s_I, nullptr, nullptr, b, lt);
+        const Inst& I = s_I;
+        const uint32_t W = I.W;
+        const uint32_t TW = min(W, bt.tw);
+        const uint32_t nt = W / TW;
+        const uint32_t w = lt * TW + threadIdx.x;
+        const bool mine = threadIdx.x < TW;
+        const uint32_t wv = mine ? I.bits[w] : 0u;
+        const uint32_t pc = __popc(wv);
+        if (mine) I.sums[W + w] = pc;
+        // levels of the tile, from the word level up to the tile root
+        s_lvl[threadIdx.x] = pc;
         __syncthreads();
-        int cur = 0;
-        while (cnt > 1u) {
-            cnt >>= 1;
-            ++lvl;
+        uint32_t lvl = 1;
+        for (uint32_t cnt = TW >> 1; cnt >= 1u; cnt >>= 1, ++lvl) {
+            uint32_t v = 0;
+            if (threadIdx.x < cnt) v = s_lvl[2 * threadIdx.x] + s_lvl[2 * threadIdx.x + 1];
+            __syncthreads();
             if (threadIdx.x < cnt) {
-                const uint32_t v = s_lvl[cur][2 * threadIdx.x] + s_lvl[cur][2 * threadIdx.x + 1];
-                s_lvl[cur ^ 1][threadIdx.x] = v;
-                I.sums[((W + tile * TW) >> lvl) + threadIdx.x] = v;
+                s_lvl[threadIdx.x] = v;
+                I.sums[((W + lt * TW) >> lvl) + threadIdx.x] = v;
             }
-            cur ^= 1;
             __syncthreads();
         }
-        // compaction of the set bits
-        Pair tot;
-        const Pair tex = block_scan(Pair{0, tsum}, tot, s_warp);
-        const Pair ex = tile_prefix(status, tile, tot, I.g, &s_excl);
-        uint32_t r = ex.b + tex.b;
-        if (mine) {
-            for (uint32_t k = 0; k < 4u && threadIdx.x * 4u + k < TW; ++k) {
-                uint32_t m = wv[k];
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    I.live[r++] = (w0 + k) * 32u + (uint32_t)b;
-                    m &= m - 1u;
-                }
-            }
+        // in-tile exclusive prefix of popcounts
+        uint32_t inc = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += y;
         }
-        // last tile finished builds the top of the tree
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t x = lane < nw ? s_w[lane] : 0u;
+            uint32_t xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+                if (lane >= o) xi += y;
+            }
+            __syncwarp();
+            if (lane < nw) s_w[lane] = xi - x;
+            if (lane == nw - 1) s_w[nw] = xi;
+        }
+        __syncthreads();
+        const uint32_t tex = s_w[warp] + inc - pc;
+        const uint32_t tot = s_w[nw];
+        __syncthreads();
+        const Pair ex = tile_prefix(status, t, lt == 0, Pair{0, tot}, I.g, &s_excl);
+        // stage the slots of the set bits, then store them coalesced
+        uint32_t m = wv, r = tex;
+        while (m) {
+            s_live[r++] = w * 32u + (uint32_t)(__ffs(m) - 1);
+            m &= m - 1u;
+        }
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < tot; k += blockDim.x) I.live[ex.b + k] = s_live[k];
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) s_last = (atomicAdd(&I.g->done, 1u) == I.ntiles_words - 1u) ? 1u : 0u;
+        if (threadIdx.x == 0) s_last = (atomicAdd(&I.g->done, 1u) == nt - 1u) ? 1u : 0u;
         __syncthreads();
         if (s_last) {
             __threadfence();
-            for (uint32_t n = I.ntiles_words >> 1; n >= 1u; n >>= 1) {
-                for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
-                    const uint32_t a = __ldcg(I.sums + 2u * (n + k)), b = __ldcg(I.sums + 2u * (n + k) + 1u);
-                    I.sums[n + k] = a + b;
-                }
+            for (uint32_t n = nt >> 1; n >= 1u; n >>= 1) {
+                for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
+                    I.sums[n + k] = __ldcg(I.sums + 2u * (n + k)) + __ldcg(I.sums + 2u * (n + k) + 1u);
                 __threadfence();
                 __syncthreads();
             }
             if (threadIdx.x == 0) {
-                const uint32_t root = __ldcg(I.sums + 1);
-                I.g->stats[kStLiveAfter] = root;
+                I.g->stats[kStLiveAfter] = __ldcg(I.sums + 1);
                 I.g->done = 0;
             }
         }
+        __syncthreads();
     }
 }
 
@@ -863,8 +1112,7 @@ __global__ void __launch_bounds__(kThreads) k_cbt(Inst I) {
 // Root bisectors (Sec. 3.3 "Initialization") and the root vertex table
 // (Alg. 1, one FP64 centroid per face summed from its smallest halfedge).
 __global__ void __launch_bounds__(kThreads) k_init(Inst I, const int32_t* twin, const int32_t* next,
-                                                   const int32_t* prev, const int32_t* face,
-                                                   const double* hpos) {
+                                                   const int32_t* prev, const double* hpos) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nth = gridDim.x * blockDim.x;
     for (uint32_t w = tid; w < I.W; w += nth) {
@@ -904,7 +1152,6 @@ __global__ void __launch_bounds__(kThreads) k_init(Inst I, const int32_t* twin, 
         R[6] = __ddiv_rn(sx, dn);
         R[7] = __ddiv_rn(sy, dn);
         R[8] = __ddiv_rn(sz, dn);
-        (void)face;
     }
 }
 
@@ -926,59 +1173,73 @@ __global__ void __launch_bounds__(kThreads) k_leaves(Inst I, uint32_t* slots, ui
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_vertices(Inst I, FrameP fp, float* out, uint32_t cap) {
-    const uint32_t N = min(I.sums[1], cap);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const uint32_t s = I.live[i];
-        const uint64_t j = I.heap[s];
-        const int d = depth_of(j, I.ch);
-        const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
-        float r[9];
-        if (d < 0 || h >= I.H) {
-            set_err(I.g, kErrLink);
-            continue;
-        }
-        if (d <= 31) {
-            uint32_t W[9], Wp[9];
-            decode_weights<uint32_t>(j, d, W, Wp);
-            eval_vertices<uint32_t>(W, d, fp.precision, fp.shift, I.rel, h, r);
-        } else {
-            unsigned long long W[9], Wp[9];
-            decode_weights<unsigned long long>(j, d, W, Wp);
-            eval_vertices<unsigned long long>(W, d, fp.precision, fp.shift, I.rel, h, r);
-        }
-        float* o = out + 9ull * i;
+__device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uint32_t i, float* out) {
+    const uint32_t s = I.live[i];
+    const uint64_t j = I.heap[s];
+    const int d = depth_of(j, I.ch);
+    const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
+    float r[9];
+    if (d < 0 || h >= I.H) {
+        set_err(I.g, kErrLink);
+        return;
+    }
+    if (d <= 31) {
+        uint32_t W[9], Wp[9];
+        decode_weights<uint32_t>(j, d, W, Wp);
+        eval_vertices<uint32_t>(W, d, fp.precision, fp.shift, I.rel, h, r);
+    } else {
+        unsigned long long W[9], Wp[9];
+        decode_weights<unsigned long long>(j, d, W, Wp);
+        eval_vertices<unsigned long long>(W, d, fp.precision, fp.shift, I.rel, h, r);
+    }
+    float* o = out + 9ull * i;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) o[k] = r[k];
+    for (int k = 0; k < 9; ++k) o[k] = r[k];
+}
+
+// Vertices of the live bisectors of every instance with an output buffer,
+// over static tiles of its pool capacity (tiles past the live count exit).
+__global__ void __launch_bounds__(kThreads) k_vertices(BatchDev bt) {
+    __shared__ uint32_t s_b;
+    __shared__ Inst s_I;
+    __shared__ FrameP s_fp;
+    for (uint32_t t = blockIdx.x; t < bt.Titems; t += gridDim.x) {
+        uint32_t b, lt;
+        tile_begin(bt, bt.vtile_base, t, &s_b, &s_I, &s_fp, nullptr, b, lt);
+        const Inst& I = s_I;
+        const FrameP& fp = s_fp;
+        const uint32_t N = fp.vout ? min(I.sums[1], fp.vcap) : 0u;
+        if (lt * kTileItems < N) {
+#pragma unroll 1
+            for (int k = 0; k < kItemsPerThread; ++k) {
+                const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+                if (i < N) vertex_item(I, fp, i, fp.vout);
+            }
+        }
+        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------- launch
 
-void launch_prep(const Inst& I, const FrameP& fp, bool frame_start, int grid, cudaStream_t s) {
-    k_prep<<<grid, kThreads, 0, s>>>(I, fp, frame_start ? 1 : 0);
+void launch_prep(const BatchDev& bt, bool frame_start, int grid, cudaStream_t s) {
+    k_prep<<<grid, kThreads, 0, s>>>(bt, frame_start ? 1 : 0);
 }
-void launch_classify(const Inst& I, const FrameP& fp, int grid, cudaStream_t s) {
-    k_classify<<<grid, kThreads, 0, s>>>(I, fp);
-}
-void launch_gate(const Inst& I, const FrameP& fp, int grid, cudaStream_t s) {
-    k_gate<<<grid, kThreads, 0, s>>>(I, fp);
-}
-void launch_scatter(const Inst& I, int grid, cudaStream_t s) { k_scatter<<<grid, kThreads, 0, s>>>(I); }
-void launch_alloc(const Inst& I, int grid, cudaStream_t s) { k_alloc<<<grid, kThreads, 0, s>>>(I); }
-void launch_free(const Inst& I, int grid, cudaStream_t s) { k_free<<<grid, kThreads, 0, s>>>(I); }
-void launch_fill(const Inst& I, int grid, cudaStream_t s) { k_fill<<<grid, kThreads, 0, s>>>(I); }
-void launch_cbt(const Inst& I, int grid, cudaStream_t s) { k_cbt<<<grid, kThreads, 0, s>>>(I); }
+void launch_classify(const BatchDev& bt, int grid, cudaStream_t s) { k_classify<<<grid, kThreads, 0, s>>>(bt); }
+void launch_gate(const BatchDev& bt, int grid, cudaStream_t s) { k_gate<<<grid, kThreads, 0, s>>>(bt); }
+void launch_scatter(const BatchDev& bt, int grid, cudaStream_t s) { k_scatter<<<grid, kThreads, 0, s>>>(bt); }
+void launch_alloc(const BatchDev& bt, int grid, cudaStream_t s) { k_alloc<<<grid, kThreads, 0, s>>>(bt); }
+void launch_free(const BatchDev& bt, int grid, cudaStream_t s) { k_free<<<grid, bt.tw, 0, s>>>(bt); }
+void launch_fill(const BatchDev& bt, int grid, cudaStream_t s) { k_fill<<<grid, kThreads, 0, s>>>(bt); }
+void launch_cbt(const BatchDev& bt, int grid, cudaStream_t s) { k_cbt<<<grid, bt.tw, 0, s>>>(bt); }
+void launch_vertices(const BatchDev& bt, int grid, cudaStream_t s) { k_vertices<<<grid, kThreads, 0, s>>>(bt); }
 void launch_init(const Inst& I, const int32_t* twin, const int32_t* next, const int32_t* prev,
-                 const int32_t* face, const double* hpos, int grid, cudaStream_t s) {
-    k_init<<<grid, kThreads, 0, s>>>(I, twin, next, prev, face, hpos);
+                 const double* hpos, int grid, cudaStream_t s) {
+    k_init<<<grid, kThreads, 0, s>>>(I, twin, next, prev, hpos);
 }
 void launch_leaves(const Inst& I, uint32_t* slots, uint64_t* heap, uint32_t* links, int grid,
                    cudaStream_t s) {
     k_leaves<<<grid, kThreads, 0, s>>>(I, slots, heap, links);
-}
-void launch_vertices(const Inst& I, const FrameP& fp, float* out, uint32_t cap, int grid, cudaStream_t s) {
-    k_vertices<<<grid, kThreads, 0, s>>>(I, fp, out, cap);
 }
 
 }  // namespace cbtgpu
