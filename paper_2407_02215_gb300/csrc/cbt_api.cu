@@ -267,7 +267,7 @@ uint32_t enqueue_kernels(const BatchDev& bt, int sms, uint32_t grid_mult, bool v
     const int prep = static_cast<int>(std::max(1u, std::min<uint32_t>((prep_n + kThreads - 1u) / kThreads,
                                                                      static_cast<uint32_t>(sms) * 4u)));
     const int items = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * grid_mult)));
-    const int scans = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * 2u)));
+    const int scans = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * 8u)));
     const int words = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Twords, static_cast<uint32_t>(sms) * 4u)));
     uint32_t k = 0;
     auto mark = [&]() {

@@ -37,7 +37,8 @@ constexpr uint32_t kMergeWish = 1u << 5;
 constexpr uint32_t kMergeGrant = 1u << 6;
 constexpr uint32_t kDepthOdd = 1u << 7;
 constexpr uint32_t kHeapOdd = 1u << 8;
-constexpr uint32_t kCand = 1u << 9;  // smallest member of a mergeable group (members in grp[i])
+constexpr uint32_t kCand = 1u << 9;    // smallest member of a mergeable group (members in grp[i])
+constexpr uint32_t kGrpMin = 1u << 10; // smallest member of a merge group whose members are in grp[i]
 
 // Edge indices of a bisector: Twin (v0,v1), Next (v1,v2), Prev (v2,v0).
 constexpr int kT = 0, kNe = 1, kPe = 2;

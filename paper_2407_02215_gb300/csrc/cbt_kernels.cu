@@ -277,6 +277,52 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
     }
 }
 
+// ----------------------------------------------------------- merge groups
+
+struct Group {
+    uint32_t m[4];
+    uint64_t j[4];
+    int n, imin, np;
+};
+
+// Alg. 4 on the frame-start state. Members: m[0] = s1, m[1] its sibling,
+// m[2] the bisector across the outer half of the refinement edge, m[3] its
+// sibling.
+__device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
+    const uint64_t j1 = I.heap[s1];
+    if (depth_of(j1, I.ch) < 1) return false;
+    const uint4 r1 = I.nb[s1];
+    const bool bit = j1 & 1ull;
+    const uint32_t s2 = bit ? r1.z : r1.y;
+    const uint32_t s3 = bit ? r1.y : r1.z;
+    if (s2 == kNull || bad_slot(I, s2, kErrLink)) return false;
+    if (s3 != kNull && bad_slot(I, s3, kErrLink)) return false;
+    const uint64_t j2 = I.heap[s2];
+    if ((j2 >> 1) != (j1 >> 1)) return false;
+    g.m[0] = s1; g.j[0] = j1;
+    g.m[1] = s2; g.j[1] = j2;
+    g.m[2] = g.m[3] = kNull;
+    g.n = 2;
+    g.np = 1;
+    if (s3 != kNull) {
+        const uint64_t j3 = I.heap[s3];
+        if (bitlen64(j3) != bitlen64(j1) || (j3 >> 1) == (j1 >> 1)) return false;
+        const uint4 r3 = I.nb[s3];
+        const uint32_t s4 = bit ? r3.y : r3.z;
+        if (s4 == kNull || bad_slot(I, s4, kErrLink)) return false;
+        const uint64_t j4 = I.heap[s4];
+        if ((j4 >> 1) != (j3 >> 1)) return false;
+        g.m[2] = s3; g.j[2] = j3;
+        g.m[3] = s4; g.j[3] = j4;
+        g.n = 4;
+        g.np = 2;
+    }
+    g.imin = 0;
+    for (int k = 1; k < g.n; ++k)
+        if (g.j[k] < g.j[g.imin]) g.imin = k;
+    return true;
+}
+
 // -------------------------------------------------------------- classify
 
 template <typename T>
@@ -334,9 +380,7 @@ __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool scatter) {
 }
 
 __device__ __forceinline__ void classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
-                                              uint32_t* s_cnt) {
-    const uint32_t s = I.live[i];
-    const uint64_t j = I.heap[s];
+                                              uint32_t s, uint64_t j, uint32_t* s_cnt) {
     const int d = depth_of(j, I.ch);
     const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
     bool split = false, merge = false;
@@ -368,8 +412,17 @@ __device__ __forceinline__ void classify_item(const Inst& I, const FrameP& fp, u
             merge = !split && d >= 1 && in_sorted(fp.merge_list, fp.n_merge, j);
             break;
     }
-    const uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
-                         ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
+    uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
+                   ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
+    // the smallest member of an Alg. 4 group (an even heap ID) records the
+    // group's members for the gate, the allocation and the fill
+    if (merge && !(j & 1ull)) {
+        Group g;
+        if (find_group(I, s, g) && g.imin == 0) {
+            I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
+            cmd |= kGrpMin;
+        }
+    }
     *cmd_ptr(I, s) = cmd;
     uint32_t cost = 0;
     if (split) cost = fp.gate == 1 ? 3u * (uint32_t)d + 4u : chain_walk(I, s, d, false);
@@ -377,7 +430,7 @@ __device__ __forceinline__ void classify_item(const Inst& I, const FrameP& fp, u
     count_stat(s_cnt, 0, split);
 }
 
-__global__ void __launch_bounds__(kThreads) k_classify(BatchDev bt) {
+__global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev bt) {
     __shared__ uint32_t s_b;
     __shared__ Inst s_I;
     __shared__ FrameP s_fp;
@@ -390,61 +443,28 @@ __global__ void __launch_bounds__(kThreads) k_classify(BatchDev bt) {
         const FrameP& fp = s_fp;
         const uint32_t N = I.g->N;
         const uint64_t key = splitmix64(((uint64_t)fp.seed << 32) | (uint64_t)fp.frame);
+        // issue the slot and heap-ID loads of the thread's items first
+        uint32_t sl[kItemsPerThread];
+        uint64_t hj[kItemsPerThread];
+#pragma unroll
+        for (int k = 0; k < kItemsPerThread; ++k) {
+            const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+            sl[k] = i < N ? I.live[i] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kItemsPerThread; ++k) {
+            const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+            hj[k] = i < N ? I.heap[sl[k]] : 0ull;
+        }
 #pragma unroll 1
         for (int k = 0; k < kItemsPerThread; ++k) {
             const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
-            if (i < N) classify_item(I, fp, key, i, s_cnt);
+            if (i < N) classify_item(I, fp, key, i, sl[k], hj[k], s_cnt);
         }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStSplitWishes);
         __syncthreads();
     }
-}
-
-// ----------------------------------------------------------- merge groups
-
-struct Group {
-    uint32_t m[4];
-    uint64_t j[4];
-    int n, imin, np;
-};
-
-// Alg. 4 on the frame-start state. Members: m[0] = s1, m[1] its sibling,
-// m[2] the bisector across the outer half of the refinement edge, m[3] its
-// sibling.
-__device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
-    const uint64_t j1 = I.heap[s1];
-    if (depth_of(j1, I.ch) < 1) return false;
-    const uint4 r1 = I.nb[s1];
-    const bool bit = j1 & 1ull;
-    const uint32_t s2 = bit ? r1.z : r1.y;
-    const uint32_t s3 = bit ? r1.y : r1.z;
-    if (s2 == kNull || bad_slot(I, s2, kErrLink)) return false;
-    if (s3 != kNull && bad_slot(I, s3, kErrLink)) return false;
-    const uint64_t j2 = I.heap[s2];
-    if ((j2 >> 1) != (j1 >> 1)) return false;
-    g.m[0] = s1; g.j[0] = j1;
-    g.m[1] = s2; g.j[1] = j2;
-    g.m[2] = g.m[3] = kNull;
-    g.n = 2;
-    g.np = 1;
-    if (s3 != kNull) {
-        const uint64_t j3 = I.heap[s3];
-        if (bitlen64(j3) != bitlen64(j1) || (j3 >> 1) == (j1 >> 1)) return false;
-        const uint4 r3 = I.nb[s3];
-        const uint32_t s4 = bit ? r3.y : r3.z;
-        if (s4 == kNull || bad_slot(I, s4, kErrLink)) return false;
-        const uint64_t j4 = I.heap[s4];
-        if ((j4 >> 1) != (j3 >> 1)) return false;
-        g.m[2] = s3; g.j[2] = j3;
-        g.m[3] = s4; g.j[3] = j4;
-        g.n = 4;
-        g.np = 2;
-    }
-    g.imin = 0;
-    for (int k = 1; k < g.n; ++k)
-        if (g.j[k] < g.j[g.imin]) g.imin = k;
-    return true;
 }
 
 // ------------------------------------------------------------------ gate
@@ -488,16 +508,14 @@ __global__ void __launch_bounds__(kThreads) k_gate(BatchDev bt) {
                 slot[k] = s;
                 const uint32_t cmd = *cmd_ptr(I, s);
                 uint32_t mc = 0;
-                if ((cmd & kMergeWish) && !(cmd & kHeapOdd)) {
-                    Group g;
-                    if (find_group(I, s, g) && g.imin == 0) {
-                        bool all = true;
-                        for (int m = 1; m < g.n; ++m) all = all && (*cmd_ptr(I, g.m[m]) & kMergeWish);
-                        if (all) {
-                            mc = gate == 1 ? 2u : (uint32_t)g.np;
-                            I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
-                        }
-                    }
+                if (cmd & kGrpMin) {
+                    const uint4 m = I.grp[i];
+                    const uint32_t ms[3] = {m.y, m.z, m.w};
+                    bool all = true;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (ms[q] != kNull) all = all && (*cmd_ptr(I, ms[q]) & kMergeWish);
+                    if (all) mc = gate == 1 ? 2u : (m.z == kNull ? 1u : 2u);
                 }
                 v[k] = Pair{mc, I.scan[i]};
                 loc = padd(loc, v[k]);
@@ -1173,9 +1191,7 @@ __global__ void __launch_bounds__(kThreads) k_leaves(Inst I, uint32_t* slots, ui
     }
 }
 
-__device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uint32_t i, float* out) {
-    const uint32_t s = I.live[i];
-    const uint64_t j = I.heap[s];
+__device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uint32_t i, uint64_t j, float* out) {
     const int d = depth_of(j, I.ch);
     const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
     float r[9];
@@ -1199,7 +1215,7 @@ __device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uin
 
 // Vertices of the live bisectors of every instance with an output buffer,
 // over static tiles of its pool capacity (tiles past the live count exit).
-__global__ void __launch_bounds__(kThreads) k_vertices(BatchDev bt) {
+__global__ void __launch_bounds__(kThreads, 3) k_vertices(BatchDev bt) {
     __shared__ uint32_t s_b;
     __shared__ Inst s_I;
     __shared__ FrameP s_fp;
@@ -1210,10 +1226,16 @@ __global__ void __launch_bounds__(kThreads) k_vertices(BatchDev bt) {
         const FrameP& fp = s_fp;
         const uint32_t N = fp.vout ? min(I.sums[1], fp.vcap) : 0u;
         if (lt * kTileItems < N) {
+            uint64_t hj[kItemsPerThread];
+#pragma unroll
+            for (int k = 0; k < kItemsPerThread; ++k) {
+                const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+                hj[k] = i < N ? I.heap[I.live[i]] : 0ull;
+            }
 #pragma unroll 1
             for (int k = 0; k < kItemsPerThread; ++k) {
                 const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
-                if (i < N) vertex_item(I, fp, i, fp.vout);
+                if (i < N) vertex_item(I, fp, i, hj[k], fp.vout);
             }
         }
         __syncthreads();
