@@ -38,13 +38,13 @@ uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems;
 
 // Per-instance arrays.
 struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, root64, rel, batch, total;
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, root64, rel, batch, total;
     uint32_t cap, W, ch;
 };
 
 // A batch region for instances with the given pool sizes and halfedge counts.
 struct BatchLayout {
-    size_t inst, fps, bg, tile_base, wtile_base, vtile_base, rel_base, status, total;
+    size_t inst, fps, bg, tile_base, ctile_base, wtile_base, vtile_base, rel_base, status, total;
     uint32_t Titems, TwordsMax, Trel;
 };
 
@@ -65,6 +65,7 @@ BatchLayout batch_layout(uint32_t n, const uint32_t* cap, const uint32_t* W, con
     L.fps = take(sizeof(FrameP) * n);
     L.bg = take(sizeof(BatchGlobals));
     L.tile_base = take(4u * (n + 1u));
+    L.ctile_base = take(4u * (n + 1u));
     L.wtile_base = take(4u * (n + 1u));
     L.vtile_base = take(4u * (n + 1u));
     L.rel_base = take(4u * (n + 1u));
@@ -96,6 +97,7 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.freel = take(4u * cap);
     L.scan = take(4u * cap);
     L.grp = take(16u * cap);
+    L.chg = take(4u * cap);
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
     const uint32_t Hh = static_cast<uint32_t>(H);
@@ -218,6 +220,7 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
     d.fps = nullptr;
     d.B = n;
     d.tile_base = reinterpret_cast<uint32_t*>(region + B->L.tile_base);
+    d.ctile_base = reinterpret_cast<uint32_t*>(region + B->L.ctile_base);
     d.wtile_base = reinterpret_cast<const uint32_t*>(region + B->L.wtile_base);
     d.vtile_base = reinterpret_cast<const uint32_t*>(region + B->L.vtile_base);
     d.rel_base = reinterpret_cast<const uint32_t*>(region + B->L.rel_base);
@@ -451,6 +454,7 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     I.freel = reinterpret_cast<uint32_t*>(b + L.freel);
     I.scan = reinterpret_cast<uint32_t*>(b + L.scan);
     I.grp = reinterpret_cast<uint4*>(b + L.grp);
+    I.chg = reinterpret_cast<uint32_t*>(b + L.chg);
     I.root64 = reinterpret_cast<double*>(b + L.root64);
     I.rel = b + L.rel;
     I.cap = L.cap;
@@ -740,8 +744,8 @@ struct ServerSlot {
 };
 
 struct TickLayout {
-    size_t inst, fps, wbase, vbase, rbase, block;  // packed block (copied per tick)
-    size_t bg, tile_base, nout, status, total;      // rest of the device region
+    size_t inst, fps, wbase, vbase, rbase, block;         // packed block (copied per tick)
+    size_t bg, tile_base, ctile_base, nout, status, total;  // rest of the device region
 };
 
 TickLayout tick_layout(uint32_t k, uint32_t n_max, uint32_t status_words) {
@@ -773,6 +777,7 @@ TickLayout tick_layout(uint32_t k, uint32_t n_max, uint32_t status_words) {
     mtake(4u * (n_max + 1u));
     L.bg = mtake(sizeof(BatchGlobals));
     L.tile_base = mtake(4u * (n_max + 1u));
+    L.ctile_base = mtake(4u * (n_max + 1u));
     L.nout = mtake(4u * n_max);
     L.status = mtake(8u * static_cast<size_t>(status_words));
     L.total = moff;
@@ -885,6 +890,7 @@ extern "C" int cbt_server_submit(cbt_server* sv, const int32_t* idx, const cbt_f
     bt.B = kk;
     bt.tw = sv->tw;
     bt.tile_base = reinterpret_cast<uint32_t*>(S.dev + L.tile_base);
+    bt.ctile_base = reinterpret_cast<uint32_t*>(S.dev + L.ctile_base);
     bt.wtile_base = reinterpret_cast<const uint32_t*>(S.dev + L.wbase);
     bt.vtile_base = reinterpret_cast<const uint32_t*>(S.dev + L.vbase);
     bt.rel_base = reinterpret_cast<const uint32_t*>(S.dev + L.rbase);

@@ -66,7 +66,8 @@ struct Globals {
     uint32_t err;       // sticky error bits
     uint32_t done;      // finished word tiles of the reduction
     uint32_t ntiles;    // item tiles of this frame: ceil(N / kTileItems)
-    uint32_t reserved[3];
+    uint32_t C;         // changed bisectors of this frame (split, or smallest member of a merge)
+    uint32_t reserved[2];
     uint32_t stats[kStCount];
     uint32_t pad[64 - 10 - kStCount];
 };
@@ -83,6 +84,7 @@ struct Inst {
     uint32_t* freel;
     uint32_t* scan;
     uint4* grp;  // per live index: members of the group whose smallest member it is
+    uint32_t* chg;  // live indices of the changed bisectors, in ascending slot order
     double* root64;
     void* rel;
     Globals* g;
@@ -110,8 +112,9 @@ struct FrameP {
 // Launch-wide counters of one batch (256 bytes).
 struct BatchGlobals {
     uint32_t tickets[8];
-    uint32_t total_tiles;  // item tiles of this frame over all instances
-    uint32_t pad[64 - 9];
+    uint32_t total_tiles;   // item tiles of this frame over all instances
+    uint32_t total_ctiles;  // tiles of changed bisectors (kThreads each) over all instances
+    uint32_t pad[64 - 10];
 };
 static_assert(sizeof(BatchGlobals) == 256, "BatchGlobals must be 256 bytes");
 
@@ -126,6 +129,7 @@ struct BatchDev {
     uint32_t B;
     uint32_t tw;          // word-tile size of the reduction and free-list kernels
     uint32_t* tile_base;  // [B+1]
+    uint32_t* ctile_base; // [B+1] tiles of kThreads changed bisectors, per frame
     const uint32_t* wtile_base;  // [B+1] word tiles, min(W_b, tw) words each
     const uint32_t* vtile_base;  // [B+1] ceil(cap_b / kTileItems)
     const uint32_t* rel_base;    // [B+1] 9 * H_b
@@ -169,34 +173,91 @@ __device__ __forceinline__ void set_err(Globals* g, uint32_t e) { atomicOr(&g->e
 
 // Integer form of Alg. 2 evaluated from the first split down: with W the
 // weights over 2^k after k levels, a 0 bit maps the rows (r0, r1, r2) to
-// (2 r0, 2 r2, r0 + r1) and a 1 bit to (2 r2, 2 r1, r0 + r1) (Eq. 1 times 2).
-// W = 2^d M exactly while entries fit T (T = u32 for d <= 31).
+// (2 r0, 2 r2, r0 + r1) and a 1 bit to (2 r2, 2 r1, r0 + r1) (Eq. 1 times 2),
+// i.e. W <- T_b W with T_0 = 2 M_0 and T_1 = 2 M_1. Six levels at once are
+// W <- P_c W with P_c = T_{c0} T_{c1} ... T_{c5} for the six path bits c
+// (most significant applied first), precomputed below for all 64 c; every
+// entry of P_c is at most 64. W = 2^d M exactly while entries fit T (T = u32
+// for d <= 31).
+struct DecTable {
+    uint32_t p[64][9];
+};
+
+constexpr DecTable make_dec6() {
+    DecTable t{};
+    for (int c = 0; c < 64; ++c) {
+        uint32_t m[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        for (int k = 5; k >= 0; --k) {
+            const int b = (c >> k) & 1;
+            uint32_t n[9] = {};
+            for (int col = 0; col < 3; ++col) {
+                n[6 + col] = m[col] + m[3 + col];
+                n[col] = 2u * (b ? m[6 + col] : m[col]);
+                n[3 + col] = 2u * (b ? m[3 + col] : m[6 + col]);
+            }
+            for (int e = 0; e < 9; ++e) m[e] = n[e];
+        }
+        for (int e = 0; e < 9; ++e) t.p[c][e] = m[e];
+    }
+    return t;
+}
+
+__constant__ DecTable c_dec6 = make_dec6();
+
+// Copies the six-level table into shared memory (call with the whole block,
+// then __syncthreads()).
+__device__ __forceinline__ void load_dec6(uint32_t* s_tab) {
+    const uint32_t* src = &c_dec6.p[0][0];
+    for (uint32_t k = threadIdx.x; k < 64u * 9u; k += blockDim.x) s_tab[k] = src[k];
+}
+
 template <typename T>
-__device__ __forceinline__ void decode_weights(uint64_t j, int d, T W[9], T Wp[9]) {
-    T a[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-#pragma unroll 1
-    for (int lvl = d - 1; lvl >= 0; --lvl) {
-        if (lvl == 0) {
+__device__ __forceinline__ void dec_step(T a[9], bool b) {
+    T n[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) Wp[k] = a[k];
-        }
-        const bool b = (j >> lvl) & 1ull;
-        T n[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            n[6 + c] = a[c] + a[3 + c];
-            n[c] = (b ? a[6 + c] : a[c]) << 1;
-            n[3 + c] = (b ? a[3 + c] : a[6 + c]) << 1;
-        }
-#pragma unroll
-        for (int k = 0; k < 9; ++k) a[k] = n[k];
+    for (int c = 0; c < 3; ++c) {
+        n[6 + c] = a[c] + a[3 + c];
+        n[c] = (b ? a[6 + c] : a[c]) << 1;
+        n[3 + c] = (b ? a[3 + c] : a[6 + c]) << 1;
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) W[k] = a[k];
-    if (d == 0) {
+    for (int k = 0; k < 9; ++k) a[k] = n[k];
+}
+
+template <typename T>
+__device__ __forceinline__ void dec_chunk(T a[9], const uint32_t* P) {
+    T n[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const T p0 = P[3 * r], p1 = P[3 * r + 1], p2 = P[3 * r + 2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) n[3 * r + c] = p0 * a[c] + p1 * a[3 + c] + p2 * a[6 + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a[k] = n[k];
+}
+
+// W = weights of bisector j at depth d, Wp = those of its parent (d >= 1);
+// tab = the six-level table in shared memory.
+template <typename T>
+__device__ __forceinline__ void decode_weights(uint64_t j, int d, T W[9], T Wp[9], const uint32_t* tab) {
+    T a[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (d >= 1) {
+        int lvl = d - 1;  // path bit applied next; the parent covers bits d-1 .. 1
+        const int rem = (d - 1) % 6;
+#pragma unroll 1
+        for (int k = 0; k < rem; ++k, --lvl) dec_step<T>(a, (j >> lvl) & 1ull);
+#pragma unroll 1
+        for (; lvl >= 6; lvl -= 6) dec_chunk<T>(a, tab + 9u * (uint32_t)((j >> (lvl - 5)) & 63ull));
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Wp[k] = a[k];
+        dec_step<T>(a, j & 1ull);
+    } else {
 #pragma unroll
         for (int k = 0; k < 9; ++k) Wp[k] = a[k];
     }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) W[k] = a[k];
 }
 
 // Correctly rounded signed 128-bit integer -> float: shift down to 63

@@ -327,9 +327,9 @@ __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
 
 template <typename T>
 __device__ __forceinline__ void lod_wishes(const Inst& I, const FrameP& fp, uint64_t j, int d,
-                                           uint32_t h, bool& split, bool& merge) {
+                                           uint32_t h, const uint32_t* tab, bool& split, bool& merge) {
     T W[9], Wp[9];
-    decode_weights<T>(j, d, W, Wp);
+    decode_weights<T>(j, d, W, Wp, tab);
     float r[9];
     eval_vertices<T>(W, d, fp.precision, fp.shift, I.rel, h, r);
     split = lod_test(r, fp) == 3u && d < (int)I.max_depth;
@@ -380,7 +380,7 @@ __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool scatter) {
 }
 
 __device__ __forceinline__ void classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
-                                              uint32_t s, uint64_t j, uint32_t* s_cnt) {
+                                              uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt) {
     const int d = depth_of(j, I.ch);
     const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
     bool split = false, merge = false;
@@ -393,9 +393,9 @@ __device__ __forceinline__ void classify_item(const Inst& I, const FrameP& fp, u
     switch (fp.mode) {
         case 0:
             if (d <= 31)
-                lod_wishes<uint32_t>(I, fp, j, d, h, split, merge);
+                lod_wishes<uint32_t>(I, fp, j, d, h, tab, split, merge);
             else
-                lod_wishes<unsigned long long>(I, fp, j, d, h, split, merge);
+                lod_wishes<unsigned long long>(I, fp, j, d, h, tab, split, merge);
             break;
         case 1:
             split = d < (int)I.max_depth;
@@ -435,6 +435,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev bt) {
     __shared__ Inst s_I;
     __shared__ FrameP s_fp;
     __shared__ uint32_t s_cnt[kBlockStats];
+    __shared__ uint32_t s_tab[64 * 9];
+    load_dec6(s_tab);
     const uint32_t T = ld_volatile(&bt.bg->total_tiles);
     for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
         uint32_t b, lt;
@@ -459,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev bt) {
 #pragma unroll 1
         for (int k = 0; k < kItemsPerThread; ++k) {
             const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
-            if (i < N) classify_item(I, fp, key, i, sl[k], hj[k], s_cnt);
+            if (i < N) classify_item(I, fp, key, i, sl[k], hj[k], s_tab, s_cnt);
         }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStSplitWishes);
@@ -649,17 +651,19 @@ __global__ void __launch_bounds__(kThreads) k_alloc(BatchDev bt) {
                     na[k] = m.z == kNull ? 1u : 2u;
                 }
             }
-            loc = padd(loc, Pair{0, na[k]});
+            loc = padd(loc, Pair{fate[k] ? 1u : 0u, na[k]});
         }
         Pair tot;
         const Pair tex = block_scan(loc, tot, s_warp);
         const Pair ex = tile_prefix(status, t, lt == 0, tot, I.g, &s_excl);
         uint32_t run = ex.b + tex.b;
+        uint32_t crun = ex.a + tex.a;
 #pragma unroll
         for (int k = 0; k < kItemsPerThread; ++k) {
             const uint32_t i = base + k;
             if (i >= N) continue;
             const uint32_t s = slot[k];
+            if (fate[k]) I.chg[crun++] = i;
             if (fate[k] == 1) {
                 *dest_ptr(I, s) = run;
             } else if (fate[k] == 3) {
@@ -678,6 +682,7 @@ __global__ void __launch_bounds__(kThreads) k_alloc(BatchDev bt) {
         }
         if (lt == I.g->ntiles - 1u && threadIdx.x == kThreads - 1) {
             I.g->A = run;
+            I.g->C = crun;
             I.g->stats[kStAllocated] = run;
             if (run > I.g->F) set_err(I.g, kErrOverflow);
         }
@@ -693,10 +698,49 @@ __global__ void __launch_bounds__(kThreads) k_alloc(BatchDev bt) {
 // (Alg. 8 for the first A ranks at once): each tile of words (one word per
 // thread) finds its zero offset from the sum tree and emits its zeros.
 __global__ void __launch_bounds__(kMaxTileWords) k_free(BatchDev bt) {
-    __shared__ uint32_t s_b;
+    __shared__ uint32_t s_b, s_carry;
     __shared__ uint32_t s_w[kMaxTileWords / 32 + 1];
     __shared__ Inst s_I;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (blockIdx.x == 0) {
+        // tiles of the changed-bisector lists, for k_fill
+        if (threadIdx.x == 0) s_carry = 0;
+        __syncthreads();
+        for (uint32_t b0 = 0; b0 < bt.B; b0 += blockDim.x) {
+            const uint32_t b = b0 + threadIdx.x;
+            const uint32_t n = b < bt.B ? (ld_volatile(&bt.inst[b].g->C) + kThreads - 1u) / kThreads : 0u;
+            uint32_t inc = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_w[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t x = lane < nw ? s_w[lane] : 0u;
+                uint32_t xi = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+                    if (lane >= o) xi += y;
+                }
+                __syncwarp();
+                if (lane < nw) s_w[lane] = xi - x;
+                if (lane == nw - 1) s_w[nw] = xi;
+            }
+            __syncthreads();
+            if (b < bt.B) bt.ctile_base[b] = s_carry + s_w[warp] + inc - n;
+            __syncthreads();
+            if (threadIdx.x == 0) s_carry += s_w[nw];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            bt.ctile_base[bt.B] = s_carry;
+            bt.bg->total_ctiles = s_carry;
+        }
+        __syncthreads();
+    }
     for (uint32_t t = blockIdx.x; t < bt.Twords; t += gridDim.x) {
         uint32_t b, lt;
         tile_begin(bt, bt.wtile_base, t, &s_b, &s_I, nullptr, nullptr, b, lt);
@@ -985,40 +1029,36 @@ __device__ void fill_merge(const Inst& I, uint32_t dest, const uint4 m, uint32_t
 }
 
 // FillNewBlocks + UpdateNeighbors + UpdateBitfield for the changed
-// bisectors. The changed bisectors of a tile are packed in shared memory
-// first, so that whole warps build families.
+// bisectors, one per thread over the instance's compacted list (written in
+// ascending slot order by k_alloc): a split bisector clears its bit and
+// writes its family; the smallest member of a merge group clears its
+// members' bits and writes the parents.
 __global__ void __launch_bounds__(kThreads) k_fill(BatchDev bt) {
-    __shared__ uint32_t s_b, s_n;
-    __shared__ uint32_t s_item[kTileItems];
+    __shared__ uint32_t s_b;
     __shared__ Inst s_I;
     __shared__ uint32_t s_cnt[kBlockStats];
-    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    const uint32_t T = ld_volatile(&bt.bg->total_ctiles);
     for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
         uint32_t b, lt;
-        if (threadIdx.x == 0) s_n = 0;
-        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
+        tile_begin(bt, bt.ctile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
         const Inst& I = s_I;
-        const uint32_t N = I.g->N;
-#pragma unroll
-        for (int k = 0; k < kItemsPerThread; ++k) {
-            const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
-            if (i >= N) continue;
-            const uint32_t s = I.live[i];
-            const uint32_t cmd = *cmd_ptr(I, s);
-            if (!(cmd & (kSplitMask | kMerged))) continue;
-            clear_bit(I, s);
-            if ((cmd & kSplitMask) || ((cmd & kCand) && (cmd & kMerged))) s_item[atomicAdd(&s_n, 1u)] = i;
-        }
-        __syncthreads();
-        const uint32_t n = s_n;
-        for (uint32_t k = threadIdx.x; k < n; k += kThreads) {
-            const uint32_t i = s_item[k];
+        const uint32_t C = I.g->C;
+        const uint32_t k = lt * kThreads + threadIdx.x;
+        if (k < C) {
+            const uint32_t i = I.chg[k];
             const uint32_t s = I.live[i];
             const uint2 c = I.cd[s];
-            if (c.x & kSplitMask)
+            if (c.x & kSplitMask) {
+                clear_bit(I, s);
                 fill_split(I, s, c.x, c.y, s_cnt);
-            else
-                fill_merge(I, c.y, I.grp[i], s_cnt);
+            } else {
+                const uint4 m = I.grp[i];
+                const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) clear_bit(I, ms[q]);
+                fill_merge(I, c.y, m, s_cnt);
+            }
         }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStRelinked);
@@ -1191,7 +1231,8 @@ __global__ void __launch_bounds__(kThreads) k_leaves(Inst I, uint32_t* slots, ui
     }
 }
 
-__device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uint32_t i, uint64_t j, float* out) {
+__device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uint32_t i, uint64_t j,
+                                            const uint32_t* tab, float* out) {
     const int d = depth_of(j, I.ch);
     const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
     float r[9];
@@ -1201,11 +1242,11 @@ __device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uin
     }
     if (d <= 31) {
         uint32_t W[9], Wp[9];
-        decode_weights<uint32_t>(j, d, W, Wp);
+        decode_weights<uint32_t>(j, d, W, Wp, tab);
         eval_vertices<uint32_t>(W, d, fp.precision, fp.shift, I.rel, h, r);
     } else {
         unsigned long long W[9], Wp[9];
-        decode_weights<unsigned long long>(j, d, W, Wp);
+        decode_weights<unsigned long long>(j, d, W, Wp, tab);
         eval_vertices<unsigned long long>(W, d, fp.precision, fp.shift, I.rel, h, r);
     }
     float* o = out + 9ull * i;
@@ -1219,6 +1260,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_vertices(BatchDev bt) {
     __shared__ uint32_t s_b;
     __shared__ Inst s_I;
     __shared__ FrameP s_fp;
+    __shared__ uint32_t s_tab[64 * 9];
+    load_dec6(s_tab);
     for (uint32_t t = blockIdx.x; t < bt.Titems; t += gridDim.x) {
         uint32_t b, lt;
         tile_begin(bt, bt.vtile_base, t, &s_b, &s_I, &s_fp, nullptr, b, lt);
@@ -1235,7 +1278,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_vertices(BatchDev bt) {
 #pragma unroll 1
             for (int k = 0; k < kItemsPerThread; ++k) {
                 const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
-                if (i < N) vertex_item(I, fp, i, hj[k], fp.vout);
+                if (i < N) vertex_item(I, fp, i, hj[k], s_tab, fp.vout);
             }
         }
         __syncthreads();
