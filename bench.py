@@ -72,12 +72,14 @@ def algorithmic_bytes(kernel: str, st: dict, cap: int) -> float:
     Wd = max(1, cap // 32)
     N2 = st["live_after"]
     return {
-        # live slot, heap ID in; command word and cost out; the twin record
-        # (links + heap) of every split wish
-        "classify": 20.0 * N + 24.0 * SW,
-        # live slot, command, cost in; running total out; group members'
-        # records (3 x links + heap + command) per merge candidate
-        "gate": 16.0 * N + 3 * 28.0 * MC,
+        # live slot, heap ID in; command word and cost out
+        "classify": 20.0 * N,
+        # live slot and command in; per split wish the twin record (links +
+        # heap) and its cost out; per merge candidate three member records
+        "walk": 8.0 * N + 28.0 * SW + 3 * 24.0 * MC,
+        # live slot, command, cost in; running total out; the members'
+        # command words per merge candidate
+        "gate": 16.0 * N + 3 * 8.0 * MC,
         # live slot, command, running total; command OR on chain members
         "scatter": 12.0 * N + 28.0 * SW,
         # live slot and command in, destination out for changed bisectors

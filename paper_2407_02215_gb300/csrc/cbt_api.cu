@@ -21,8 +21,8 @@ using namespace cbtgpu;
 
 namespace {
 
-constexpr int kNumKernels = 9;
-const char* const kKernelNames[kNumKernels] = {"prep", "classify", "gate", "scatter", "alloc",
+constexpr int kNumKernels = 10;
+const char* const kKernelNames[kNumKernels] = {"prep", "classify", "walk", "gate", "scatter", "alloc",
                                                "free", "fill", "cbt", "vertices"};
 
 size_t align256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
@@ -281,6 +281,8 @@ uint32_t enqueue_kernels(const BatchDev& bt, int sms, uint32_t grid_mult, bool v
     launch_prep(bt, true, prep, s);
     mark();
     launch_classify(bt, items, s);
+    mark();
+    launch_walk(bt, items, s);
     mark();
     launch_gate(bt, scans, s);
     mark();

@@ -412,22 +412,59 @@ __device__ __forceinline__ void classify_item(const Inst& I, const FrameP& fp, u
             merge = !split && d >= 1 && in_sorted(fp.merge_list, fp.n_merge, j);
             break;
     }
-    uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
-                   ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
-    // the smallest member of an Alg. 4 group (an even heap ID) records the
-    // group's members for the gate, the allocation and the fill
-    if (merge && !(j & 1ull)) {
-        Group g;
-        if (find_group(I, s, g) && g.imin == 0) {
-            I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
-            cmd |= kGrpMin;
-        }
-    }
+    const uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
+                         ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
     *cmd_ptr(I, s) = cmd;
-    uint32_t cost = 0;
-    if (split) cost = fp.gate == 1 ? 3u * (uint32_t)d + 4u : chain_walk(I, s, d, false);
-    I.scan[i] = cost;
+    // the paper's gate charges 3d + 4 without walking the chain (k_walk
+    // computes the exact chain cost otherwise)
+    I.scan[i] = (split && fp.gate == 1) ? 3u * (uint32_t)d + 4u : 0u;
     count_stat(s_cnt, 0, split);
+}
+
+// Pointer chases of the frame, after classify: the compatibility-chain cost
+// of every split wish (command form of Alg. 3) and the Alg. 4 group of every
+// merge wish with an even heap ID, whose smallest member records the members
+// (for the gate, the allocation and the fill). The items that need a walk
+// are packed per tile in shared memory first, so that whole warps walk.
+__global__ void __launch_bounds__(kThreads) k_walk(BatchDev bt) {
+    __shared__ uint32_t s_b, s_n;
+    __shared__ Inst s_I;
+    __shared__ uint32_t s_list[kTileItems];
+    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        uint32_t b, lt;
+        if (threadIdx.x == 0) s_n = 0;
+        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, nullptr, b, lt);
+        const Inst& I = s_I;
+        const FrameP& fp = frame_of(bt, b);
+        const bool chain = fp.gate != 1;
+        const uint32_t N = I.g->N;
+#pragma unroll
+        for (int k = 0; k < kItemsPerThread; ++k) {
+            const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
+            if (i >= N) continue;
+            const uint32_t cmd = *cmd_ptr(I, I.live[i]);
+            const bool need = ((cmd & kSplitWish) && chain) || ((cmd & kMergeWish) && !(cmd & kHeapOdd));
+            if (need) s_list[atomicAdd(&s_n, 1u)] = i;
+        }
+        __syncthreads();
+        const uint32_t n = s_n;
+        for (uint32_t q = threadIdx.x; q < n; q += kThreads) {
+            const uint32_t i = s_list[q];
+            const uint32_t s = I.live[i];
+            const uint32_t cmd = *cmd_ptr(I, s);
+            if (cmd & kSplitWish) {
+                I.scan[i] = chain_walk(I, s, depth_of(I.heap[s], I.ch), false);
+            } else {
+                Group g;
+                if (find_group(I, s, g) && g.imin == 0) {
+                    I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
+                    atomicOr(cmd_ptr(I, s), kGrpMin);
+                }
+            }
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev bt) {
@@ -1291,6 +1328,7 @@ void launch_prep(const BatchDev& bt, bool frame_start, int grid, cudaStream_t s)
     k_prep<<<grid, kThreads, 0, s>>>(bt, frame_start ? 1 : 0);
 }
 void launch_classify(const BatchDev& bt, int grid, cudaStream_t s) { k_classify<<<grid, kThreads, 0, s>>>(bt); }
+void launch_walk(const BatchDev& bt, int grid, cudaStream_t s) { k_walk<<<grid, kThreads, 0, s>>>(bt); }
 void launch_gate(const BatchDev& bt, int grid, cudaStream_t s) { k_gate<<<grid, kThreads, 0, s>>>(bt); }
 void launch_scatter(const BatchDev& bt, int grid, cudaStream_t s) { k_scatter<<<grid, kThreads, 0, s>>>(bt); }
 void launch_alloc(const BatchDev& bt, int grid, cudaStream_t s) { k_alloc<<<grid, kThreads, 0, s>>>(bt); }

@@ -11,6 +11,7 @@ namespace cbtgpu {
 // Launch entry points (defined in cbt_kernels.cu).
 void launch_prep(const BatchDev& bt, bool frame_start, int grid, cudaStream_t s);
 void launch_classify(const BatchDev& bt, int grid, cudaStream_t s);
+void launch_walk(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_gate(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_scatter(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_alloc(const BatchDev& bt, int grid, cudaStream_t s);
