@@ -44,7 +44,7 @@ struct Layout {
 
 // A batch region for instances with the given pool sizes and halfedge counts.
 struct BatchLayout {
-    size_t inst, fps, bg, tile_base, ctile_base, wtile_base, vtile_base, rel_base, status, total;
+    size_t inst, fps, bg, tile_base, ctile_base, stile_base, wtile_base, vtile_base, rel_base, status, total;
     uint32_t Titems, TwordsMax, Trel;
 };
 
@@ -66,6 +66,7 @@ BatchLayout batch_layout(uint32_t n, const uint32_t* cap, const uint32_t* W, con
     L.bg = take(sizeof(BatchGlobals));
     L.tile_base = take(4u * (n + 1u));
     L.ctile_base = take(4u * (n + 1u));
+    L.stile_base = take(4u * (n + 1u));
     L.wtile_base = take(4u * (n + 1u));
     L.vtile_base = take(4u * (n + 1u));
     L.rel_base = take(4u * (n + 1u));
@@ -221,6 +222,7 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
     d.B = n;
     d.tile_base = reinterpret_cast<uint32_t*>(region + B->L.tile_base);
     d.ctile_base = reinterpret_cast<uint32_t*>(region + B->L.ctile_base);
+    d.stile_base = reinterpret_cast<uint32_t*>(region + B->L.stile_base);
     d.wtile_base = reinterpret_cast<const uint32_t*>(region + B->L.wtile_base);
     d.vtile_base = reinterpret_cast<const uint32_t*>(region + B->L.vtile_base);
     d.rel_base = reinterpret_cast<const uint32_t*>(region + B->L.rel_base);
@@ -270,7 +272,7 @@ uint32_t enqueue_kernels(const BatchDev& bt, int sms, uint32_t grid_mult, bool v
     const int prep = static_cast<int>(std::max(1u, std::min<uint32_t>((prep_n + kThreads - 1u) / kThreads,
                                                                      static_cast<uint32_t>(sms) * 4u)));
     const int items = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * grid_mult)));
-    const int scans = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * 8u)));
+    const int scans = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Titems, static_cast<uint32_t>(sms) * 4u)));
     const int words = std::max(1, static_cast<int>(std::min<uint32_t>(bt.Twords, static_cast<uint32_t>(sms) * 4u)));
     uint32_t k = 0;
     auto mark = [&]() {
@@ -747,7 +749,7 @@ struct ServerSlot {
 
 struct TickLayout {
     size_t inst, fps, wbase, vbase, rbase, block;         // packed block (copied per tick)
-    size_t bg, tile_base, ctile_base, nout, status, total;  // rest of the device region
+    size_t bg, tile_base, ctile_base, stile_base, nout, status, total;  // rest of the device region
 };
 
 TickLayout tick_layout(uint32_t k, uint32_t n_max, uint32_t status_words) {
@@ -780,6 +782,7 @@ TickLayout tick_layout(uint32_t k, uint32_t n_max, uint32_t status_words) {
     L.bg = mtake(sizeof(BatchGlobals));
     L.tile_base = mtake(4u * (n_max + 1u));
     L.ctile_base = mtake(4u * (n_max + 1u));
+    L.stile_base = mtake(4u * (n_max + 1u));
     L.nout = mtake(4u * n_max);
     L.status = mtake(8u * static_cast<size_t>(status_words));
     L.total = moff;
@@ -893,6 +896,7 @@ extern "C" int cbt_server_submit(cbt_server* sv, const int32_t* idx, const cbt_f
     bt.tw = sv->tw;
     bt.tile_base = reinterpret_cast<uint32_t*>(S.dev + L.tile_base);
     bt.ctile_base = reinterpret_cast<uint32_t*>(S.dev + L.ctile_base);
+    bt.stile_base = reinterpret_cast<uint32_t*>(S.dev + L.stile_base);
     bt.wtile_base = reinterpret_cast<const uint32_t*>(S.dev + L.wbase);
     bt.vtile_base = reinterpret_cast<const uint32_t*>(S.dev + L.vbase);
     bt.rel_base = reinterpret_cast<const uint32_t*>(S.dev + L.rbase);

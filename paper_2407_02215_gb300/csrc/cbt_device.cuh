@@ -67,7 +67,8 @@ struct Globals {
     uint32_t done;      // finished word tiles of the reduction
     uint32_t ntiles;    // item tiles of this frame: ceil(N / kTileItems)
     uint32_t C;         // changed bisectors of this frame (split, or smallest member of a merge)
-    uint32_t reserved[2];
+    uint32_t nstiles;   // scan tiles of this frame: ceil(N / kScanItems)
+    uint32_t reserved[1];
     uint32_t stats[kStCount];
     uint32_t pad[64 - 10 - kStCount];
 };
@@ -114,7 +115,8 @@ struct BatchGlobals {
     uint32_t tickets[8];
     uint32_t total_tiles;   // item tiles of this frame over all instances
     uint32_t total_ctiles;  // tiles of changed bisectors (kThreads each) over all instances
-    uint32_t pad[64 - 10];
+    uint32_t total_stiles;  // scan tiles (kScanItems each) over all instances
+    uint32_t pad[64 - 11];
 };
 static_assert(sizeof(BatchGlobals) == 256, "BatchGlobals must be 256 bytes");
 
@@ -130,6 +132,7 @@ struct BatchDev {
     uint32_t tw;          // word-tile size of the reduction and free-list kernels
     uint32_t* tile_base;  // [B+1]
     uint32_t* ctile_base; // [B+1] tiles of kThreads changed bisectors, per frame
+    uint32_t* stile_base; // [B+1] scan tiles of kScanItems live bisectors, per frame
     const uint32_t* wtile_base;  // [B+1] word tiles, min(W_b, tw) words each
     const uint32_t* vtile_base;  // [B+1] ceil(cap_b / kTileItems)
     const uint32_t* rel_base;    // [B+1] 9 * H_b
@@ -142,6 +145,10 @@ struct BatchDev {
 constexpr int kThreads = 256;
 constexpr int kItemsPerThread = 4;
 constexpr uint32_t kTileItems = kThreads * kItemsPerThread;  // 1024 live indices
+// The two look-back scans use larger tiles, so that fewer tiles chain.
+constexpr int kScanThreads = 512;
+constexpr int kScanPerThread = 8;
+constexpr uint32_t kScanItems = kScanThreads * kScanPerThread;  // 4096 live indices
 constexpr uint32_t kMaxTileWords = 256;                       // up to 8192 bits per tile
 constexpr uint32_t kMinTileWords = 64;
 

@@ -58,10 +58,11 @@ __device__ __forceinline__ uint32_t find_inst(const uint32_t* base, uint32_t B, 
 
 // ------------------------------------------------------------ block scans
 
-// Exclusive scan of one Pair per thread over a 256-thread block; returns the
-// thread's exclusive prefix and the block total. s_warp needs 9 Pairs.
+// Exclusive scan of one Pair per thread over the block (up to 1024
+// threads); returns the thread's exclusive prefix and the block total.
+// s_warp needs blockDim.x / 32 + 1 Pairs.
 __device__ __forceinline__ Pair block_scan(Pair x, Pair& total, Pair* s_warp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     Pair inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -73,7 +74,7 @@ __device__ __forceinline__ Pair block_scan(Pair x, Pair& total, Pair* s_warp) {
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        Pair w = lane < kThreads / 32 ? s_warp[lane] : Pair{0, 0};
+        Pair w = lane < nw ? s_warp[lane] : Pair{0, 0};
         Pair wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -83,12 +84,12 @@ __device__ __forceinline__ Pair block_scan(Pair x, Pair& total, Pair* s_warp) {
         Pair we{__shfl_up_sync(0xFFFFFFFFu, wi.a, 1), __shfl_up_sync(0xFFFFFFFFu, wi.b, 1)};
         if (lane == 0) we = Pair{0, 0};
         __syncwarp();
-        if (lane < kThreads / 32) s_warp[lane] = we;
-        if (lane == kThreads / 32 - 1) s_warp[kThreads / 32] = wi;
+        if (lane < nw) s_warp[lane] = we;
+        if (lane == nw - 1) s_warp[nw] = wi;
     }
     __syncthreads();
     const Pair r = padd(s_warp[warp], ex);
-    total = s_warp[kThreads / 32];
+    total = s_warp[nw];
     __syncthreads();
     return r;
 }
@@ -211,17 +212,17 @@ __device__ __forceinline__ void tile_begin(const BatchDev& bt, const uint32_t* b
 // (block 0), the look-back descriptors zeroed, and the camera-relative root
 // tables. FP64 is used here only to subtract the eye from the root vertices.
 __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start) {
-    __shared__ uint32_t s_carry;
+    __shared__ uint32_t s_carry, s_scarry;
     __shared__ Pair s_warp[kThreads / 32 + 1];
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nth = gridDim.x * blockDim.x;
     if (frame_start) {
         if (blockIdx.x == 0) {
-            if (threadIdx.x == 0) s_carry = 0;
+            if (threadIdx.x == 0) s_carry = s_scarry = 0;
             __syncthreads();
             for (uint32_t b0 = 0; b0 < bt.B; b0 += kThreads) {
                 const uint32_t b = b0 + threadIdx.x;
-                uint32_t tiles = 0;
+                uint32_t tiles = 0, stl = 0;
                 if (b < bt.B) {
                     const Inst& I = bt.inst[b];
                     const uint32_t N = I.sums[1];
@@ -233,6 +234,8 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
                     g->done = 0;
                     tiles = (N + kTileItems - 1u) / kTileItems;
                     g->ntiles = tiles;
+                    stl = (N + kScanItems - 1u) / kScanItems;
+                    g->nstiles = stl;
                     for (int k = 0; k < kStCount; ++k) g->stats[k] = 0;
                     g->stats[kStLiveBefore] = N;
                     g->stats[kStFreeBefore] = I.cap - N;
@@ -240,15 +243,23 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
                     if (bt.nout) bt.nout[b] = N;
                 }
                 Pair tot;
-                const Pair ex = block_scan(Pair{0, tiles}, tot, s_warp);
-                if (b < bt.B) bt.tile_base[b] = s_carry + ex.b;
+                const Pair ex = block_scan(Pair{stl, tiles}, tot, s_warp);
+                if (b < bt.B) {
+                    bt.tile_base[b] = s_carry + ex.b;
+                    bt.stile_base[b] = s_scarry + ex.a;
+                }
                 __syncthreads();
-                if (threadIdx.x == 0) s_carry += tot.b;
+                if (threadIdx.x == 0) {
+                    s_carry += tot.b;
+                    s_scarry += tot.a;
+                }
                 __syncthreads();
             }
             if (threadIdx.x == 0) {
                 bt.tile_base[bt.B] = s_carry;
+                bt.stile_base[bt.B] = s_scarry;
                 bt.bg->total_tiles = s_carry;
+                bt.bg->total_stiles = s_scarry;
                 for (int k = 0; k < 8; ++k) bt.bg->tickets[k] = 0;
             }
         }
@@ -515,36 +526,32 @@ __global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev bt) {
 // Sec. 3.3). The smallest member (always an even heap ID) walks its group
 // once and records the members for k_alloc and k_fill: m0, m1 are the
 // children of the smaller parent, m2, m3 those of the larger one.
-__global__ void __launch_bounds__(kThreads) k_gate(BatchDev bt) {
+__global__ void __launch_bounds__(kScanThreads) k_gate(BatchDev bt) {
     __shared__ uint32_t s_tile, s_b, s_mg;
-    __shared__ Pair s_warp[kThreads / 32 + 1];
+    __shared__ Pair s_warp[kScanThreads / 32 + 1];
     __shared__ Pair s_excl;
     __shared__ Inst s_I;
     __shared__ uint32_t s_cnt[kBlockStats];
-    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    const uint32_t T = ld_volatile(&bt.bg->total_stiles);
     unsigned long long* status = bt.status;
     for (;;) {
         const uint32_t t = next_ticket(bt.bg, 0, &s_tile);
         if (t >= T) break;
         uint32_t b, lt;
         if (threadIdx.x == 0) s_mg = 0;
-        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
+        tile_begin(bt, bt.stile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
         const Inst& I = s_I;
-        const FrameP& fp = frame_of(bt, b);
-        const uint32_t gate = fp.gate;
+        const uint32_t gate = frame_of(bt, b).gate;
         const uint32_t N = I.g->N, F = I.g->F;
-        const uint32_t base = lt * kTileItems + threadIdx.x * kItemsPerThread;
-        Pair v[kItemsPerThread];
-        uint32_t slot[kItemsPerThread];
+        const uint32_t base = lt * kScanItems + threadIdx.x * kScanPerThread;
+        Pair v[kScanPerThread];
         Pair loc{0, 0};
 #pragma unroll
-        for (int k = 0; k < kItemsPerThread; ++k) {
+        for (int k = 0; k < kScanPerThread; ++k) {
             const uint32_t i = base + k;
             v[k] = Pair{0, 0};
-            slot[k] = kNull;
             if (i < N) {
                 const uint32_t s = I.live[i];
-                slot[k] = s;
                 const uint32_t cmd = *cmd_ptr(I, s);
                 uint32_t mc = 0;
                 if (cmd & kGrpMin) {
@@ -565,13 +572,13 @@ __global__ void __launch_bounds__(kThreads) k_gate(BatchDev bt) {
         const Pair ex = tile_prefix(status, t, lt == 0, tot, I.g, &s_excl);
         Pair run = padd(ex, tex);
 #pragma unroll
-        for (int k = 0; k < kItemsPerThread; ++k) {
+        for (int k = 0; k < kScanPerThread; ++k) {
             const uint32_t i = base + k;
             run = padd(run, v[k]);
             if (i >= N) continue;
             const bool cand = v[k].a > 0;
             const bool granted = cand && run.a <= F;
-            if (cand) atomicOr(cmd_ptr(I, slot[k]), granted ? (kCand | kMergeGrant) : kCand);
+            if (cand) atomicOr(cmd_ptr(I, I.live[i]), granted ? (kCand | kMergeGrant) : kCand);
             if (granted) atomicMax(&s_mg, run.a);
             I.scan[i] = run.b;
             count_stat(s_cnt, 0, cand);
@@ -633,41 +640,36 @@ __device__ __forceinline__ uint32_t leaves_of(uint32_t sb) {
 // (ReserveBlocks): a split bisector takes 2-4 leaves, a valid merge group
 // its parents at its smallest member, which also marks every member merged
 // and gives each the free-list index of its parent.
-__global__ void __launch_bounds__(kThreads) k_alloc(BatchDev bt) {
+__global__ void __launch_bounds__(kScanThreads) k_alloc(BatchDev bt) {
     __shared__ uint32_t s_tile, s_b;
-    __shared__ Pair s_warp[kThreads / 32 + 1];
+    __shared__ Pair s_warp[kScanThreads / 32 + 1];
     __shared__ Pair s_excl;
     __shared__ Inst s_I;
     __shared__ uint32_t s_cnt[kBlockStats];
-    const uint32_t T = ld_volatile(&bt.bg->total_tiles);
+    const uint32_t T = ld_volatile(&bt.bg->total_stiles);
     unsigned long long* status = bt.status + bt.Titems;
     for (;;) {
         const uint32_t t = next_ticket(bt.bg, 1, &s_tile);
         if (t >= T) break;
         uint32_t b, lt;
-        tile_begin(bt, bt.tile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
+        tile_begin(bt, bt.stile_base, t, &s_b, &s_I, nullptr, s_cnt, b, lt);
         const Inst& I = s_I;
         const uint32_t N = I.g->N;
-        const uint32_t base = lt * kTileItems + threadIdx.x * kItemsPerThread;
-        uint32_t na[kItemsPerThread], slot[kItemsPerThread];
-        uint32_t fate[kItemsPerThread];  // 0 keep (or merged, not smallest), 1 split, 3 merge at smallest
-        uint4 mem[kItemsPerThread];
+        const uint32_t base = lt * kScanItems + threadIdx.x * kScanPerThread;
+        // fate per item, 4 bits each: allocation count (0-4) and whether the
+        // item is a merge at its smallest member
+        uint32_t packed = 0;
         Pair loc{0, 0};
 #pragma unroll
-        for (int k = 0; k < kItemsPerThread; ++k) {
+        for (int k = 0; k < kScanPerThread; ++k) {
             const uint32_t i = base + k;
-            na[k] = 0;
-            fate[k] = 0;
-            slot[k] = kNull;
-            mem[k] = make_uint4(kNull, kNull, kNull, kNull);
             if (i >= N) continue;
             const uint32_t s = I.live[i];
-            slot[k] = s;
             const uint32_t cmd = *cmd_ptr(I, s);
             const uint32_t sb = cmd & kSplitMask;
+            uint32_t na = 0, merge = 0;
             if (sb) {
-                na[k] = leaves_of(sb);
-                fate[k] = 1;
+                na = leaves_of(sb);
             } else if ((cmd & kCand) && (cmd & kMergeGrant)) {
                 const uint4 m = I.grp[i];
                 const uint32_t ms[3] = {m.y, m.z, m.w};
@@ -683,12 +685,12 @@ __global__ void __launch_bounds__(kThreads) k_alloc(BatchDev bt) {
                     ok = ok && (c & kMergeWish) && !(c & kSplitMask);
                 }
                 if (ok) {
-                    fate[k] = 3;
-                    mem[k] = m;
-                    na[k] = m.z == kNull ? 1u : 2u;
+                    merge = 1;
+                    na = m.z == kNull ? 1u : 2u;
                 }
             }
-            loc = padd(loc, Pair{fate[k] ? 1u : 0u, na[k]});
+            packed |= (na | (merge << 3)) << (4 * k);
+            loc = padd(loc, Pair{na ? 1u : 0u, na});
         }
         Pair tot;
         const Pair tex = block_scan(loc, tot, s_warp);
@@ -696,28 +698,30 @@ __global__ void __launch_bounds__(kThreads) k_alloc(BatchDev bt) {
         uint32_t run = ex.b + tex.b;
         uint32_t crun = ex.a + tex.a;
 #pragma unroll
-        for (int k = 0; k < kItemsPerThread; ++k) {
+        for (int k = 0; k < kScanPerThread; ++k) {
             const uint32_t i = base + k;
-            if (i >= N) continue;
-            const uint32_t s = slot[k];
-            if (fate[k]) I.chg[crun++] = i;
-            if (fate[k] == 1) {
-                *dest_ptr(I, s) = run;
-            } else if (fate[k] == 3) {
-                const uint32_t ms[4] = {mem[k].x, mem[k].y, mem[k].z, mem[k].w};
+            const uint32_t f = (packed >> (4 * k)) & 15u;
+            const uint32_t na = f & 7u;
+            if (i >= N || !na) continue;
+            I.chg[crun++] = i;
+            if (!(f & 8u)) {
+                *dest_ptr(I, I.live[i]) = run;
+                count_stat(s_cnt, 0, true);
+            } else {
+                const uint4 m = I.grp[i];
+                const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (ms[q] == kNull) continue;
                     atomicOr(cmd_ptr(I, ms[q]), kMerged);
                     *dest_ptr(I, ms[q]) = run + (q < 2 ? 0u : 1u);
                 }
-                atomicAdd(&s_cnt[2], mem[k].z == kNull ? 2u : 4u);
+                atomicAdd(&s_cnt[2], m.z == kNull ? 2u : 4u);
+                count_stat(s_cnt, 1, true);
             }
-            run += na[k];
-            count_stat(s_cnt, 0, fate[k] == 1);
-            count_stat(s_cnt, 1, fate[k] == 3);
+            run += na;
         }
-        if (lt == I.g->ntiles - 1u && threadIdx.x == kThreads - 1) {
+        if (lt == I.g->nstiles - 1u && threadIdx.x == blockDim.x - 1) {
             I.g->A = run;
             I.g->C = crun;
             I.g->stats[kStAllocated] = run;
@@ -1329,9 +1333,9 @@ void launch_prep(const BatchDev& bt, bool frame_start, int grid, cudaStream_t s)
 }
 void launch_classify(const BatchDev& bt, int grid, cudaStream_t s) { k_classify<<<grid, kThreads, 0, s>>>(bt); }
 void launch_walk(const BatchDev& bt, int grid, cudaStream_t s) { k_walk<<<grid, kThreads, 0, s>>>(bt); }
-void launch_gate(const BatchDev& bt, int grid, cudaStream_t s) { k_gate<<<grid, kThreads, 0, s>>>(bt); }
+void launch_gate(const BatchDev& bt, int grid, cudaStream_t s) { k_gate<<<grid, kScanThreads, 0, s>>>(bt); }
 void launch_scatter(const BatchDev& bt, int grid, cudaStream_t s) { k_scatter<<<grid, kThreads, 0, s>>>(bt); }
-void launch_alloc(const BatchDev& bt, int grid, cudaStream_t s) { k_alloc<<<grid, kThreads, 0, s>>>(bt); }
+void launch_alloc(const BatchDev& bt, int grid, cudaStream_t s) { k_alloc<<<grid, kScanThreads, 0, s>>>(bt); }
 void launch_free(const BatchDev& bt, int grid, cudaStream_t s) { k_free<<<grid, bt.tw, 0, s>>>(bt); }
 void launch_fill(const BatchDev& bt, int grid, cudaStream_t s) { k_fill<<<grid, kThreads, 0, s>>>(bt); }
 void launch_cbt(const BatchDev& bt, int grid, cudaStream_t s) { k_cbt<<<grid, bt.tw, 0, s>>>(bt); }
