@@ -1109,23 +1109,14 @@ __global__ void __launch_bounds__(kThreads) k_fill(BatchDev bt) {
 
 // ------------------------------------------------------ reduce + compact
 
-// SumReduction over the updated bitfield fused with CachePointers' live list:
-// each tile of words (one word per thread) writes its part of the sum tree,
-// finds its live-count prefix by look-back and writes the slots of its set
-// bits, staged in shared memory so that the stores are coalesced; the last
-// tile of an instance to finish builds the levels above its tiles.
+// SumReduction over the updated bitfield (Sec. 3.1): each tile of words (one
+// word per thread) writes its part of the sum tree; the last tile of an
+// instance to finish builds the levels above its tiles.
 __global__ void __launch_bounds__(kMaxTileWords) k_cbt(BatchDev bt) {
-    __shared__ uint32_t s_tile, s_b, s_last;
-    __shared__ uint32_t s_w[kMaxTileWords / 32 + 1];
-    __shared__ Pair s_excl;
+    __shared__ uint32_t s_b, s_last;
     __shared__ uint32_t s_lvl[kMaxTileWords];
-    __shared__ uint32_t s_live[kMaxTileWords * 32];
     __shared__ Inst s_I;
-    unsigned long long* status = bt.status + 2u * bt.Titems;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (;;) {
-        const uint32_t t = next_ticket(bt.bg, 2, &s_tile);
-        if (t >= bt.Twords) break;
+    for (uint32_t t = blockIdx.x; t < bt.Twords; t += gridDim.x) {
         uint32_t b, lt;
         tile_begin(bt, bt.wtile_base, t, &s_b, &s_I, nullptr, nullptr, b, lt);
         const Inst& I = s_I;
@@ -1134,10 +1125,8 @@ __global__ void __launch_bounds__(kMaxTileWords) k_cbt(BatchDev bt) {
         const uint32_t nt = W / TW;
         const uint32_t w = lt * TW + threadIdx.x;
         const bool mine = threadIdx.x < TW;
-        const uint32_t wv = mine ? I.bits[w] : 0u;
-        const uint32_t pc = __popc(wv);
+        const uint32_t pc = mine ? __popc(I.bits[w]) : 0u;
         if (mine) I.sums[W + w] = pc;
-        // levels of the tile, from the word level up to the tile root
         s_lvl[threadIdx.x] = pc;
         __syncthreads();
         uint32_t lvl = 1;
@@ -1151,7 +1140,50 @@ __global__ void __launch_bounds__(kMaxTileWords) k_cbt(BatchDev bt) {
             }
             __syncthreads();
         }
-        // in-tile exclusive prefix of popcounts
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(&I.g->done, 1u) == nt - 1u) ? 1u : 0u;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            for (uint32_t n = nt >> 1; n >= 1u; n >>= 1) {
+                for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
+                    I.sums[n + k] = __ldcg(I.sums + 2u * (n + k)) + __ldcg(I.sums + 2u * (n + k) + 1u);
+                __threadfence();
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                I.g->stats[kStLiveAfter] = __ldcg(I.sums + 1);
+                I.g->done = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// CachePointers' live list (Alg. 7 for every rank at once) from the finished
+// sum tree: each tile of words finds its live-count offset by walking up the
+// tree (adding left siblings), scans its popcounts and writes the slots of
+// its set bits, staged in shared memory so that the stores are coalesced.
+__global__ void __launch_bounds__(kMaxTileWords) k_compact(BatchDev bt) {
+    __shared__ uint32_t s_b;
+    __shared__ uint32_t s_w[kMaxTileWords / 32 + 1];
+    __shared__ uint32_t s_live[kMaxTileWords * 32];
+    __shared__ Inst s_I;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t t = blockIdx.x; t < bt.Twords; t += gridDim.x) {
+        uint32_t b, lt;
+        tile_begin(bt, bt.wtile_base, t, &s_b, &s_I, nullptr, nullptr, b, lt);
+        const Inst& I = s_I;
+        const uint32_t W = I.W;
+        const uint32_t TW = min(W, bt.tw);
+        const uint32_t nt = W / TW;
+        uint32_t before = 0;
+        for (uint32_t n = nt + lt; n > 1; n >>= 1)
+            if (n & 1u) before += I.sums[n - 1];
+        const uint32_t w = lt * TW + threadIdx.x;
+        const uint32_t wv = threadIdx.x < TW ? I.bits[w] : 0u;
+        const uint32_t pc = __popc(wv);
         uint32_t inc = pc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1173,35 +1205,15 @@ __global__ void __launch_bounds__(kMaxTileWords) k_cbt(BatchDev bt) {
             if (lane == nw - 1) s_w[nw] = xi;
         }
         __syncthreads();
-        const uint32_t tex = s_w[warp] + inc - pc;
+        uint32_t r = s_w[warp] + inc - pc;
         const uint32_t tot = s_w[nw];
-        __syncthreads();
-        const Pair ex = tile_prefix(status, t, lt == 0, Pair{0, tot}, I.g, &s_excl);
-        // stage the slots of the set bits, then store them coalesced
-        uint32_t m = wv, r = tex;
+        uint32_t m = wv;
         while (m) {
             s_live[r++] = w * 32u + (uint32_t)(__ffs(m) - 1);
             m &= m - 1u;
         }
         __syncthreads();
-        for (uint32_t k = threadIdx.x; k < tot; k += blockDim.x) I.live[ex.b + k] = s_live[k];
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last = (atomicAdd(&I.g->done, 1u) == nt - 1u) ? 1u : 0u;
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            for (uint32_t n = nt >> 1; n >= 1u; n >>= 1) {
-                for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
-                    I.sums[n + k] = __ldcg(I.sums + 2u * (n + k)) + __ldcg(I.sums + 2u * (n + k) + 1u);
-                __threadfence();
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) {
-                I.g->stats[kStLiveAfter] = __ldcg(I.sums + 1);
-                I.g->done = 0;
-            }
-        }
+        for (uint32_t k = threadIdx.x; k < tot; k += blockDim.x) I.live[before + k] = s_live[k];
         __syncthreads();
     }
 }
@@ -1338,7 +1350,10 @@ void launch_scatter(const BatchDev& bt, int grid, cudaStream_t s) { k_scatter<<<
 void launch_alloc(const BatchDev& bt, int grid, cudaStream_t s) { k_alloc<<<grid, kScanThreads, 0, s>>>(bt); }
 void launch_free(const BatchDev& bt, int grid, cudaStream_t s) { k_free<<<grid, bt.tw, 0, s>>>(bt); }
 void launch_fill(const BatchDev& bt, int grid, cudaStream_t s) { k_fill<<<grid, kThreads, 0, s>>>(bt); }
-void launch_cbt(const BatchDev& bt, int grid, cudaStream_t s) { k_cbt<<<grid, bt.tw, 0, s>>>(bt); }
+void launch_cbt(const BatchDev& bt, int grid, cudaStream_t s) {
+    k_cbt<<<grid, bt.tw, 0, s>>>(bt);
+    k_compact<<<grid, bt.tw, 0, s>>>(bt);
+}
 void launch_vertices(const BatchDev& bt, int grid, cudaStream_t s) { k_vertices<<<grid, kThreads, 0, s>>>(bt); }
 void launch_init(const Inst& I, const int32_t* twin, const int32_t* next, const int32_t* prev,
                  const double* hpos, int grid, cudaStream_t s) {
