@@ -213,14 +213,27 @@ void cbt_destroy(cbt_state* st);
 /* Number of kernel launches the last cbt_update enqueued. */
 uint32_t cbt_last_launch_count(const cbt_state* st);
 
-/* Per-kernel timing of cbt_update with CUDA events recorded on the update's
- * stream between its kernels (off by default). cbt_kernel_times waits for the
- * last frame and writes up to n durations in ms, in launch order; it returns
- * how many were written (0 when timing is off). cbt_kernel_name gives the
- * name of the k-th kernel of a frame. */
+/* Execution form of a frame (Alg. 9). Fused (the default): the whole frame is
+ * one cooperative launch of a persistent kernel whose phases are separated by
+ * grid-wide barriers; every block is resident, and every barrier wait is
+ * bounded (a wait that runs out makes every instance of the launch report
+ * CBT_DERR_TIMEOUT). Not fused: one launch per step (cbt_kernel_name). The
+ * results are identical either way. cbt_set_fused(on) may re-upload the
+ * word-tile prefixes on `stream` and waits for it; cbt_fused reads the form.
+ * Host only. */
+int cbt_set_fused(cbt_state* st, int on, cbt_stream_t stream);
+int cbt_fused(const cbt_state* st);
+
+/* Timing of cbt_update (off by default). Per-step form: CUDA events recorded
+ * on the update's stream between its kernels, one duration per kernel
+ * (cbt_kernel_name). Fused form: the device's global timer read by block 0
+ * at the phase boundaries, one duration per phase (cbt_phase_name).
+ * cbt_kernel_times waits for the last frame and writes up to n durations in
+ * ms, in order; it returns how many were written (0 when timing is off). */
 int cbt_set_timing(cbt_state* st, int on);
 uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n);
 const char* cbt_kernel_name(uint32_t k);
+const char* cbt_phase_name(uint32_t k);
 
 /* Update through a CUDA graph (on: the frame's launches are captured once
  * and replayed; the frame parameters reach the device through a copy from
@@ -257,17 +270,22 @@ int cbt_batch_update(cbt_batch* b, const cbt_frame* frames, cbt_stream_t stream)
 /* Replay the batch frame as a CUDA graph (see cbt_set_graph). Host only. */
 int cbt_batch_set_graph(cbt_batch* b, int on);
 
-/* Online autotuner: the next 9 * rounds frames try the 9 combinations of
- * reduction / rank-to-bit tile width (64, 128 or 256 words) and blocks per SM
- * of the item kernels (4, 8 or 16), one per frame, and then keep the one
- * with the smallest median frame time. The configuration never changes the
- * results. cbt_batch_config reads the current choice (tuning = 1 while
- * trying); cbt_batch_set_config sets it directly. */
+/* Online autotuner: the next 10 * rounds frames try, one per frame, the 9
+ * per-step configurations (reduction / rank-to-bit tile width of 64, 128 or
+ * 256 words, times 4, 8 or 16 blocks per SM for the item kernels) and the
+ * fused form, and then keep the one with the smallest median frame time.
+ * The configuration never changes the results. cbt_batch_config reads the
+ * current choice (tuning = 1 while trying); cbt_batch_set_config sets a
+ * per-step configuration directly (and leaves the fused form). */
 int cbt_batch_autotune(cbt_batch* b, uint32_t rounds);
 int cbt_batch_config(const cbt_batch* b, uint32_t* tile_words, uint32_t* blocks_per_sm, int* tuning);
 int cbt_batch_set_config(cbt_batch* b, uint32_t tile_words, uint32_t blocks_per_sm, cbt_stream_t stream);
 
-/* Per-kernel timing of cbt_batch_update (as cbt_set_timing / cbt_kernel_times). */
+/* Execution form of the batch frame (as cbt_set_fused / cbt_fused). */
+int cbt_batch_set_fused(cbt_batch* b, int on, cbt_stream_t stream);
+int cbt_batch_fused(const cbt_batch* b);
+
+/* Timing of cbt_batch_update (as cbt_set_timing / cbt_kernel_times). */
 int cbt_batch_set_timing(cbt_batch* b, int on);
 uint32_t cbt_batch_kernel_times(cbt_batch* b, float* ms, uint32_t n);
 uint32_t cbt_batch_last_launch_count(const cbt_batch* b);

@@ -79,6 +79,12 @@ def load(path: str | None = None):
     lib.cbt_kernel_times.restype = U32
     lib.cbt_kernel_name.argtypes = [U32]
     lib.cbt_kernel_name.restype = C.c_char_p
+    lib.cbt_phase_name.argtypes = [U32]
+    lib.cbt_phase_name.restype = C.c_char_p
+    lib.cbt_set_fused.argtypes = [P, C.c_int, P]
+    lib.cbt_fused.argtypes = [P]
+    lib.cbt_batch_set_fused.argtypes = [P, C.c_int, P]
+    lib.cbt_batch_fused.argtypes = [P]
     _lib = lib
     return lib
 
@@ -239,11 +245,23 @@ class CBT:
         if rc:
             raise CBTError(rc, "cbt_set_timing")
 
+    def set_fused(self, on: bool = True, stream=None):
+        """One cooperative launch per frame (default) or one launch per step."""
+        rc = _lib.cbt_set_fused(self._h, 1 if on else 0, _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_set_fused")
+
+    @property
+    def fused(self) -> bool:
+        return bool(_lib.cbt_fused(self._h))
+
     def kernel_times(self) -> dict:
-        """Per-kernel durations (ms) of the last frame, by kernel name."""
+        """Durations (ms) of the last frame: per kernel (per-step form) or
+        per phase (fused form), by name."""
         buf = (C.c_float * 16)()
         n = _lib.cbt_kernel_times(self._h, buf, 16)
-        return {_lib.cbt_kernel_name(k).decode(): float(buf[k]) for k in range(n)}
+        name = _lib.cbt_phase_name if self.fused else _lib.cbt_kernel_name
+        return {name(k).decode(): float(buf[k]) for k in range(n)}
 
     def live_count(self, stream=None) -> int:
         n = C.c_uint32()
@@ -345,7 +363,8 @@ class Batch:
     def config(self):
         tw, bm, tun = C.c_uint32(), C.c_uint32(), C.c_int()
         _lib.cbt_batch_config(self._h, C.byref(tw), C.byref(bm), C.byref(tun))
-        return {"tile_words": tw.value, "blocks_per_sm": bm.value, "tuning": bool(tun.value)}
+        return {"tile_words": tw.value, "blocks_per_sm": bm.value, "tuning": bool(tun.value),
+                "fused": self.fused}
 
     def set_config(self, tile_words: int, blocks_per_sm: int, stream=None):
         rc = _lib.cbt_batch_set_config(self._h, tile_words, blocks_per_sm, _stream_ptr(stream))
@@ -355,10 +374,20 @@ class Batch:
     def set_timing(self, on: bool = True):
         _lib.cbt_batch_set_timing(self._h, 1 if on else 0)
 
+    def set_fused(self, on: bool = True, stream=None):
+        rc = _lib.cbt_batch_set_fused(self._h, 1 if on else 0, _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_batch_set_fused")
+
+    @property
+    def fused(self) -> bool:
+        return bool(_lib.cbt_batch_fused(self._h))
+
     def kernel_times(self) -> dict:
         buf = (C.c_float * 16)()
         n = _lib.cbt_batch_kernel_times(self._h, buf, 16)
-        return {_lib.cbt_kernel_name(k).decode(): float(buf[k]) for k in range(n)}
+        name = _lib.cbt_phase_name if self.fused else _lib.cbt_kernel_name
+        return {name(k).decode(): float(buf[k]) for k in range(n)}
 
     @property
     def last_launch_count(self) -> int:

@@ -26,6 +26,10 @@ const char* const kKernelNames[kNumKernels] = {"prep", "classify", "walk", "gate
                                                "free", "fill", "cbt", "vertices"};
 // launches per entry of kKernelNames ("cbt" is the reduction plus the compaction)
 constexpr uint32_t kLaunchesPerStep[kNumKernels] = {1, 1, 1, 1, 1, 1, 1, 1, 2, 1};
+// phases of the one-launch frame
+const char* const kPhaseNames[kFramePhases] = {"prep", "classify", "gate_sum", "gate",    "alloc_sum",
+                                               "alloc", "fill",    "reduce",   "compact", "vertices"};
+constexpr uint32_t kFusedTileWords = 64;
 
 size_t align256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
 
@@ -153,12 +157,14 @@ struct cbt_batch {
     FrameP* h_fps = nullptr;  // pinned staging for the per-instance frame parameters
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
-    uint32_t tw = 256;
+    uint32_t tw = kFusedTileWords;
     uint32_t grid_mult = 8;
+    bool fused = true;   // one cooperative launch per frame (else one launch per step)
+    int fused_grid = 1;  // its blocks: resident blocks per SM x SMs, at most the tiles
     bool use_graph = false;
     cudaGraphExec_t exec = nullptr;
     uint32_t exec_tw = 0, exec_mult = 0;
-    bool exec_vertices = false;
+    bool exec_vertices = false, exec_fused = false;
     bool timing = false;
     cudaEvent_t ev[kNumKernels + 1] = {};
     uint32_t timed = 0, launches = 0;
@@ -239,6 +245,12 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
         cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming))
         rc = CBT_ECUDA;
     if (!rc) rc = upload_static_prefixes(B, s);
+    if (!rc) {
+        const int per_sm = frame_blocks_per_sm();
+        if (per_sm <= 0) rc = CBT_ECUDA;
+        const uint32_t work = std::max({B->dev.Titems, B->dev.Twords, (B->dev.Trel + 255u) / 256u, 1u});
+        B->fused_grid = static_cast<int>(std::min<uint32_t>(work, static_cast<uint32_t>(per_sm * B->sms)));
+    }
     if (rc) {
         if (B->h_fps) cudaFreeHost(B->h_fps);
         delete B;
@@ -309,17 +321,42 @@ uint32_t enqueue_kernels(const BatchDev& bt, int sms, uint32_t grid_mult, bool v
     return launches;
 }
 
-// The kernels of one frame. `timed`: record events between the kernels.
+// The kernels of one frame. `timed`: record events between the kernels (the
+// one-launch frame records its phase boundaries on the device instead).
 void enqueue_frame(cbt_batch* B, cudaStream_t s, bool vertices, bool timed) {
+    if (B->fused) {
+        BatchDev bt = B->dev;
+        bt.timing = timed ? 1u : 0u;
+        launch_frame(bt, B->fused_grid, s);
+        B->launches = 1;
+        // a batch exports vertices within its compaction phase
+        B->timed = timed ? static_cast<uint32_t>(B->n == 1 ? kFramePhases : kFramePhases - 1) : 0u;
+        return;
+    }
     B->launches = enqueue_kernels(B->dev, B->sms, B->grid_mult, vertices, s, timed ? B->ev : nullptr);
     B->timed = timed ? (vertices ? 10u : 9u) : 0u;
 }
 
 int apply_config(cbt_batch* B, uint32_t tw, uint32_t mult, cudaStream_t s) {
     B->grid_mult = mult;
+    B->fused = false;
     if (tw == B->tw) return CBT_OK;
     B->tw = tw;
     return upload_static_prefixes(B, s);
+}
+
+int set_fused(cbt_batch* B, bool on, cudaStream_t s) {
+    if (!on) {
+        B->fused = false;
+        return CBT_OK;
+    }
+    if (B->tw != kFusedTileWords) {
+        B->tw = kFusedTileWords;
+        const int rc = upload_static_prefixes(B, s);
+        if (rc) return rc;
+    }
+    B->fused = true;
+    return CBT_OK;
 }
 
 int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
@@ -340,7 +377,10 @@ int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
             B->tune_ms.push_back(ms);
             B->tune_pending = false;
         }
-        const uint32_t ncfg = 9;
+        const uint32_t ncfg = 10;  // 3 x 3 per-step configurations, then the one-launch frame
+        auto apply = [&](uint32_t c) {
+            return c == 9 ? set_fused(B, true, s) : apply_config(B, kTuneTw[c / 3], kTuneMult[c % 3], s);
+        };
         if (B->tune_ms.size() >= ncfg * B->tune_rounds) {
             uint32_t best = 0;
             float best_ms = 1e30f;
@@ -356,11 +396,10 @@ int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
             }
             B->tuning = false;
             B->tune_cfg = best;
-            int rc = apply_config(B, kTuneTw[best / 3], kTuneMult[best % 3], s);
+            int rc = apply(best);
             if (rc) return rc;
         } else {
-            const uint32_t c = static_cast<uint32_t>(B->tune_ms.size()) % ncfg;
-            int rc = apply_config(B, kTuneTw[c / 3], kTuneMult[c % 3], s);
+            int rc = apply(static_cast<uint32_t>(B->tune_ms.size()) % ncfg);
             if (rc) return rc;
         }
     }
@@ -370,7 +409,8 @@ int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
         // the graph copies the frame parameters from pinned staging
         if (B->staged_pending) cudaEventSynchronize(B->staged);
         std::memcpy(B->h_fps, fps.data(), sizeof(FrameP) * n);
-        if (!B->exec || B->exec_tw != B->tw || B->exec_mult != B->grid_mult || B->exec_vertices != vertices) {
+        if (!B->exec || B->exec_tw != B->tw || B->exec_mult != B->grid_mult || B->exec_vertices != vertices ||
+            B->exec_fused != B->fused) {
             if (B->exec) {
                 cudaGraphExecDestroy(B->exec);
                 B->exec = nullptr;
@@ -391,6 +431,7 @@ int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
             B->exec_tw = B->tw;
             B->exec_mult = B->grid_mult;
             B->exec_vertices = vertices;
+            B->exec_fused = B->fused;
         }
         if (cudaGraphLaunch(B->exec, s) != cudaSuccess) return CBT_ECUDA;
         cudaEventRecord(B->staged, s);
@@ -634,6 +675,20 @@ int set_timing(cbt_batch* B, int on) {
 }
 uint32_t kernel_times(cbt_batch* B, float* ms, uint32_t n) {
     if (!B->timing || B->timed == 0 || !ms) return 0u;
+    if (B->fused) {
+        unsigned long long t[kFramePhases + 1];
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(t, B->dev.bg->t, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return 0u;
+        // t[k] opens phase k; the last phase ends at t[kFramePhases] (the
+        // latest block end)
+        const uint32_t m = std::min(n, B->timed);
+        for (uint32_t k = 0; k < m; ++k) {
+            const unsigned long long end = k + 1 == B->timed ? t[kFramePhases] : t[k + 1];
+            ms[k] = end > t[k] ? static_cast<float>(end - t[k]) * 1e-6f : 0.0f;
+        }
+        return m;
+    }
     if (cudaEventSynchronize(B->ev[B->timed]) != cudaSuccess) return 0u;
     const uint32_t m = std::min(n, B->timed);
     for (uint32_t k = 0; k < m; ++k) {
@@ -651,6 +706,17 @@ extern "C" uint32_t cbt_kernel_times(cbt_state* st, float* ms, uint32_t n) {
 }
 
 extern "C" const char* cbt_kernel_name(uint32_t k) { return k < kNumKernels ? kKernelNames[k] : ""; }
+
+extern "C" const char* cbt_phase_name(uint32_t k) {
+    return k < static_cast<uint32_t>(kFramePhases) ? kPhaseNames[k] : "";
+}
+
+extern "C" int cbt_set_fused(cbt_state* st, int on, cbt_stream_t stream) {
+    if (!st) return CBT_EINVAL;
+    return set_fused(st->self, on != 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cbt_fused(const cbt_state* st) { return st && st->self->fused ? 1 : 0; }
 
 extern "C" int cbt_set_graph(cbt_state* st, int on) {
     if (!st) return CBT_EINVAL;
@@ -727,6 +793,13 @@ extern "C" int cbt_batch_set_config(cbt_batch* b, uint32_t tile_words, uint32_t 
 }
 
 extern "C" int cbt_batch_set_timing(cbt_batch* b, int on) { return b ? set_timing(b, on) : CBT_EINVAL; }
+
+extern "C" int cbt_batch_set_fused(cbt_batch* b, int on, cbt_stream_t stream) {
+    if (!b) return CBT_EINVAL;
+    return set_fused(b, on != 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cbt_batch_fused(const cbt_batch* b) { return b && b->fused ? 1 : 0; }
 
 extern "C" uint32_t cbt_batch_kernel_times(cbt_batch* b, float* ms, uint32_t n) {
     return b ? kernel_times(b, ms, n) : 0u;

@@ -68,7 +68,7 @@ struct Globals {
     uint32_t ntiles;    // item tiles of this frame: ceil(N / kTileItems)
     uint32_t C;         // changed bisectors of this frame (split, or smallest member of a merge)
     uint32_t nstiles;   // scan tiles of this frame: ceil(N / kScanItems)
-    uint32_t reserved[1];
+    uint32_t Stot;      // total split cost requested this frame (one-launch frame)
     uint32_t stats[kStCount];
     uint32_t pad[64 - 10 - kStCount];
 };
@@ -110,13 +110,21 @@ struct FrameP {
     uint32_t vcap;
 };
 
+constexpr int kFramePhases = 10;  // phases of the one-launch frame (a batch skips the last)
+
 // Launch-wide counters of one batch (256 bytes).
 struct BatchGlobals {
     uint32_t tickets[8];
     uint32_t total_tiles;   // item tiles of this frame over all instances
     uint32_t total_ctiles;  // tiles of changed bisectors (kThreads each) over all instances
     uint32_t total_stiles;  // scan tiles (kScanItems each) over all instances
-    uint32_t pad[64 - 11];
+    uint32_t bar_count;     // grid barrier of the one-launch frame: arrivals (monotonic),
+    uint32_t bar_epoch;     // and their count when the current launch started
+    uint32_t abort;         // a bounded wait ran out: later waits return at once
+    uint32_t scan_ipt;      // one-launch frame: items per thread of its scan tiles
+    uint32_t pad0[1];
+    unsigned long long t[16];  // phase boundaries (ns) of the one-launch frame
+    uint32_t pad[64 - 16 - 32];
 };
 static_assert(sizeof(BatchGlobals) == 256, "BatchGlobals must be 256 bytes");
 
@@ -140,6 +148,7 @@ struct BatchDev {
     unsigned long long* status;  // [2 * Titems + Twords] look-back descriptors
     uint32_t Titems, Twords, Trel;
     uint32_t* nout;              // optional [B]: live count at frame start per instance
+    uint32_t timing;             // one-launch frame: record phase boundaries
 };
 
 constexpr int kThreads = 256;

@@ -37,12 +37,13 @@ def _population():
     return pop
 
 
-def _run_batch(P, graph=False, autotune=0, vertices=False):
+def _run_batch(P, graph=False, autotune=0, vertices=False, fused=True):
     import torch
     pop = _population()
     gs = [P.CBT(m, D, md) for m, D, md, _ in pop]
     os_ = [Oracle(m, D, md) for m, D, md, _ in pop]
     batch = P.Batch(gs)
+    batch.set_fused(fused)
     if graph:
         batch.set_graph(True)
     if autotune:
@@ -68,12 +69,15 @@ def _run_batch(P, graph=False, autotune=0, vertices=False):
     return batch
 
 
-def test_batch_matches_oracle_per_instance(P):
-    _run_batch(P, vertices=True)
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "per_step"])
+def test_batch_matches_oracle_per_instance(P, fused):
+    b = _run_batch(P, vertices=True, fused=fused)
+    assert b.last_launch_count == (1 if fused else 11)
 
 
-def test_batch_graph_replay(P):
-    _run_batch(P, graph=True)
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "per_step"])
+def test_batch_graph_replay(P, fused):
+    _run_batch(P, graph=True, fused=fused)
 
 
 def test_batch_autotune_keeps_results(P):
@@ -82,9 +86,11 @@ def test_batch_autotune_keeps_results(P):
     assert not cfg["tuning"] and cfg["tile_words"] in (64, 128, 256)
 
 
-def test_single_instance_graph_mode(P):
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "per_step"])
+def test_single_instance_graph_mode(P, fused):
     spec = W.configs.config1()
     g = P.CBT(spec.mesh, spec.D, spec.max_depth)
+    g.set_fused(fused)
     g.set_graph(True)
     o = Oracle(spec.mesh, spec.D, spec.max_depth)
     for k, fp in enumerate(spec.frames):

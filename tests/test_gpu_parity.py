@@ -13,11 +13,20 @@ from tests.gpu_helpers import assert_same_state, run_pair
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def CBT():
+@pytest.fixture(scope="module", params=["fused", "per_step"])
+def CBT(request):
+    """Instances in either execution form: one cooperative launch per frame,
+    or one launch per step."""
     import paper_2407_02215_gb300 as P
     P.build_library()
-    return P.CBT
+    fused = request.param == "fused"
+
+    def make(*args, **kw):
+        g = P.CBT(*args, **kw)
+        g.set_fused(fused)
+        assert g.fused == fused
+        return g
+    return make
 
 
 TINY = [
@@ -47,6 +56,16 @@ def test_small_pools_and_ragged_words(CBT):
     for D in (4, 5, 6, 7):
         frames = [forced_params(MODE_RANDOM, seed=D) for _ in range(40)]
         run_pair(W.meshes.fig1_mesh(), D, 8, frames, CBT, Oracle)
+
+
+def test_merge_requests_beyond_free_slots(CBT):
+    """A saturated pool of 8 tiles asked to merge everything: the merge
+    requests need more parents than there are free slots, so the gate grants
+    them in slot order only while their running total fits."""
+    frames = [forced_params(MODE_FORCE_SPLIT) for _ in range(10)]
+    frames += [forced_params(MODE_FORCE_MERGE) for _ in range(6)]
+    frames += [forced_params(MODE_RANDOM, seed=31) for _ in range(10)]
+    g, o = run_pair(W.meshes.cube_mesh(), 13, 12, frames, CBT, Oracle, check_every=2)
 
 
 def test_paper_gate(CBT):
