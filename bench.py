@@ -63,6 +63,28 @@ def workload_config(spec, K):
 
 STEP_KERNELS = ("prep", "classify", "walk", "gate", "scatter", "alloc", "free", "fill", "cbt", "vertices")
 
+# DRAM traffic of the one-launch frame from one ncu capture (dram__bytes_read
+# + dram__bytes_write, L2 flushed before each pass), per live bisector at
+# frame start, valid only for the kernel sources it was taken on
+# (profiles/grid_flythrough_k_frame.md has the capture and its command).
+FRAME_TRAFFIC = {"sources_sha256_16": "869bb541a526b295", "bytes_per_live": 84.3,
+                 "capture": "frames 7 and 8 of the flythrough: 55.8 MB at 659,164 live, "
+                            "59.8 MB at 712,190 live"}
+FRAME_SOURCES = ("cbt_fused.cu", "cbt_phases.cuh", "cbt_device.cuh")
+
+
+def frame_traffic(mean_live):
+    """Measured DRAM bytes per launch scaled to the mean live count, or None
+    once the kernel sources differ from the ones the capture was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in FRAME_SOURCES:
+        with open(os.path.join(ROOT, "paper_2407_02215_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != FRAME_TRAFFIC["sources_sha256_16"]:
+        return None
+    return FRAME_TRAFFIC["bytes_per_live"] * mean_live
+
 
 def algorithmic_bytes(kernel: str, st: dict, cap: int) -> float:
     """Bytes each kernel must move per frame at minimum, from the frame's
@@ -363,7 +385,9 @@ def bench_ours(args):
         "roofline": {"bound": "hbm", "kernel": "k_frame (the whole frame, one cooperative launch)",
                      "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                      "peak_source": "measured" if peaks else "fallback",
-                     "algorithmic_bytes_per_frame": frame_bytes / len(frames), "traffic": None},
+                     "algorithmic_bytes_per_frame": frame_bytes / len(frames),
+                     "traffic": frame_traffic(bis / len(frames)),
+                     "traffic_note": "ncu DRAM bytes per launch scaled by live count; null if the kernel changed"},
         "phase_ms_per_frame": {k: round(v / len(frames), 5) for k, v in ptimes.items()},
         "phase_share": phase_share,
         "phase_times_from": "second pass over the same frames, device timer at the phase boundaries",

@@ -44,7 +44,7 @@ uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems;
 
 // Per-instance arrays.
 struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, root64, rel, batch, total;
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, root64, rel, batch, total;
     uint32_t cap, W, ch;
 };
 
@@ -105,6 +105,7 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.scan = take(4u * cap);
     L.grp = take(16u * cap);
     L.chg = take(4u * cap);
+    L.chgr = take(16u * cap);
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
     const uint32_t Hh = static_cast<uint32_t>(H);
@@ -504,6 +505,7 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     I.scan = reinterpret_cast<uint32_t*>(b + L.scan);
     I.grp = reinterpret_cast<uint4*>(b + L.grp);
     I.chg = reinterpret_cast<uint32_t*>(b + L.chg);
+    I.chgr = reinterpret_cast<uint4*>(b + L.chgr);
     I.root64 = reinterpret_cast<double*>(b + L.root64);
     I.rel = b + L.rel;
     I.cap = L.cap;

@@ -14,7 +14,9 @@
 //   freel[cap] u32   the first A zero bits of the frame-start bitfield (Alg. 8)
 //   scan[cap]  u32   per live index: split cost, then its running total
 //   grp[cap]   uint4 per live index: the members of the merge group whose
-//                    smallest member it is (written by the gate)
+//                    smallest member it is, or of a split wish's chain
+//   chg[cap]   u32   live indices of the frame's changed bisectors, ascending
+//   chgr[cap]  uint4 the same as records {live index, slot, cmd, dest}
 //   root64[H*9], rel[H*9]: root vertices (FP64) and their per-frame offsets
 //                    from the camera (FP32, fixed point or FP64)
 // and, per batch (a single instance carries a batch of one), the instance
@@ -86,6 +88,7 @@ struct Inst {
     uint32_t* scan;
     uint4* grp;  // per live index: members of the group whose smallest member it is
     uint32_t* chg;  // live indices of the changed bisectors, in ascending slot order
+    uint4* chgr;    // one-launch frame: per changed bisector {live index, slot, cmd, dest}
     double* root64;
     void* rel;
     Globals* g;

@@ -225,8 +225,12 @@ __device__ void phase_prep(const BatchDev& bt, Pair* s_warp, uint32_t* s_tmp) {
             bt.bg->t[kFramePhases] = 0;
         }
     }
-    const uint32_t nth = gridDim.x * blockDim.x;
-    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < bt.Trel; e += nth) rel_entry(bt, e);
+    // block 0 sets up the instances; the others share the root tables
+    if (gridDim.x == 1 || blockIdx.x > 0) {
+        const uint32_t nb = gridDim.x > 1 ? gridDim.x - 1u : 1u, bb = gridDim.x > 1 ? blockIdx.x - 1u : 0u;
+        const uint32_t nth = nb * blockDim.x;
+        for (uint32_t e = bb * blockDim.x + threadIdx.x; e < bt.Trel; e += nth) rel_entry(bt, e);
+    }
 }
 
 // Walks of listed items on the frame-start state: the chain cost of a split
@@ -486,15 +490,15 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
             const uint2 e = s_list[q];
             const uint4 r = recorded ? I.grp[e.x] : make_uint4(kNull, kNull, kNull, kNull);
-            if (r.w == kNull) {
+            if (r.x == kNull && r.w == kNull) {
                 chain_walk(I, e.y, 0, true);
                 continue;
             }
             atomicOr(cmd_ptr(I, e.y), kR);
-            const uint32_t m[3] = {r.x, r.y, r.z};
+            const uint32_t m[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
-            for (uint32_t q2 = 0; q2 < 3; ++q2)
-                if (q2 < r.w) atomicOr(cmd_ptr(I, m[q2] & 0x3FFFFFFFu), chain_code_bits(m[q2] >> 30));
+            for (uint32_t q2 = 0; q2 < 4; ++q2)
+                if (m[q2] >> 30) atomicOr(cmd_ptr(I, m[q2] & 0x3FFFFFFFu), chain_code_bits(m[q2] >> 30));
         }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStMergeGranted, kStSplitGranted);
@@ -610,11 +614,18 @@ __device__ void phase_alloc(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32
         Pair before, all;
         tile_sums(bt.status + bt.Titems, c, before, all, s_red);
         const uint32_t i0 = stile_first(c, ipt);
-        uint32_t f[kMaxIpt];
+        uint32_t f[kMaxIpt], sl[kMaxIpt], cm[kMaxIpt];
         Pair loc{0, 0};
 #pragma unroll
         for (uint32_t k = 0; k < kMaxIpt; ++k) {
-            f[k] = (k < ipt && i0 + k < N) ? I.scan[i0 + k] : 0u;
+            const bool in = k < ipt && i0 + k < N;
+            f[k] = in ? I.scan[i0 + k] : 0u;
+            sl[k] = in ? I.live[i0 + k] : 0u;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) cm[k] = (f[k] & 7u) ? *cmd_ptr(I, sl[k]) : 0u;
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) {
             const uint32_t na = f[k] & 7u;
             loc = padd(loc, Pair{na ? 1u : 0u, na});
         }
@@ -625,7 +636,8 @@ __device__ void phase_alloc(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32
         for (uint32_t k = 0; k < kMaxIpt; ++k) {
             const uint32_t na = f[k] & 7u;
             if (!na) continue;
-            I.chg[crun++] = i0 + k;
+            // the fill's record: everything it needs before its first gather
+            I.chgr[crun++] = make_uint4(i0 + k, sl[k], cm[k], run);
             alloc_apply(I, i0 + k, f[k], run, s_cnt);
             run += na;
         }
@@ -642,19 +654,21 @@ __device__ void phase_alloc(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32
     }
 }
 
-__device__ __forceinline__ void fill_item(const Inst& I, uint32_t i, uint32_t* s_cnt) {
-    const uint32_t s = I.live[i];
-    const uint2 cd = I.cd[s];
-    if (cd.x & kSplitMask) {
+// One changed bisector: live index i, slot s, command word and free-list
+// index of its first new record (a split, or a merge group's smallest
+// member, whose command word carries no split bits).
+__device__ __forceinline__ void fill_item(const Inst& I, uint32_t i, uint32_t s, uint32_t cmd, uint32_t dest,
+                                          uint32_t* s_cnt) {
+    if (cmd & kSplitMask) {
         clear_bit(I, s);
-        fill_split(I, s, cd.x, cd.y, s_cnt);
+        fill_split(I, s, cmd, dest, s_cnt);
     } else {
         const uint4 m = I.grp[i];
         const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) clear_bit(I, ms[q]);
-        fill_merge(I, cd.y, m, s_cnt);
+        fill_merge(I, dest, m, s_cnt);
     }
 }
 
@@ -668,8 +682,10 @@ __device__ void phase_fill(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         ctx_tile(bt, bt.tile_base, 0, 1, c);  // instance 0 in shared memory
         const Inst& I = c.I;
         const uint32_t C = I.g->C;
-        for (uint32_t q = blockIdx.x * kFThreads + threadIdx.x; q < C; q += gridDim.x * kFThreads)
-            fill_item(I, I.chg[q], s_cnt);
+        for (uint32_t q = blockIdx.x * kFThreads + threadIdx.x; q < C; q += gridDim.x * kFThreads) {
+            const uint4 r = I.chgr[q];
+            fill_item(I, r.x, r.y, r.z, r.w, s_cnt);
+        }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStRelinked);
         __syncthreads();
@@ -689,7 +705,12 @@ __device__ void phase_fill(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         }
         __syncthreads();
         const uint32_t n = *s_n;
-        for (uint32_t q = threadIdx.x; q < n; q += kFThreads) fill_item(I, s_list[q], s_cnt);
+        for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
+            const uint32_t i = s_list[q];
+            const uint32_t s = I.live[i];
+            const uint2 cd = I.cd[s];
+            fill_item(I, i, s, cd.x, cd.y, s_cnt);
+        }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStRelinked);
         __syncthreads();

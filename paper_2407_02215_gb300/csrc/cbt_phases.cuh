@@ -290,16 +290,16 @@ __device__ __forceinline__ void lod_wishes(const Inst& I, const FrameP& fp, uint
 // Compatibility chain of bisector b on the frame-start state (command form
 // of Alg. 3): returns its allocation count; with `scatter` it ORs R (and N or
 // P on coarser members) into the command words. With `rec` (cost mode) it
-// also records the members after b: up to three as slot | code << 30 (code
-// 1 = R, 2 = R+N, 3 = R+P) in x, y, z with their count in w, or all kNull
-// when the chain is longer or broken (the marking then walks it again).
+// also records the members after b: up to four as slot | code << 30 (code
+// 1 = R, 2 = R+N, 3 = R+P; 0 = no member) in x, y, z, w, or all kNull when
+// the chain is longer or broken (the marking then walks it again).
 __device__ __forceinline__ uint32_t chain_code_bits(uint32_t code) {
     return code == 1u ? kR : (code == 2u ? (kR | kN) : (kR | kP));
 }
 
 static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool scatter, uint4* rec = nullptr) {
     uint32_t cur = b, cost = 2;
-    uint32_t m0 = 0, m1 = 0, m2 = 0, n = 0;
+    uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, n = 0;
     bool over = false;
     auto note = [&](uint32_t t, uint32_t code) {
         const uint32_t v = t | (code << 30);
@@ -309,12 +309,14 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
             m1 = v;
         else if (n == 2)
             m2 = v;
+        else if (n == 3)
+            m3 = v;
         else
             over = true;
         ++n;
     };
     auto done = [&](uint32_t c, bool ok) {
-        if (rec) *rec = (ok && !over) ? make_uint4(m0, m1, m2, n) : make_uint4(kNull, kNull, kNull, kNull);
+        if (rec) *rec = (ok && !over) ? make_uint4(m0, m1, m2, m3) : make_uint4(kNull, kNull, kNull, kNull);
         return c;
     };
     if (scatter) atomicOr(cmd_ptr(I, b), kR);
