@@ -67,9 +67,9 @@ STEP_KERNELS = ("prep", "classify", "walk", "gate", "scatter", "alloc", "free", 
 # + dram__bytes_write, L2 flushed before each pass), per live bisector at
 # frame start, valid only for the kernel sources it was taken on
 # (profiles/grid_flythrough_k_frame.md has the capture and its command).
-FRAME_TRAFFIC = {"sources_sha256_16": "869bb541a526b295", "bytes_per_live": 84.3,
-                 "capture": "frames 7 and 8 of the flythrough: 55.8 MB at 659,164 live, "
-                            "59.8 MB at 712,190 live"}
+FRAME_TRAFFIC = {"sources_sha256_16": "f41395ee7e558eb9", "bytes_per_live": 81.3,
+                 "capture": "frames 7 and 8 of the flythrough: 54.9 MB at 659,164 live, "
+                            "56.4 MB at 712,190 live"}
 FRAME_SOURCES = ("cbt_fused.cu", "cbt_phases.cuh", "cbt_device.cuh")
 
 
@@ -434,9 +434,10 @@ def _sync_stats(gs):
 
 
 def bench_batch(args):
-    """Batched form (256 uneven instances, 64 frames): one launch per kernel
-    and frame for the whole batch (CUDA graph, autotuned tiles) against 256
-    plain per-instance launches of the same frames; identical results."""
+    """Batched form (256 uneven instances, 64 frames): the whole batch per
+    frame in one launch (fused) or one launch per step, whichever the online
+    autotuner picks (CUDA graph), against 256 plain per-instance updates of
+    the same frames; identical results."""
     import torch
 
     from paper_2407_02215_gb300 import CBT, Batch
@@ -458,15 +459,18 @@ def bench_batch(args):
     # batched: tune on a discarded copy, then time a fresh batch
     tune = [CBT(s.mesh, s.D, s.max_depth) for s in specs]
     bt = Batch(tune)
-    bt.autotune(2)
-    for k in range(min(args.frames, 18 + 2)):
+    bt.autotune(2)  # 10 candidates x 2 rounds, chosen at the 21st frame
+    for k in range(min(args.frames, 21)):
         bt.update([s.frames[k] for s in specs])
     torch.cuda.synchronize()
     cfg = bt.config()
     del bt, tune
     gs = [CBT(s.mesh, s.D, s.max_depth) for s in specs]
     batch = Batch(gs)
-    batch.set_config(cfg["tile_words"], cfg["blocks_per_sm"])
+    if cfg["fused"]:
+        batch.set_fused(True)
+    else:
+        batch.set_config(cfg["tile_words"], cfg["blocks_per_sm"])
     batch.set_graph(True)
     t_batch, bis_batch = 0.0, 0
     torch.cuda.synchronize()

@@ -273,8 +273,10 @@ int cbt_batch_set_graph(cbt_batch* b, int on);
 /* Online autotuner: the next 10 * rounds frames try, one per frame, the 9
  * per-step configurations (reduction / rank-to-bit tile width of 64, 128 or
  * 256 words, times 4, 8 or 16 blocks per SM for the item kernels) and the
- * fused form, and then keep the one with the smallest median frame time.
- * The configuration never changes the results. cbt_batch_config reads the
+ * fused form, and then keep the one with the smallest median frame time per
+ * live bisector (the candidates run on different frames; each waits for its
+ * frame and reads the batch's live count). The configuration never changes
+ * the results. cbt_batch_config reads the
  * current choice (tuning = 1 while trying); cbt_batch_set_config sets a
  * per-step configuration directly (and leaves the fused form). */
 int cbt_batch_autotune(cbt_batch* b, uint32_t rounds);

@@ -27,8 +27,8 @@ const char* const kKernelNames[kNumKernels] = {"prep", "classify", "walk", "gate
 // launches per entry of kKernelNames ("cbt" is the reduction plus the compaction)
 constexpr uint32_t kLaunchesPerStep[kNumKernels] = {1, 1, 1, 1, 1, 1, 1, 1, 2, 1};
 // phases of the one-launch frame
-const char* const kPhaseNames[kFramePhases] = {"prep", "classify", "gate_sum", "gate",    "alloc_sum",
-                                               "alloc", "fill",    "reduce",   "compact", "vertices"};
+const char* const kPhaseNames[kFramePhases] = {"prep",  "classify", "gate_sum", "gate",    "alloc_sum",
+                                               "alloc", "fill",     "reduce",   "compact", "vertices"};
 constexpr uint32_t kFusedTileWords = 64;
 
 size_t align256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
@@ -369,13 +369,18 @@ int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
         vertices = vertices || fps[b].vout != nullptr;
     }
     // online autotuner: one candidate configuration per frame, round robin,
-    // then the fastest by median frame time (results do not depend on it)
+    // then the fastest by median time per live bisector (results do not depend on it)
     if (B->tuning) {
         if (B->tune_pending) {
+            // candidates run on different frames, whose work differs: compare
+            // time per live bisector of the batch
             float ms = 0.0f;
+            uint32_t live = 0;
             cudaEventSynchronize(B->tune_ev[1]);
             cudaEventElapsedTime(&ms, B->tune_ev[0], B->tune_ev[1]);
-            B->tune_ms.push_back(ms);
+            if (cudaMemcpy(&live, &B->dev.bg->live_total, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return CBT_ECUDA;
+            B->tune_ms.push_back(ms / static_cast<float>(std::max(live, 1u)));
             B->tune_pending = false;
         }
         const uint32_t ncfg = 10;  // 3 x 3 per-step configurations, then the one-launch frame

@@ -125,7 +125,7 @@ struct BatchGlobals {
     uint32_t bar_epoch;     // and their count when the current launch started
     uint32_t abort;         // a bounded wait ran out: later waits return at once
     uint32_t scan_ipt;      // one-launch frame: items per thread of its scan tiles
-    uint32_t pad0[1];
+    uint32_t live_total;    // live bisectors of the batch at frame start (saturating)
     unsigned long long t[16];  // phase boundaries (ns) of the one-launch frame
     uint32_t pad[64 - 16 - 32];
 };

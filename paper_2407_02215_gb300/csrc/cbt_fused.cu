@@ -222,6 +222,7 @@ __device__ void phase_prep(const BatchDev& bt, Pair* s_warp, uint32_t* s_tmp) {
             bt.bg->total_tiles = s_tmp[0];
             bt.bg->total_stiles = s_tmp[1];
             bt.bg->scan_ipt = ipt;
+            bt.bg->live_total = s_tmp[2];
             bt.bg->t[kFramePhases] = 0;
         }
     }

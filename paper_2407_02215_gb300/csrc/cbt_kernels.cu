@@ -20,13 +20,13 @@ namespace cbtgpu {
 // (block 0), the look-back descriptors zeroed, and the camera-relative root
 // tables. FP64 is used here only to subtract the eye from the root vertices.
 __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start) {
-    __shared__ uint32_t s_carry, s_scarry;
+    __shared__ uint32_t s_carry, s_scarry, s_live;
     __shared__ Pair s_warp[kThreads / 32 + 1];
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nth = gridDim.x * blockDim.x;
     if (frame_start) {
         if (blockIdx.x == 0) {
-            if (threadIdx.x == 0) s_carry = s_scarry = 0;
+            if (threadIdx.x == 0) s_carry = s_scarry = s_live = 0;
             __syncthreads();
             for (uint32_t b0 = 0; b0 < bt.B; b0 += kThreads) {
                 const uint32_t b = b0 + threadIdx.x;
@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
                     g->stats[kStFreeBefore] = I.cap - N;
                     g->stats[kStFrame] = frame_of(bt, b).frame;
                     if (bt.nout) bt.nout[b] = N;
+                    atomicAdd(&s_live, N);
                 }
                 Pair tot;
                 const Pair ex = block_scan(Pair{stl, tiles}, tot, s_warp);
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
                 bt.stile_base[bt.B] = s_scarry;
                 bt.bg->total_tiles = s_carry;
                 bt.bg->total_stiles = s_scarry;
+                bt.bg->live_total = s_live;
                 for (int k = 0; k < 8; ++k) bt.bg->tickets[k] = 0;
             }
         }

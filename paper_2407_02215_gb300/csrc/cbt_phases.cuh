@@ -355,17 +355,16 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
     return done(cost, false);
 }
 
-__device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
-                                              uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt) {
+// Split and merge wishes of bisector j (Sec. 3.3 GenerateCommands): the LOD
+// reading R8 (mode 0), forced splits or merges, seeded random requests, or
+// sorted request lists. Returns false when j does not decode to a root of
+// this mesh.
+__device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uint64_t key, uint64_t j,
+                                            const uint32_t* tab, bool& split, bool& merge) {
     const int d = depth_of(j, I.ch);
     const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
-    bool split = false, merge = false;
-    if (d < 0 || h >= I.H) {
-        set_err(I.g, kErrLink);
-        *cmd_ptr(I, s) = 0u;
-        I.scan[i] = 0u;
-        return 0u;
-    }
+    split = merge = false;
+    if (d < 0 || h >= I.H) return false;
     switch (fp.mode) {
         case 0:
             if (d <= 31)
@@ -388,6 +387,19 @@ __device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& f
             merge = !split && d >= 1 && in_sorted(fp.merge_list, fp.n_merge, j);
             break;
     }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
+                                                  uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt) {
+    bool split, merge;
+    if (!item_wishes(I, fp, key, j, tab, split, merge)) {
+        set_err(I.g, kErrLink);
+        *cmd_ptr(I, s) = 0u;
+        I.scan[i] = 0u;
+        return 0u;
+    }
+    const int d = depth_of(j, I.ch);
     const uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
                          ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
     *cmd_ptr(I, s) = cmd;
@@ -735,6 +747,5 @@ __device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uin
     for (int k = 0; k < 9; ++k) o[k] = r[k];
 }
 
-// Vertices of the live bisectors of every instance with an output buffer,
 
 }  // namespace cbtgpu
