@@ -511,6 +511,50 @@ def bench_serve(args):
                                    f"{args.planets} planets), Poisson arrivals, HBM budget {args.hbm_budget_gb} GB"}}
 
 
+def bench_reduce(args):
+    """SumReduction (Sec. 3.1) alone at 2^27 slots, the size at which the paper
+    times the prior method's reduction (0.4 ms on its GPU; context, not a
+    ratio): a seeded random bitfield of 16 MB in, the 32 MB sum tree out, L2
+    flushed before every timed run."""
+    import torch
+
+    from paper_2407_02215_gb300 import sum_reduce
+    D = 27
+    W = 1 << (D - 5)
+    g = torch.Generator(device="cuda").manual_seed(27)
+    bits = torch.randint(-2**31, 2**31 - 1, (W,), dtype=torch.int32, device="cuda", generator=g)
+    sums = torch.zeros(2 * W, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        sum_reduce(bits, D, sums)
+    reps = 50
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        sum_reduce(bits, D, sums)
+        b.record()
+    torch.cuda.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    # the bitfield is read once; every node of the tree (2W words) is written once
+    alg = 4.0 * W + 8.0 * W
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    gbs = alg / (ms.mean() / 1e3) / 1e9
+    root = int(sums[1].item())
+    want = int(np.unpackbits(bits.cpu().numpy().view(np.uint8)).sum())
+    return {"metric": "CBT sum reduction over 2^27 slots (Sec. 3.1), us per reduction", "unit": "us",
+            "value": float(ms.mean() * 1e3), "p50": float(np.median(ms) * 1e3), "p99": float(np.percentile(ms, 99) * 1e3),
+            "higher_is_better": False,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "algorithmic_bytes": alg, "peak_source": "measured" if peaks else "fallback"},
+            "root": root, "root_equals_popcount": root == want,
+            "paper": {"value_us": 400.0, "what": "original implicit CBT sum reduction at 2^27 on an AMD 6800 XT",
+                      "cite": "Sec. 4 (reduction cost of the prior method)"},
+            "config": {"workload": "reduce: random bitfield (seeded), 2^27 slots, L2 flushed before every run",
+                       "reps": reps}}
+
+
 def bench_planet(args):
     """Planet descent (pool 2^22, max depth 48, fixed point): frame times."""
     import torch
@@ -544,7 +588,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
-    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "serve", "planet"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "serve", "planet", "reduce"],
                     help="grid = the headline workload; the others are extra measurements")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--planets", type=int, default=8)
@@ -556,7 +600,8 @@ def main():
     if args.workload != "grid":
         import paper_2407_02215_gb300 as P
         P.build_library()
-        fn = {"batch": bench_batch, "serve": bench_serve, "planet": bench_planet}[args.workload]
+        fn = {"batch": bench_batch, "serve": bench_serve, "planet": bench_planet,
+              "reduce": bench_reduce}[args.workload]
         print(json.dumps(fn(args)))
         return
     if args.impl == "reference":

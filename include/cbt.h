@@ -333,6 +333,24 @@ int32_t cbt_server_next_slot_free(const cbt_server* sv);
  * caller's. */
 void cbt_server_destroy(cbt_server* sv);
 
+/* SumReduction (Sec. 3.1) alone over a caller's bitfield, as a streaming
+ * kernel: the per-level uint32 sums above the bitfield words, in the layout
+ * of cbt_cbt (sums[W + w] = popcount of word w, sums[n] = sums[2n] +
+ * sums[2n+1], sums[1] = the number of set bits). This is the prior method's
+ * bottleneck that the paper times at 2^27 slots (Sec. 4); the frame update
+ * runs the same reduction inside its own launch.
+ *   d_bitfield: DEVICE u32[2^D / 32], 16-byte aligned, read only;
+ *   D: 5 <= D <= 28 (W = 2^(D-5) words);
+ *   d_sums: DEVICE u32[2W], 16-byte aligned, caller-owned. Its unused word
+ *           sums[0] counts the call's finished chunks: it must be 0 when the
+ *           call starts (a zeroed buffer) and the call leaves it 0, so calls
+ *           on one d_sums must not overlap on the GPU.
+ * One launch on `stream` (chunks of 4096 words; the last chunk to finish
+ * builds the levels above the chunk roots); allocates nothing. Errors:
+ * CBT_EINVAL (NULL or misaligned pointer, D < 5), CBT_ECAPACITY (D > 28),
+ * CBT_ECUDA. Asynchronous. */
+int cbt_sum_reduce(const uint32_t* d_bitfield, int32_t D, uint32_t* d_sums, cbt_stream_t stream);
+
 /* The reduction and live-slot compaction step of cbt_update (the CBT sum
  * tree and the ascending list of set bits) over a caller's bitfield, for
  * callers that cannot allocate device memory: a real-time frame loop in which

@@ -6,4 +6,5 @@ include/cbt.h) with a thin Python binding. Import fails loudly when the CUDA
 library has not been built.
 """
 from .build import build as build_library  # noqa: F401
-from .cbt import CBT, Batch, Server, CBTError, CBT_NULL, halfedges_from_faces, load, workspace_bytes  # noqa: F401
+from .cbt import (CBT, CBT_NULL, Batch, CBTError, Server, halfedges_from_faces, load,  # noqa: F401
+                  sum_reduce, workspace_bytes)

@@ -81,6 +81,7 @@ def load(path: str | None = None):
     lib.cbt_kernel_name.restype = C.c_char_p
     lib.cbt_phase_name.argtypes = [U32]
     lib.cbt_phase_name.restype = C.c_char_p
+    lib.cbt_sum_reduce.argtypes = [P, I32, P, P]
     lib.cbt_set_fused.argtypes = [P, C.c_int, P]
     lib.cbt_fused.argtypes = [P]
     lib.cbt_batch_set_fused.argtypes = [P, C.c_int, P]
@@ -146,6 +147,14 @@ def halfedges_from_faces(mesh) -> dict:
     if rc:
         raise CBTError(rc, "cbt_halfedges_from_faces")
     return out
+
+
+def sum_reduce(bits, D: int, sums, stream=None):
+    """SumReduction (Sec. 3.1) of a device bitfield (uint32 tensor of 2^D / 32
+    words) into `sums` (uint32 tensor of 2W words, layout of CBT.cbt())."""
+    rc = load().cbt_sum_reduce(_t_ptr(bits), int(D), _t_ptr(sums), _stream_ptr(stream))
+    if rc:
+        raise CBTError(rc, "cbt_sum_reduce")
 
 
 def workspace_bytes(H: int, D: int) -> int:
