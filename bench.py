@@ -555,6 +555,60 @@ def bench_reduce(args):
                        "reps": reps}}
 
 
+def bench_dodeca(args):
+    """The paper's planet scene shape (Sec. 4, Table 3: H = 60, D = 17, 0.1 ms
+    per update on its GPU): dodecahedron base on an Earth-sized sphere,
+    vertices projected onto the sphere in FP64, 14 px refinement edges, a
+    300-frame descent from 2e7 m to 2 m; one instance, CUDA graph, vertices
+    exported every frame, L2 flushed before every frame."""
+    import torch
+
+    from paper_2407_02215_gb300 import CBT
+    spec = W.configs.config_dodeca()
+    g0 = CBT(spec.mesh, spec.D, spec.max_depth)
+    vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device="cuda")
+    for fp in spec.frames[:max(args.warmup, 3)]:
+        g0.update(fp, vertices_out=vbuf)
+    del g0
+    g = CBT(spec.mesh, spec.D, spec.max_depth)
+    g.set_graph(True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in spec.frames]
+    live = []
+    for k, fp in enumerate(spec.frames):
+        flush.zero_()
+        ev[k][0].record()
+        g.update(fp, vertices_out=vbuf)
+        ev[k][1].record()
+        live.append(g.stats()["live_before"])
+    torch.cuda.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    live = np.array(live)
+    busy = live > 1000  # frames with the planet in view
+    # phase breakdown of the frames with the planet in view (device timer)
+    gk = CBT(spec.mesh, spec.D, spec.max_depth)
+    gk.set_timing(True)
+    pt, nb = {}, 0
+    for k, fp in enumerate(spec.frames):
+        flush.zero_()
+        gk.update(fp, vertices_out=vbuf)
+        if busy[k]:
+            nb += 1
+            for name, v in gk.kernel_times().items():
+                pt[name] = pt.get(name, 0.0) + v
+    del gk
+    return {"metric": METRIC + " [paper's planet shape]", "value": float(live.sum() / (ms.sum() / 1e3)),
+            "unit": UNIT, "ms_per_frame_mean": float(ms.mean()), "ms_per_frame_p50": float(np.median(ms)),
+            "ms_per_frame_p99": float(np.percentile(ms, 99)),
+            "ms_per_frame_p50_in_view": float(np.median(ms[busy])) if busy.any() else None,
+            "live_p50_in_view": float(np.median(live[busy])) if busy.any() else None, "live_max": int(live.max()),
+            "phase_ms_per_frame_in_view": {k: round(v / max(nb, 1), 5) for k, v in pt.items()},
+            "paper": {"ms_per_update": 0.1, "what": "Table 3, water planet (H 60, D 17), AMD 6800 XT, FP64 vertex decode"},
+            "config": {"workload": "dodeca planet: dodecahedron (60 halfedges), R 6.371e6 m, pool 2^17, max depth 50, "
+                                   "300-frame descent 2e7 m -> 2 m, sphere projection in FP64, 14 px edges, "
+                                   "L2 flushed before every frame", "frames": len(spec.frames)}}
+
+
 def bench_planet(args):
     """Planet descent (pool 2^22, max depth 48, fixed point): frame times."""
     import torch
@@ -588,7 +642,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
-    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "serve", "planet", "reduce"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "serve", "planet", "reduce", "dodeca"],
                     help="grid = the headline workload; the others are extra measurements")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--planets", type=int, default=8)
@@ -601,7 +655,7 @@ def main():
         import paper_2407_02215_gb300 as P
         P.build_library()
         fn = {"batch": bench_batch, "serve": bench_serve, "planet": bench_planet,
-              "reduce": bench_reduce}[args.workload]
+              "reduce": bench_reduce, "dodeca": bench_dodeca}[args.workload]
         print(json.dumps(fn(args)))
         return
     if args.impl == "reference":

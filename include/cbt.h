@@ -72,8 +72,11 @@ enum {
 /* Wish modes: the LOD test of Sec. 3.3 kernel 4, or test modes. */
 enum { CBT_MODE_LOD = 0, CBT_MODE_FORCE_SPLIT = 1, CBT_MODE_FORCE_MERGE = 2, CBT_MODE_RANDOM = 3,
        CBT_MODE_LIST = 4 };
-/* Vertex evaluation: FP32, fixed point with exact integer sums, FP64. */
-enum { CBT_PREC_FP32 = 0, CBT_PREC_FIXED = 1, CBT_PREC_FP64 = 2 };
+/* Vertex evaluation: FP32, fixed point with exact integer sums, FP64, or
+ * projected onto a sphere about the world origin (radius sphere_radius) in
+ * FP64 before the camera offset (the paper projects the vertices onto a
+ * sphere during refinement, Sec. 4). */
+enum { CBT_PREC_FP32 = 0, CBT_PREC_FIXED = 1, CBT_PREC_FP64 = 2, CBT_PREC_SPHERE = 3 };
 /* Allocation budget per request: exact chain cost, or the paper's 3d + 4. */
 enum { CBT_GATE_CHAIN = 0, CBT_GATE_PAPER = 1 };
 
@@ -85,7 +88,10 @@ enum { CBT_GATE_CHAIN = 0, CBT_GATE_PAPER = 1 };
  * vertices_out: optional DEVICE buffer of vertices_cap * 9 floats; when set,
  * the frame ends by writing the vertices of the new live bisectors (ascending
  * slot order) relative to eye in the frame's precision, as cbt_vertices does;
- * rows beyond vertices_cap are not written (size it 2^D rows to be safe). */
+ * rows beyond vertices_cap are not written (size it 2^D rows to be safe).
+ * sphere_radius: CBT_PREC_SPHERE only, the radius (> 0) of the sphere about
+ * the world origin onto which the vertices (LOD test and export) are
+ * projected. */
 typedef struct {
     double eye[3];
     float planes[5][3];
@@ -102,6 +108,7 @@ typedef struct {
     uint32_t n_merge;
     float* vertices_out;
     uint32_t vertices_cap;
+    double sphere_radius; /* CBT_PREC_SPHERE: the sphere's radius (> 0), else unused */
 } cbt_frame;
 
 /* Per-frame counters (read with cbt_stats). */
@@ -192,7 +199,8 @@ int cbt_leaves(cbt_state* st, uint32_t* d_slots, uint64_t* d_heap, uint32_t* d_l
  * fixed-point or FP64 evaluation as `precision`; FP64 is used on the device
  * only to subtract h_origin from the root vertices). d_out: caller device
  * memory of cap * 9 floats. *h_count receives N. CBT_ENOMEM when N > cap.
- * Synchronous. */
+ * CBT_PREC_SPHERE is not taken here (CBT_EINVAL): sphere vertices come from
+ * cbt_update's vertices_out, which carries the radius. Synchronous. */
 int cbt_vertices(cbt_state* st, float* d_out, const double h_origin[3], uint32_t precision,
                  int32_t fixed_shift, uint32_t cap, uint32_t* h_count, cbt_stream_t stream);
 

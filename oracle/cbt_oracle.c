@@ -326,16 +326,23 @@ void or_decode_weights(uint64_t j, int32_t ch, uint64_t* W9) {
 typedef struct {
     uint32_t precision;
     int32_t shift;
+    double radius;       /* PREC_SPHERE */
+    double org[3];       /* PREC_SPHERE: the origin, subtracted after the projection */
+    const double* abs64; /* PREC_SPHERE: the FP64 root vertices themselves */
     float* r32;   /* [H][9] FP32 root vertices minus the origin */
     int64_t* x;   /* [H][9] fixed point round((V - origin) 2^shift) */
     double* d64;  /* [H][9] FP64 root vertices minus the origin */
 } rel_roots;
 
 static int make_rel(const or_state* st, const double org[3], uint32_t precision, int32_t shift,
-                    rel_roots* R) {
+                    double radius, rel_roots* R) {
     memset(R, 0, sizeof(*R));
     R->precision = precision;
     R->shift = shift;
+    R->radius = radius;
+    for (int c = 0; c < 3; ++c) R->org[c] = org[c];
+    R->abs64 = st->root;
+    if (precision == OR_PREC_SPHERE && !(radius > 0.0)) return OR_EINVAL;
     const size_t n = (size_t)st->H * 9u;
     R->r32 = (float*)malloc(sizeof(float) * n);
     R->x = (int64_t*)malloc(sizeof(int64_t) * n);
@@ -362,12 +369,40 @@ static void free_rel(rel_roots* R) {
  * readings): exact integer weights W, then
  *   FP32:  (w0 R0 + w1 R1) + w2 R2 with w = float(W) 2^-d,
  *   FIXED: float(sum W X) 2^-(d + shift), the integer sum exact in 128 bits,
- *   FP64:  float((w0 D0 + w1 D1) + w2 D2) with w = double(W) 2^-d. */
+ *   FP64:  float((w0 D0 + w1 D1) + w2 D2) with w = double(W) 2^-d,
+ *   SPHERE: the FP64 point p of the flat root triangle (V absolute) moved
+ *           radially onto the sphere about the world origin, then taken
+ *           relative to the origin and rounded to FP32 (the paper projects
+ *           the vertices onto a sphere during refinement, Sec. 4; R13
+ *           reading). In FP64 with fused multiply-adds:
+ *             p_c = fma(w2, V2c, fma(w1, V1c, w0 V0c)),
+ *             n2  = fma(pz, pz, fma(py, py, px px)),
+ *             y   = 1 / sqrt(n2): the FP32 estimate 1/sqrtf(float(n2)),
+ *                   then twice y = fma(y/2, fma(-n2, y y, 1), y) (Newton),
+ *             out = float(fma(p_c, radius y, -origin_c)). */
 static void bisector_rel(const or_state* st, const rel_roots* R, uint64_t j, float out[9]) {
     const int d = depth_of(st, j);
     const uint32_t h = root_of(st, j);
     uint64_t W[9];
     or_decode_weights(j, st->ch, W);
+    if (R->precision == OR_PREC_SPHERE) {
+        for (int i = 0; i < 3; ++i) {
+            const double w0 = ldexp((double)W[3 * i + 0], -d);
+            const double w1 = ldexp((double)W[3 * i + 1], -d);
+            const double w2 = ldexp((double)W[3 * i + 2], -d);
+            double p[3];
+            for (int c = 0; c < 3; ++c) {
+                const size_t b = 9u * h + (size_t)c;
+                p[c] = fma(w2, R->abs64[b + 6], fma(w1, R->abs64[b + 3], w0 * R->abs64[b + 0]));
+            }
+            const double n2 = fma(p[2], p[2], fma(p[1], p[1], p[0] * p[0]));
+            double y = (double)(1.0f / sqrtf((float)n2));
+            for (int it = 0; it < 2; ++it) y = fma(y * 0.5, fma(-n2, y * y, 1.0), y);
+            const double f = R->radius * y;
+            for (int c = 0; c < 3; ++c) out[3 * i + c] = (float)fma(p[c], f, -R->org[c]);
+        }
+        return;
+    }
     for (int i = 0; i < 3; ++i) {
         for (int c = 0; c < 3; ++c) {
             const size_t b = 9u * h + (size_t)c;
@@ -393,9 +428,9 @@ static void bisector_rel(const or_state* st, const rel_roots* R, uint64_t j, flo
 }
 
 void or_vertices(const or_state* st, const double origin[3], uint32_t precision,
-                 int32_t fixed_shift, float* out) {
+                 int32_t fixed_shift, double sphere_radius, float* out) {
     rel_roots R;
-    if (make_rel(st, origin, precision, fixed_shift, &R) == OR_OK) {
+    if (make_rel(st, origin, precision, fixed_shift, sphere_radius, &R) == OR_OK) {
         uint32_t i = 0;
         for (uint32_t s = 0; s < st->cap; ++s)
             if (st->cbt[st->cap + s]) bisector_rel(st, &R, st->heap[s], out + 9u * (size_t)i++);
@@ -824,7 +859,7 @@ int or_update(or_state* st, const or_frame* fr, or_stats* stats) {
 
     /* 2. GenerateCommands, decision part: wishes on the frame-start state. */
     if (fr->mode == OR_MODE_LOD) {
-        rc = make_rel(st, fr->eye, fr->precision, fr->fixed_shift, &R);
+        rc = make_rel(st, fr->eye, fr->precision, fr->fixed_shift, fr->sphere_radius, &R);
         if (rc) goto done;
     }
     for (uint32_t i = 0; i < N; ++i) classify(st, fr, &R, st->heap[L[i]], &sw[L[i]], &mw[L[i]]);

@@ -25,7 +25,7 @@ extern "C" {
 
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ECAPACITY = 2, OR_EDEPTH = 3, OR_ENOMEM = 4, OR_EINTERNAL = 10 };
 enum { OR_MODE_LOD = 0, OR_MODE_FORCE_SPLIT = 1, OR_MODE_FORCE_MERGE = 2, OR_MODE_RANDOM = 3, OR_MODE_LIST = 4 };
-enum { OR_PREC_FP32 = 0, OR_PREC_FIXED = 1, OR_PREC_FP64 = 2 };
+enum { OR_PREC_FP32 = 0, OR_PREC_FIXED = 1, OR_PREC_FP64 = 2, OR_PREC_SPHERE = 3 };
 enum { OR_GATE_CHAIN = 0, OR_GATE_PAPER = 1 };
 
 typedef struct {
@@ -42,6 +42,7 @@ typedef struct {
     uint32_t n_split;
     const uint64_t* merge_list; /* sorted, MODE_LIST only */
     uint32_t n_merge;
+    double sphere_radius;       /* PREC_SPHERE: radius of the sphere about the origin */
 } or_frame;
 
 typedef struct {
@@ -80,7 +81,7 @@ uint32_t or_leaves(const or_state* st, uint32_t* slots, uint64_t* heap, uint32_t
 /* FP32 vertices [N][3][3] of the live bisectors relative to ``origin`` using
  * the given precision form; and the FP64 reference positions (absolute). */
 void or_vertices(const or_state* st, const double origin[3], uint32_t precision,
-                 int32_t fixed_shift, float* out);
+                 int32_t fixed_shift, double sphere_radius, float* out);
 void or_vertices_f64(const or_state* st, double* out);
 void or_root_table(const or_state* st, double* out);
 

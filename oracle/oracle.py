@@ -28,7 +28,7 @@ def _load():
         lib.or_export.argtypes = [P, P, P, P, P, P]
         lib.or_leaves.argtypes = [P, P, P, P]
         lib.or_leaves.restype = C.c_uint32
-        lib.or_vertices.argtypes = [P, P, C.c_uint32, C.c_int32, P]
+        lib.or_vertices.argtypes = [P, P, C.c_uint32, C.c_int32, C.c_double, P]
         lib.or_vertices_f64.argtypes = [P, P]
         lib.or_root_table.argtypes = [P, P]
         lib.or_set_order_seed.argtypes = [P, C.c_uint64]
@@ -68,6 +68,7 @@ class _Frame(C.Structure):
         ("n_split", C.c_uint32),
         ("merge_list", C.c_void_p),
         ("n_merge", C.c_uint32),
+        ("sphere_radius", C.c_double),
     ]
 
 
@@ -142,6 +143,7 @@ class Oracle:
         f.precision = int(fp.precision)
         f.fixed_shift = int(fp.fixed_shift)
         f.gate = int(fp.gate)
+        f.sphere_radius = float(getattr(fp, "sphere_radius", 0.0))
         keep = []
         for name, cnt, arr in (("split_list", "n_split", fp.split_list),
                                ("merge_list", "n_merge", fp.merge_list)):
@@ -191,11 +193,11 @@ class Oracle:
         _lib.or_leaves(self._h, _ptr(slots), _ptr(heap), _ptr(links))
         return slots, heap, links
 
-    def vertices(self, origin, precision=0, fixed_shift=20):
+    def vertices(self, origin, precision=0, fixed_shift=20, sphere_radius=0.0):
         n = self.live_count
         out = np.zeros((n, 3, 3), np.float32)
         o = np.ascontiguousarray(origin, np.float64)
-        _lib.or_vertices(self._h, _ptr(o), precision, fixed_shift, _ptr(out))
+        _lib.or_vertices(self._h, _ptr(o), precision, fixed_shift, float(sphere_radius), _ptr(out))
         return out
 
     def vertices_f64(self):

@@ -109,6 +109,7 @@ class Frame(C.Structure):
         ("n_merge", C.c_uint32),
         ("vertices_out", C.c_void_p),
         ("vertices_cap", C.c_uint32),
+        ("sphere_radius", C.c_double),
     ]
 
 
@@ -181,6 +182,7 @@ def frame_struct(fp, device, vertices_out=None) -> tuple:
     f.precision = int(fp.precision)
     f.fixed_shift = int(fp.fixed_shift)
     f.gate = int(fp.gate)
+    f.sphere_radius = float(getattr(fp, "sphere_radius", 0.0))
     keep = []
     for name, cnt, arr in (("split_list", "n_split", getattr(fp, "split_list", ())),
                            ("merge_list", "n_merge", getattr(fp, "merge_list", ()))):

@@ -44,7 +44,7 @@ uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems;
 
 // Per-instance arrays.
 struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, root64, rel, batch, total;
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, root64, rel, batch, total;
     uint32_t cap, W, ch;
 };
 
@@ -106,6 +106,7 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.grp = take(16u * cap);
     L.chg = take(4u * cap);
     L.chgr = take(16u * cap);
+    L.vc = take(36u * cap);
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
     const uint32_t Hh = static_cast<uint32_t>(H);
@@ -118,7 +119,8 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
 int check_launch() { return cudaGetLastError() == cudaSuccess ? CBT_OK : CBT_ECUDA; }
 
 bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
-    if (!f || f->precision > 2u || f->mode > 4u || f->nplanes > 5u || f->gate > 1u) return false;
+    if (!f || f->precision > 3u || f->mode > 4u || f->nplanes > 5u || f->gate > 1u) return false;
+    if (f->precision == 3u && !(f->sphere_radius > 0.0 && f->sphere_radius < 1e300)) return false;
     if (f->fixed_shift < 0 || f->fixed_shift > 62) return false;
     if (f->mode == CBT_MODE_LIST && ((f->n_split && !f->split_list) || (f->n_merge && !f->merge_list)))
         return false;
@@ -132,6 +134,7 @@ bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
     fp.mode = f->mode;
     fp.seed = f->seed;
     fp.precision = f->precision;
+    fp.radius = f->sphere_radius;
     fp.shift = f->fixed_shift;
     fp.gate = f->gate;
     fp.split_list = f->split_list;
@@ -511,6 +514,7 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     I.grp = reinterpret_cast<uint4*>(b + L.grp);
     I.chg = reinterpret_cast<uint32_t*>(b + L.chg);
     I.chgr = reinterpret_cast<uint4*>(b + L.chgr);
+    I.vc = reinterpret_cast<float*>(b + L.vc);
     I.root64 = reinterpret_cast<double*>(b + L.root64);
     I.rel = b + L.rel;
     I.cap = L.cap;

@@ -17,6 +17,9 @@
 //                    smallest member it is, or of a split wish's chain
 //   chg[cap]   u32   live indices of the frame's changed bisectors, ascending
 //   chgr[cap]  uint4 the same as records {live index, slot, cmd, dest}
+//   vc[cap]    9 x f32 in the sphere form, the vertices the LOD test
+//                    evaluated this frame (valid while the slot's cmd has
+//                    kVcValid), copied by the vertex export
 //   root64[H*9], rel[H*9]: root vertices (FP64) and their per-frame offsets
 //                    from the camera (FP32, fixed point or FP64)
 // and, per batch (a single instance carries a batch of one), the instance
@@ -41,6 +44,7 @@ constexpr uint32_t kDepthOdd = 1u << 7;
 constexpr uint32_t kHeapOdd = 1u << 8;
 constexpr uint32_t kCand = 1u << 9;    // smallest member of a mergeable group (members in grp[i])
 constexpr uint32_t kGrpMin = 1u << 10; // smallest member of a merge group whose members are in grp[i]
+constexpr uint32_t kVcValid = 1u << 11; // vc[slot] holds this frame's vertices (sphere form, one-launch frame)
 
 // Edge indices of a bisector: Twin (v0,v1), Next (v1,v2), Prev (v2,v0).
 constexpr int kT = 0, kNe = 1, kPe = 2;
@@ -89,6 +93,7 @@ struct Inst {
     uint4* grp;  // per live index: members of the group whose smallest member it is
     uint32_t* chg;  // live indices of the changed bisectors, in ascending slot order
     uint4* chgr;    // one-launch frame: per changed bisector {live index, slot, cmd, dest}
+    float* vc;      // per slot, the frame's FP32 vertices [3][3] (sphere form, one-launch frame)
     double* root64;
     void* rel;
     Globals* g;
@@ -111,6 +116,7 @@ struct FrameP {
     uint32_t frame;  // frame counter (RANDOM mode key)
     float* vout;     // optional vertex export, vcap rows of 9 floats
     uint32_t vcap;
+    double radius;   // precision 3: radius of the sphere about the world origin
 };
 
 constexpr int kFramePhases = 10;  // phases of the one-launch frame (a batch skips the last)
@@ -298,14 +304,82 @@ __device__ __forceinline__ float i128_to_float(__int128 s) {
     return neg ? -f : f;
 }
 
-// Vertices of a bisector relative to the frame's origin, rounded to FP32:
-//   FP32:  (w0 R0 + w1 R1) + w2 R2, w = float(W) 2^-d (no contraction);
-//   FIXED: float(sum W X) 2^-(d + shift), the sum exact in 128 bits;
-//   FP64:  float((w0 D0 + w1 D1) + w2 D2), w = double(W) 2^-d.
+// Vertex v (0..2) of a bisector relative to the frame's origin, rounded to
+// FP32, into r[0..2]:
+//   FP32:   (w0 R0 + w1 R1) + w2 R2, w = float(W) 2^-d (no contraction);
+//   FIXED:  float(sum W X) 2^-(d + shift), the sum exact in 128 bits;
+//   FP64:   float((w0 D0 + w1 D1) + w2 D2), w = double(W) 2^-d;
+//   SPHERE: the FP64 point p of the flat root triangle (V absolute) moved
+//           radially onto the sphere about the world origin, relative to the
+//           eye, rounded to FP32; with fused multiply-adds:
+//             p_c = fma(w2, V2c, fma(w1, V1c, w0 V0c)),
+//             n2  = fma(pz, pz, fma(py, py, px px)),
+//             y   = 1 / sqrt(n2): the FP32 estimate 1 / sqrtf(float(n2)),
+//                   then twice y = fma(y/2, fma(-n2, y y, 1), y) (Newton),
+//             r_c = float(fma(p_c, radius y, -eye_c)).
 template <typename T>
-__device__ __forceinline__ void eval_vertices(const T W[9], int d, uint32_t precision, int shift,
-                                              const void* rel, uint32_t h, float r[9]) {
-    if (precision == 1) {
+__device__ __forceinline__ void eval_vertex(const T W[9], int v, int d, const FrameP& fp, const void* rel,
+                                            uint32_t h, float r[3]) {
+    const uint32_t precision = fp.precision;
+    if (precision == 3) {
+        const double* V = static_cast<const double*>(rel) + 9u * h;
+        const double sc = pow2d(-d);
+        const double w0 = __dmul_rn(__ull2double_rn(W[3 * v + 0]), sc);
+        const double w1 = __dmul_rn(__ull2double_rn(W[3 * v + 1]), sc);
+        const double w2 = __dmul_rn(__ull2double_rn(W[3 * v + 2]), sc);
+        double p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] = __fma_rn(w2, V[6 + c], __fma_rn(w1, V[3 + c], __dmul_rn(w0, V[c])));
+        const double n2 = __fma_rn(p[2], p[2], __fma_rn(p[1], p[1], __dmul_rn(p[0], p[0])));
+        double y = (double)__frcp_rn(__fsqrt_rn(__double2float_rn(n2)));
+#pragma unroll
+        for (int it = 0; it < 2; ++it) y = __fma_rn(__dmul_rn(y, 0.5), __fma_rn(-n2, __dmul_rn(y, y), 1.0), y);
+        const double f = __dmul_rn(fp.radius, y);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = __double2float_rn(__fma_rn(p[c], f, -fp.eye[c]));
+    } else if (precision == 1) {
+        const long long* X = static_cast<const long long*>(rel) + 9u * h;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            __int128 s = (__int128)(unsigned long long)W[3 * v + 0] * (__int128)X[c];
+            s += (__int128)(unsigned long long)W[3 * v + 1] * (__int128)X[3 + c];
+            s += (__int128)(unsigned long long)W[3 * v + 2] * (__int128)X[6 + c];
+            r[c] = __fmul_rn(i128_to_float(s), pow2f(-(d + fp.shift)));
+        }
+    } else if (precision == 2) {
+        const double* Dp = static_cast<const double*>(rel) + 9u * h;
+        const double sc = pow2d(-d);
+        const double w0 = __dmul_rn(__ull2double_rn(W[3 * v + 0]), sc);
+        const double w1 = __dmul_rn(__ull2double_rn(W[3 * v + 1]), sc);
+        const double w2 = __dmul_rn(__ull2double_rn(W[3 * v + 2]), sc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double t = __dadd_rn(__dadd_rn(__dmul_rn(w0, Dp[c]), __dmul_rn(w1, Dp[3 + c])),
+                                       __dmul_rn(w2, Dp[6 + c]));
+            r[c] = __double2float_rn(t);
+        }
+    } else {
+        const float* R = static_cast<const float*>(rel) + 9u * h;
+        const float sc = pow2f(-d);
+        const float w0 = __fmul_rn(__ull2float_rn(W[3 * v + 0]), sc);
+        const float w1 = __fmul_rn(__ull2float_rn(W[3 * v + 1]), sc);
+        const float w2 = __fmul_rn(__ull2float_rn(W[3 * v + 2]), sc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            r[c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])), __fmul_rn(w2, R[6 + c]));
+    }
+}
+
+// All three vertices, r[3 v + c] (the same roundings as eval_vertex; the
+// root table is read once for the three).
+template <typename T>
+__device__ __forceinline__ void eval_vertices(const T W[9], int d, const FrameP& fp, const void* rel, uint32_t h,
+                                              float r[9]) {
+    const uint32_t precision = fp.precision;
+    if (precision == 3) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) eval_vertex<T>(W, v, d, fp, rel, h, r + 3 * v);
+    } else if (precision == 1) {
         const long long* X = static_cast<const long long*>(rel) + 9u * h;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -314,7 +388,7 @@ __device__ __forceinline__ void eval_vertices(const T W[9], int d, uint32_t prec
                 __int128 s = (__int128)(unsigned long long)W[3 * i + 0] * (__int128)X[c];
                 s += (__int128)(unsigned long long)W[3 * i + 1] * (__int128)X[3 + c];
                 s += (__int128)(unsigned long long)W[3 * i + 2] * (__int128)X[6 + c];
-                r[3 * i + c] = __fmul_rn(i128_to_float(s), pow2f(-(d + shift)));
+                r[3 * i + c] = __fmul_rn(i128_to_float(s), pow2f(-(d + fp.shift)));
             }
     } else if (precision == 2) {
         const double* Dp = static_cast<const double*>(rel) + 9u * h;
@@ -341,8 +415,7 @@ __device__ __forceinline__ void eval_vertices(const T W[9], int d, uint32_t prec
             const float w2 = __fmul_rn(__ull2float_rn(W[3 * i + 2]), sc);
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-                r[3 * i + c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])),
-                                         __fmul_rn(w2, R[6 + c]));
+                r[3 * i + c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])), __fmul_rn(w2, R[6 + c]));
         }
     }
 }

@@ -259,7 +259,7 @@ __device__ __forceinline__ void walk_list(const Inst& I, const uint2* s_list, ui
 __device__ __forceinline__ void classify_one(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i, uint32_t s,
                                              uint64_t j, const uint32_t* s_tab, uint32_t* s_cnt, bool chain,
                                              uint32_t* s_n, uint2* s_list) {
-    const uint32_t cmd = classify_item(I, fp, key, i, s, j, s_tab, s_cnt);
+    const uint32_t cmd = classify_item(I, fp, key, i, s, j, s_tab, s_cnt, fp.precision == 3 && fp.vout);
     const bool split = (cmd & kSplitWish) && chain;
     const bool group = (cmd & kMergeWish) && !(cmd & kHeapOdd);
     if (split || group) s_list[atomicAdd(s_n, 1u)] = make_uint2(i | (split ? 0x80000000u : 0u), s);
@@ -834,7 +834,7 @@ __device__ void phase_compact(const BatchDev& bt, FCtx& c, const uint32_t* s_tab
             const uint32_t lim = fp.vcap;
             for (uint32_t k = threadIdx.x; k < tot; k += blockDim.x) {
                 const uint32_t i = before + k;
-                if (i < lim) vertex_item(I, fp, i, I.heap[s_buf[k]], s_tab, fp.vout);
+                if (i < lim) vertex_item_cached(I, fp, i, s_buf[k], s_tab, fp.vout);
             }
         }
         __syncthreads();
@@ -848,7 +848,9 @@ __device__ void phase_compact(const BatchDev& bt, FCtx& c, const uint32_t* s_tab
 #endif
 
 // P9 (single instance): the vertices of the new live list, strided over the
-// whole grid (word tiles hold very different live counts); the slot and
+// whole grid (word tiles hold very different live counts). In the sphere
+// form the unchanged bisectors' vertices are copied from the cache P1 filled
+// (each costs three FP64 projections to evaluate); otherwise the slot and
 // heap ID of the next round are loaded while the current one is evaluated.
 __device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_tab) {
     ctx_tile(bt, bt.tile_base, 0, 1, c);
@@ -857,6 +859,11 @@ __device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_ta
     if (!fp.vout) return;
     const uint32_t n = min(__ldcg(I.sums + 1), fp.vcap);
     const uint32_t stride = gridDim.x * kFThreads;
+    if (fp.precision == 3) {  // the LOD test's vertices are cached for the unchanged bisectors
+        for (uint32_t i = blockIdx.x * kFThreads + threadIdx.x; i < n; i += stride)
+            vertex_item_cached(I, fp, i, I.live[i], s_tab, fp.vout);
+        return;
+    }
     uint32_t i = blockIdx.x * kFThreads + threadIdx.x;
     uint64_t j = i < n ? I.heap[I.live[i]] : 0ull;
     for (; i < n; i += stride) {

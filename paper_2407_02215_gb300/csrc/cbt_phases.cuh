@@ -219,6 +219,8 @@ __device__ __forceinline__ void rel_entry(const BatchDev& bt, uint32_t e) {
         static_cast<long long*>(I.rel)[le] = x;
     } else if (fp.precision == 2) {
         static_cast<double*>(I.rel)[le] = diff;
+    } else if (fp.precision == 3) {
+        static_cast<double*>(I.rel)[le] = I.root64[le];  // absolute: the projection needs it
     } else {
         static_cast<float*>(I.rel)[le] = __double2float_rn(diff);
     }
@@ -274,16 +276,38 @@ static __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
 
 template <typename T>
 __device__ __forceinline__ void lod_wishes(const Inst& I, const FrameP& fp, uint64_t j, int d,
-                                           uint32_t h, const uint32_t* tab, bool& split, bool& merge) {
+                                           uint32_t h, const uint32_t* tab, bool& split, bool& merge,
+                                           float* keep) {
     T W[9], Wp[9];
     decode_weights<T>(j, d, W, Wp, tab);
     float r[9];
-    eval_vertices<T>(W, d, fp.precision, fp.shift, I.rel, h, r);
+    eval_vertices<T>(W, d, fp, I.rel, h, r);
+    if (keep)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) keep[k] = r[k];
     split = lod_test(r, fp) == 3u && d < (int)I.max_depth;
     merge = false;
     if (!split && d >= 1) {
-        eval_vertices<T>(Wp, d - 1, fp.precision, fp.shift, I.rel, h, r);
-        merge = lod_test(r, fp) != 3u;
+        // Two vertices of the parent are the child's: a 0 bit makes the
+        // child's rows (2 r0, 2 r2, r0 + r1) of the parent's, a 1 bit
+        // (2 r2, 2 r1, r0 + r1) (Eq. 1), and a row doubled over a doubled
+        // denominator evaluates to the same value in every precision form.
+        // The new vertex is the parent's v0 (1 bit) or v1 (0 bit); the row
+        // is picked by selects so that every lane takes the same path.
+        const bool odd = (j & 1ull) != 0ull;
+        T row[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) row[k] = odd ? Wp[k] : Wp[3 + k];
+        float nv[3];
+        eval_vertex<T>(row, 0, d - 1, fp, I.rel, h, nv);
+        float q[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q[c] = odd ? nv[c] : r[c];
+            q[3 + c] = odd ? r[3 + c] : nv[c];
+            q[6 + c] = odd ? r[c] : r[3 + c];
+        }
+        merge = lod_test(q, fp) != 3u;
     }
 }
 
@@ -359,18 +383,24 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
 // reading R8 (mode 0), forced splits or merges, seeded random requests, or
 // sorted request lists. Returns false when j does not decode to a root of
 // this mesh.
+//
+// keep (optional): where the LOD test's vertices of j are stored (only the
+// LOD mode evaluates them; `kept` says whether it did).
 __device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uint64_t key, uint64_t j,
-                                            const uint32_t* tab, bool& split, bool& merge) {
+                                            const uint32_t* tab, bool& split, bool& merge, float* keep = nullptr,
+                                            bool* kept = nullptr) {
     const int d = depth_of(j, I.ch);
     const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
     split = merge = false;
+    if (kept) *kept = false;
     if (d < 0 || h >= I.H) return false;
     switch (fp.mode) {
         case 0:
             if (d <= 31)
-                lod_wishes<uint32_t>(I, fp, j, d, h, tab, split, merge);
+                lod_wishes<uint32_t>(I, fp, j, d, h, tab, split, merge, keep);
             else
-                lod_wishes<unsigned long long>(I, fp, j, d, h, tab, split, merge);
+                lod_wishes<unsigned long long>(I, fp, j, d, h, tab, split, merge, keep);
+            if (kept) *kept = keep != nullptr;
             break;
         case 1:
             split = d < (int)I.max_depth;
@@ -390,10 +420,14 @@ __device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uin
     return true;
 }
 
+// With `cache` (the one-launch frame exporting sphere-form vertices) the LOD
+// test's vertices go to vc[s] and the command word says so (kVcValid): the
+// export then copies them instead of projecting again in FP64.
 __device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
-                                                  uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt) {
-    bool split, merge;
-    if (!item_wishes(I, fp, key, j, tab, split, merge)) {
+                                                  uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt,
+                                                  bool cache = false) {
+    bool split, merge, kept;
+    if (!item_wishes(I, fp, key, j, tab, split, merge, cache ? I.vc + 9ull * s : nullptr, &kept)) {
         set_err(I.g, kErrLink);
         *cmd_ptr(I, s) = 0u;
         I.scan[i] = 0u;
@@ -401,7 +435,7 @@ __device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& f
     }
     const int d = depth_of(j, I.ch);
     const uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
-                         ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u);
+                         ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u) | (kept ? kVcValid : 0u);
     *cmd_ptr(I, s) = cmd;
     // the paper's gate charges 3d + 4 without walking the chain (k_walk
     // computes the exact chain cost otherwise)
@@ -674,6 +708,7 @@ static __device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint3
         }
         I.nb[slots[l]] = make_uint4(lk[0], lk[1], lk[2], rv);
         I.heap[slots[l]] = (j << f.shift[l]) + f.off[l];
+        *cmd_ptr(I, slots[l]) = 0u;  // a new record: no cached vertices
         set_bit(I, slots[l]);
     }
 }
@@ -714,6 +749,7 @@ static __device__ void fill_merge(const Inst& I, uint32_t dest, const uint4 m, u
         I.nb[ps[pk]] = make_uint4(tw, xb.slot[kT][0], xa.slot[kT][0],
                                   rvT | (xb.rev[kT][0] << 2) | (xa.rev[kT][0] << 4));
         I.heap[ps[pk]] = ju >> 1;
+        *cmd_ptr(I, ps[pk]) = 0u;  // a new record: no cached vertices
         set_bit(I, ps[pk]);
     }
 }
@@ -736,15 +772,30 @@ __device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uin
     if (d <= 31) {
         uint32_t W[9], Wp[9];
         decode_weights<uint32_t>(j, d, W, Wp, tab);
-        eval_vertices<uint32_t>(W, d, fp.precision, fp.shift, I.rel, h, r);
+        eval_vertices<uint32_t>(W, d, fp, I.rel, h, r);
     } else {
         unsigned long long W[9], Wp[9];
         decode_weights<unsigned long long>(j, d, W, Wp, tab);
-        eval_vertices<unsigned long long>(W, d, fp.precision, fp.shift, I.rel, h, r);
+        eval_vertices<unsigned long long>(W, d, fp, I.rel, h, r);
     }
     float* o = out + 9ull * i;
 #pragma unroll
     for (int k = 0; k < 9; ++k) o[k] = r[k];
+}
+
+// Vertices of the live bisector in slot s at output row i: in the sphere
+// form copied from the frame's cache when the LOD test stored them, else
+// evaluated.
+__device__ __forceinline__ void vertex_item_cached(const Inst& I, const FrameP& fp, uint32_t i, uint32_t s,
+                                                   const uint32_t* tab, float* out) {
+    if (fp.precision == 3 && (*cmd_ptr(I, s) & kVcValid)) {
+        const float* src = I.vc + 9ull * s;
+        float* o = out + 9ull * i;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) o[k] = src[k];
+    } else {
+        vertex_item(I, fp, i, I.heap[s], tab, out);
+    }
 }
 
 

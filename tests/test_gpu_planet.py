@@ -87,3 +87,25 @@ def test_planet_precision_report(P):
             assert (e <= bound).all(), name
     print(f"planet vertex error (mm); nearest bisector {dist.min():.0f} m away:", errs)
     assert errs["fp32"]["max_mm"] > 10.0
+
+
+def test_dodecahedron_planet_sphere_projection(P):
+    """The paper's planet shape (Sec. 4): dodecahedron base, vertices
+    projected onto the Earth-sized sphere in FP64 (PREC_SPHERE), every 3rd
+    frame of the descent on a 2^15 pool (saturated near the ground), state
+    identical to the oracle's; then the exported sphere vertices of one more
+    frame are bit-identical to the oracle's."""
+    import torch
+    spec = W.configs.config_dodeca(n_frames=300, D=15)
+    frames = spec.frames[::3]
+    g, o = run_pair(spec.mesh, 15, spec.max_depth, frames[:-1], P.CBT, Oracle, check_every=10)
+    fp = frames[-1]
+    vbuf = torch.empty((1 << 15, 3, 3), dtype=torch.float32, device="cuda")
+    g.update(fp, vertices_out=vbuf)
+    o.update(fp)
+    torch.cuda.synchronize()
+    n = o.live_count
+    assert g.live_count() == n
+    vo = o.vertices(fp.eye, 3, 20, fp.sphere_radius)
+    vg = vbuf[:n].cpu().numpy()
+    assert np.array_equal(vg.view(np.uint32), vo.view(np.uint32))

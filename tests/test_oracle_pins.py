@@ -267,3 +267,50 @@ def test_textbook_order_independence():
             assert sa == sb
             for x, y in zip(a.leaves(), b.leaves()):
                 assert np.array_equal(x, y)
+
+
+def test_dodecahedron_mesh():
+    """The planet base of the paper's scenes (Sec. 4, H = 60): 12 planar
+    pentagons, every directed edge twinned once, outward orientation, every
+    vertex on the sphere."""
+    R = 6.371e6
+    m = W.meshes.dodecahedron_mesh(R)
+    assert m.F == 12 and list(m.face_sizes) == [5] * 12 and m.H == 60
+    assert np.allclose(np.linalg.norm(m.pos, axis=1), R, rtol=1e-15, atol=0)
+    edges = set()
+    off = 0
+    for f in range(m.F):
+        idx = list(m.face_verts[off:off + 5])
+        off += 5
+        P = m.pos[idx]
+        c = P.mean(0)
+        n = np.cross(P[1] - P[0], P[2] - P[0])
+        assert np.dot(n, c) > 0  # outward, counter-clockwise seen from outside
+        assert np.abs((P - c) @ (n / np.linalg.norm(n))).max() < 1e-9 * R  # planar
+        for k in range(5):
+            edges.add((idx[k], idx[(k + 1) % 5]))
+    assert len(edges) == 60 and all((b, a) in edges for a, b in edges)
+
+
+def test_sphere_projection_properties():
+    """PREC_SPHERE (R13 reading): after four uniform levels on the
+    dodecahedron, every exported vertex plus the eye lies on the sphere to
+    FP32 rounding of the camera-relative coordinate, and points the same way
+    from the centre as the flat FP64 vertex it comes from (radial move); the
+    mesh vertices themselves stay put."""
+    R = 6.371e6
+    m = W.meshes.dodecahedron_mesh(R)
+    o = Oracle(m, 12, 8)
+    for _ in range(4):
+        o.update(forced_params(MODE_FORCE_SPLIT))
+    eye = np.array([0.1 * R, -0.2 * R, 1.05 * R])
+    v = o.vertices(eye, 3, 20, R).reshape(-1, 3).astype(np.float64)
+    flat = o.vertices_f64().reshape(-1, 3)
+    on = v + eye
+    ulp = np.spacing(np.abs(v).max(axis=1).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(np.linalg.norm(on, axis=1) - R) <= 2.0 * ulp + 1e-9 * R)
+    cross = np.linalg.norm(np.cross(on, flat), axis=1) / (np.linalg.norm(on, axis=1) * np.linalg.norm(flat, axis=1))
+    assert cross.max() < 1e-6
+    assert np.all(np.einsum("ij,ij->i", on, flat) > 0)
+    corner = np.isclose(np.linalg.norm(flat, axis=1), R, rtol=1e-12)
+    assert corner.any() and np.allclose(on[corner], flat[corner], rtol=0, atol=2.0 * ulp[corner].max())

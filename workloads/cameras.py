@@ -20,6 +20,8 @@ import numpy as np
 MODE_LOD, MODE_FORCE_SPLIT, MODE_FORCE_MERGE, MODE_RANDOM, MODE_LIST = 0, 1, 2, 3, 4
 # Vertex-evaluation precision (frame parameter ``precision``).
 PREC_FP32, PREC_FIXED, PREC_FP64 = 0, 1, 2
+# Vertices projected onto a sphere about the origin, evaluated in FP64.
+PREC_SPHERE = 3
 # Gate (frame parameter ``gate``).
 GATE_CHAIN, GATE_PAPER = 0, 1
 
@@ -50,6 +52,7 @@ class FrameParams:
     gate: int = GATE_CHAIN
     split_list: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint64))
     merge_list: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint64))
+    sphere_radius: float = 0.0  # PREC_SPHERE: radius of the sphere about the origin
 
 
 def camera_basis(cam: Camera):
@@ -153,4 +156,30 @@ def descent_path(mesh, n_frames: int, seed: int, alt_hi=2e7, alt_lo=2.0):
         alt = np.exp(np.log(alt_hi) + (np.log(alt_lo) - np.log(alt_hi)) * t)
         eye = target + nrm * alt
         cams.append(Camera(eye=eye, target=target + tang * 10.0 * alt, up=nrm))
+    return cams
+
+
+def sphere_descent_path(mesh, radius: float, n_frames: int, seed: int, alt_hi=2e7, alt_lo=2.0):
+    """Descent onto a sphere of the given radius about the origin: a seeded
+    interior point of one coarse face, projected onto the sphere, is the
+    target; the altitude above the sphere is log-spaced alt_hi -> alt_lo;
+    the camera looks at target + tangent * 10 * altitude; up = the radial
+    direction."""
+    rng = np.random.default_rng(seed)
+    f = int(rng.integers(mesh.F))
+    off = int(mesh.face_sizes[:f].sum())
+    idx = mesh.face_verts[off:off + int(mesh.face_sizes[f])]
+    P = mesh.pos[idx]
+    w = rng.dirichlet(np.ones(len(idx)))
+    nrm = (w[:, None] * P).sum(0)
+    nrm /= np.linalg.norm(nrm)
+    target = nrm * radius
+    tang = P[1] - P[0]
+    tang -= nrm * np.dot(tang, nrm)
+    tang /= np.linalg.norm(tang)
+    cams = []
+    for k in range(n_frames):
+        t = k / max(1, n_frames - 1)
+        alt = np.exp(np.log(alt_hi) + (np.log(alt_lo) - np.log(alt_hi)) * t)
+        cams.append(Camera(eye=nrm * (radius + alt), target=target + tang * 10.0 * alt, up=nrm))
     return cams

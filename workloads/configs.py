@@ -67,6 +67,19 @@ def config3(n_frames: int = 600, tau_px: float = 4.0, precision: int = C.PREC_FI
     return InstanceSpec("planet", mesh, D, 48, frames)
 
 
+def config_dodeca(n_frames: int = 300, tau_px: float = 14.0, D: int = 17, max_depth: int = 50,
+                  radius: float = 6.371e6) -> InstanceSpec:
+    """The paper's planet scene shape (Sec. 4 and Table 3): a regular
+    dodecahedron base (60 halfedges) on an Earth-sized sphere, pool 2^17,
+    vertices projected onto the sphere during refinement, triangles of about
+    49 px (a refinement edge of 14 px), a seeded descent from 2e7 m to 2 m
+    above the sphere."""
+    mesh = M.dodecahedron_mesh(radius)
+    cams = C.sphere_descent_path(mesh, radius, n_frames, seed=17)
+    frames = [C.frame_params(c, tau_px, precision=C.PREC_SPHERE, sphere_radius=radius) for c in cams]
+    return InstanceSpec("dodeca-planet", mesh, D, max_depth, frames)
+
+
 def config4(n_inst: int = 256, n_frames: int = 64, seed: int = 4, tau_px: float = 4.0,
             h_max: int = 40000) -> list[InstanceSpec]:
     rng = np.random.default_rng(seed)

@@ -155,3 +155,32 @@ def cube_sphere_mesh(n: int = 8, radius: float = 6.371e6) -> PolyMesh:
                         quad = quad[::-1]
                     faces.append(quad)
     return _mesh(f"cubesphere{n}", faces, np.asarray(pos), fp32=False)
+
+
+def dodecahedron_mesh(radius: float = 6.371e6) -> PolyMesh:
+    """Regular dodecahedron inscribed in a sphere of the given radius: 20
+    vertices, 12 planar pentagons (60 halfedges), outward counter-clockwise
+    faces, FP64 positions. Each face is the five vertices farthest along one
+    of the 12 directions (0, +-phi, +-1) and their cyclic permutations."""
+    phi = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(x, y, z) for x in (-1.0, 1.0) for y in (-1.0, 1.0) for z in (-1.0, 1.0)]
+    for a in (-1.0 / phi, 1.0 / phi):
+        for b in (-phi, phi):
+            v += [(0.0, a, b), (a, b, 0.0), (b, 0.0, a)]
+    pos = np.asarray(v, np.float64) * (radius / 3.0 ** 0.5)
+    normals = []
+    for a in (-1.0, 1.0):
+        for b in (-phi, phi):
+            normals += [(0.0, b, a), (b, a, 0.0), (a, 0.0, b)]
+    faces = []
+    for n in np.asarray(normals, np.float64):
+        n = n / np.linalg.norm(n)
+        d = pos @ n
+        idx = np.argsort(-d)[:5]
+        c = pos[idx].mean(0)
+        e1 = pos[idx[0]] - c
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(n, e1)
+        ang = np.arctan2((pos[idx] - c) @ e2, (pos[idx] - c) @ e1)
+        faces.append([int(k) for k in idx[np.argsort(ang)]])
+    return _mesh("dodecahedron", faces, pos, fp32=False)
