@@ -497,16 +497,23 @@ def bench_serve(args):
 
     from paper_2407_02215_gb300.serving import ServeLoop
     specs = W.configs.config5(n_inst=args.instances, n_planets=args.planets, n_frames=args.frames)
-    loop = ServeLoop(specs, hbm_budget_bytes=int(args.hbm_budget_gb * 2**30), inflight=2, max_batch=4096)
-    torch.cuda.synchronize()
     rates = [float(r) for r in args.rates.split(",")]
-    out = []
-    loop.run(rates[0], 0.5, seed=99)  # warm-up
-    for r in rates:
-        out.append(loop.run(r, args.duration, seed=int(r)))
+    forms = {}
+    for name, fused in (("per_step_overlapped_ticks", False), ("fused_serial_ticks", True)):
+        loop = ServeLoop(specs, hbm_budget_bytes=int(args.hbm_budget_gb * 2**30), inflight=2, max_batch=4096,
+                         fused=fused)
+        torch.cuda.synchronize()
+        out = []
+        loop.run(rates[0], 0.5, seed=99)  # warm-up
+        for r in rates:
+            out.append(loop.run(r, args.duration, seed=int(r)))
+        forms[name] = out
+        admitted, rejected, used = len(loop.specs), len(loop.rejected), loop.hbm_used
+        del loop
+        torch.cuda.synchronize()
     return {"metric": "served LOD-update requests: latency and throughput", "unit": "ms / bisectors/s",
-            "admitted": len(loop.specs), "rejected": len(loop.rejected),
-            "hbm_used_gb": loop.hbm_used / 2**30, "rates": out,
+            "admitted": admitted, "rejected": rejected,
+            "hbm_used_gb": used / 2**30, "rates": forms["per_step_overlapped_ticks"], "forms": forms,
             "config": {"workload": f"served: {len(specs)} instances ({args.instances} batch-like + "
                                    f"{args.planets} planets), Poisson arrivals, HBM budget {args.hbm_budget_gb} GB"}}
 

@@ -337,6 +337,15 @@ int cbt_server_poll(cbt_server* sv, int32_t ticket, int wait, uint32_t* live_bef
 /* 1 if the slot the next submit will use is free. */
 int32_t cbt_server_next_slot_free(const cbt_server* sv);
 
+/* Tick form. Not fused (the default): a tick is one launch per step, and a
+ * tick submitted on another stream overlaps the running one on the device.
+ * Fused: a tick is one cooperative launch of the whole frame (cbt_set_fused),
+ * and each tick waits on the device for the previous one (two cooperative
+ * launches are never in flight together); submission, admission and
+ * polling still overlap the running tick. Switch only with no tick pending
+ * (CBT_EINVAL otherwise). Results are identical either way. Host only. */
+int cbt_server_set_fused(cbt_server* sv, int on);
+
 /* Releases the server (waiting for outstanding ticks); workspaces stay the
  * caller's. */
 void cbt_server_destroy(cbt_server* sv);

@@ -82,6 +82,7 @@ def load(path: str | None = None):
     lib.cbt_phase_name.argtypes = [U32]
     lib.cbt_phase_name.restype = C.c_char_p
     lib.cbt_sum_reduce.argtypes = [P, I32, P, P]
+    lib.cbt_server_set_fused.argtypes = [P, C.c_int]
     lib.cbt_set_fused.argtypes = [P, C.c_int, P]
     lib.cbt_fused.argtypes = [P]
     lib.cbt_batch_set_fused.argtypes = [P, C.c_int, P]
@@ -430,6 +431,12 @@ class Server:
         if getattr(self, "_h", None) is not None and _lib is not None:
             _lib.cbt_server_destroy(self._h)
             self._h = None
+
+    def set_fused(self, on: bool = True):
+        """Ticks as one cooperative launch each, one at a time on the device."""
+        rc = _lib.cbt_server_set_fused(self._h, 1 if on else 0)
+        if rc:
+            raise CBTError(rc, "cbt_server_set_fused")
 
     def next_slot_free(self) -> bool:
         return bool(_lib.cbt_server_next_slot_free(self._h))

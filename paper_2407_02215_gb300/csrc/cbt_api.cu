@@ -887,8 +887,11 @@ struct cbt_server {
     uint32_t status_words = 0;
     size_t slot_bytes = 0;
     uint32_t tw = 256, grid_mult = 8;
+    bool fused = false;  // ticks as one cooperative launch each, one at a time on the device
+    int frame_per_sm = 0;
     std::vector<ServerSlot> slots;
     uint32_t next = 0;
+    bool any_tick = false;
 };
 
 extern "C" size_t cbt_server_workspace_bytes(cbt_state* const* states, int32_t n, int32_t inflight) {
@@ -930,9 +933,12 @@ extern "C" int cbt_server_create(cbt_state* const* states, int32_t n, int32_t in
         ServerSlot& S = sv->slots[r];
         S.dev = static_cast<char*>(workspace) + L.total * static_cast<size_t>(r);
         if (cudaMallocHost(reinterpret_cast<void**>(&S.host), L.block + 4u * sv->n) != cudaSuccess ||
-            cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMemset(S.dev + L.bg, 0, sizeof(BatchGlobals)) != cudaSuccess)  // grid-barrier counters
             rc = CBT_ECUDA;
     }
+    sv->frame_per_sm = frame_blocks_per_sm();
+    if (!rc && sv->frame_per_sm <= 0) rc = CBT_ECUDA;
     if (rc) {
         for (auto& S : sv->slots) {
             if (S.host) cudaFreeHost(S.host);
@@ -976,6 +982,12 @@ extern "C" int cbt_server_submit(cbt_server* sv, const int32_t* idx, const cbt_f
         hr[i + 1] = hr[i] + 9u * st->inst.H;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // a fused tick starts after the previous tick (two cooperative launches
+    // are never in flight together)
+    if (sv->fused && sv->any_tick) {
+        const uint32_t prev = (r + static_cast<uint32_t>(sv->slots.size()) - 1u) % static_cast<uint32_t>(sv->slots.size());
+        if (cudaStreamWaitEvent(s, sv->slots[prev].done, 0) != cudaSuccess) return CBT_ECUDA;
+    }
     if (cudaMemcpyAsync(S.dev, S.host, L.block, cudaMemcpyHostToDevice, s) != cudaSuccess) return CBT_ECUDA;
     BatchDev bt{};
     bt.inst = reinterpret_cast<const Inst*>(S.dev + L.inst);
@@ -994,7 +1006,13 @@ extern "C" int cbt_server_submit(cbt_server* sv, const int32_t* idx, const cbt_f
     bt.Twords = hw[kk];
     bt.Trel = hr[kk];
     bt.nout = reinterpret_cast<uint32_t*>(S.dev + L.nout);
-    enqueue_kernels(bt, sv->sms, sv->grid_mult, vertices, s, nullptr);
+    if (sv->fused) {
+        const uint32_t work = std::max({bt.Titems, bt.Twords, (bt.Trel + 255u) / 256u, 1u});
+        const uint32_t grid = std::min(work, static_cast<uint32_t>(sv->frame_per_sm * sv->sms));
+        if (launch_frame(bt, static_cast<int>(grid), s) != cudaSuccess) return CBT_ECUDA;
+    } else {
+        enqueue_kernels(bt, sv->sms, sv->grid_mult, vertices, s, nullptr);
+    }
     cudaMemcpyAsync(S.host + L.block, bt.nout, 4u * kk, cudaMemcpyDeviceToHost, s);
     if (cudaEventRecord(S.done, s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return CBT_ECUDA;
     S.busy = true;
@@ -1004,7 +1022,17 @@ extern "C" int cbt_server_submit(cbt_server* sv, const int32_t* idx, const cbt_f
         sv->st[idx[i]]->frame += 1u;
     }
     sv->next = (r + 1u) % static_cast<uint32_t>(sv->slots.size());
+    sv->any_tick = true;
     *ticket = static_cast<int32_t>(r);
+    return CBT_OK;
+}
+
+extern "C" int cbt_server_set_fused(cbt_server* sv, int on) {
+    if (!sv) return CBT_EINVAL;
+    for (const auto& S : sv->slots)
+        if (S.busy) return CBT_EINVAL;  // switch between ticks only
+    sv->fused = on != 0;
+    sv->tw = sv->fused ? kFusedTileWords : 256u;
     return CBT_OK;
 }
 

@@ -30,7 +30,7 @@ def ping_pong(frames, k):
 
 class ServeLoop:
     def __init__(self, specs, hbm_budget_bytes: int, inflight: int = 2, max_batch: int = 512,
-                 device="cuda"):
+                 device="cuda", fused: bool = False):
         self.device = torch.device(device)
         self.specs, self.instances, self.rejected = [], [], []
         used = 0
@@ -44,6 +44,8 @@ class ServeLoop:
             self.specs.append(spec)
         self.hbm_used = used
         self.server = Server(self.instances, inflight)
+        if fused:
+            self.server.set_fused(True)
         self.hbm_used += self.server.workspace.numel()
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(inflight)]
         self.max_batch = max_batch

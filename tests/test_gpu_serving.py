@@ -26,13 +26,14 @@ def _population():
     return specs
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("fused", [False, True], ids=["per_step", "fused"])
+def test_served_results_equal_alone(fused):
     import torch
 
     import paper_2407_02215_gb300 as P
     from paper_2407_02215_gb300.serving import ServeLoop, ping_pong
     P.build_library()
-    loop = ServeLoop(_population(), hbm_budget_bytes=1 << 36, inflight=2, max_batch=4)
+    loop = ServeLoop(_population(), hbm_budget_bytes=1 << 36, inflight=2, max_batch=4, fused=fused)
     stats = loop.run(rate_hz=4000.0, duration_s=5.0, seed=7, max_requests=240)
     assert stats["requests"] == 240
     assert stats["p99_ms"] >= stats["p50_ms"] > 0.0
