@@ -232,6 +232,16 @@ uint32_t cbt_last_launch_count(const cbt_state* st);
 int cbt_set_fused(cbt_state* st, int on, cbt_stream_t stream);
 int cbt_fused(const cbt_state* st);
 
+/* Self-test of the bounded waits of the fused form, without a fault: a
+ * cooperative launch of `blocks` blocks (1..64) meets a grid barrier that
+ * expects one arrival more than there are blocks, so every wait runs out
+ * after `limit` polls, sets the abort word and returns; the kernel ends
+ * normally and the context stays usable. d_scratch: DEVICE, 256 bytes,
+ * 256-byte aligned (cleared by the call). Returns CBT_ETIMEOUT when the
+ * waits gave up (the expected outcome), CBT_OK if they did not, CBT_EINVAL,
+ * CBT_ECUDA. Synchronous. */
+int cbt_selftest_bounded_wait(void* d_scratch, int32_t blocks, int32_t limit, cbt_stream_t stream);
+
 /* Timing of cbt_update (off by default). Per-step form: CUDA events recorded
  * on the update's stream between its kernels, one duration per kernel
  * (cbt_kernel_name). Fused form: the device's global timer read by block 0

@@ -83,6 +83,7 @@ def load(path: str | None = None):
     lib.cbt_phase_name.restype = C.c_char_p
     lib.cbt_sum_reduce.argtypes = [P, I32, P, P]
     lib.cbt_server_set_fused.argtypes = [P, C.c_int]
+    lib.cbt_selftest_bounded_wait.argtypes = [P, I32, I32, P]
     lib.cbt_set_fused.argtypes = [P, C.c_int, P]
     lib.cbt_fused.argtypes = [P]
     lib.cbt_batch_set_fused.argtypes = [P, C.c_int, P]

@@ -722,6 +722,20 @@ extern "C" const char* cbt_phase_name(uint32_t k) {
     return k < static_cast<uint32_t>(kFramePhases) ? kPhaseNames[k] : "";
 }
 
+extern "C" int cbt_selftest_bounded_wait(void* d_scratch, int32_t blocks, int32_t limit, cbt_stream_t stream) {
+    if (!d_scratch || blocks < 1 || blocks > 64 || limit < 1) return CBT_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_scratch) & 255u) return CBT_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    BatchGlobals* bg = static_cast<BatchGlobals*>(d_scratch);
+    if (cudaMemsetAsync(bg, 0, sizeof(BatchGlobals), s) != cudaSuccess) return CBT_ECUDA;
+    if (launch_wait_selftest(bg, blocks, limit, s) != cudaSuccess) return CBT_ECUDA;
+    uint32_t abort_word = 0;
+    if (cudaMemcpyAsync(&abort_word, &bg->abort, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CBT_ECUDA;
+    return abort_word ? CBT_ETIMEOUT : CBT_OK;
+}
+
 extern "C" int cbt_set_fused(cbt_state* st, int on, cbt_stream_t stream) {
     if (!st) return CBT_EINVAL;
     return set_fused(st->self, on != 0, reinterpret_cast<cudaStream_t>(stream));

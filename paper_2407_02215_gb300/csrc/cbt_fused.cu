@@ -57,15 +57,14 @@ __device__ __forceinline__ void red_release_gpu(uint32_t* p, uint32_t v) {
 // Arrival is a release reduction of the block's writes (ordered after the
 // whole block by __syncthreads); the spin is an acquire load. The launch is
 // cooperative, so every block is resident and every arrival comes.
-__device__ void grid_sync(BatchGlobals* bg, uint32_t epoch, uint32_t k) {
+__device__ void grid_wait(BatchGlobals* bg, uint32_t target, int limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t target = epoch + k * gridDim.x;
         red_release_gpu(&bg->bar_count, 1u);
         int it = 0;
         while ((int)(ld_acquire_gpu(&bg->bar_count) - target) < 0) {
             if (ld_volatile(&bg->abort)) break;
-            if (++it > kBarrierSpin) {
+            if (++it > limit) {
                 atomicExch(&bg->abort, 1u);
                 break;
             }
@@ -73,6 +72,10 @@ __device__ void grid_sync(BatchGlobals* bg, uint32_t epoch, uint32_t k) {
         }
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void grid_sync(BatchGlobals* bg, uint32_t epoch, uint32_t k) {
+    grid_wait(bg, epoch + k * gridDim.x, kBarrierSpin);
 }
 
 __device__ __forceinline__ void stamp(const BatchDev& bt, int k) {
@@ -930,7 +933,30 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame(Batch
     }
 }
 
+// Self-test of the bounded wait: one barrier that expects one more arrival
+// than the grid has. Every wait runs out after `limit` polls, sets the abort
+// word and returns; block 0 then moves the epoch past this launch's
+// arrivals so that the counters stay consistent.
+__global__ void __launch_bounds__(kFThreads) k_wait_selftest(BatchGlobals* bg, int limit) {
+    const uint32_t epoch = ld_volatile(&bg->bar_epoch);
+    grid_wait(bg, epoch + gridDim.x + 1u, limit);
+    if (blockIdx.x == 0 && threadIdx.x == 0) bg->bar_epoch = epoch + gridDim.x;
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(BatchGlobals* bg, int blocks, int limit, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(kFThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_wait_selftest, bg, limit);
+}
 
 int frame_blocks_per_sm() {
     int n = 0;

@@ -23,6 +23,7 @@ void launch_vertices(const BatchDev& bt, int grid, cudaStream_t s);
 // cooperative launch over `grid` blocks.
 int frame_blocks_per_sm();
 cudaError_t launch_frame(const BatchDev& bt, int grid, cudaStream_t s);
+cudaError_t launch_wait_selftest(BatchGlobals* bg, int blocks, int limit, cudaStream_t s);
 void launch_init(const Inst& I, const int32_t* twin, const int32_t* next, const int32_t* prev,
                  const double* hpos, int grid, cudaStream_t s);
 void launch_leaves(const Inst& I, uint32_t* slots, uint64_t* heap, uint32_t* links, int grid,
