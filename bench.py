@@ -67,9 +67,9 @@ STEP_KERNELS = ("prep", "classify", "walk", "gate", "scatter", "alloc", "free", 
 # + dram__bytes_write, L2 flushed before each pass), per live bisector at
 # frame start, valid only for the kernel sources it was taken on
 # (profiles/grid_flythrough_k_frame.md has the capture and its command).
-FRAME_TRAFFIC = {"sources_sha256_16": "f41395ee7e558eb9", "bytes_per_live": 81.3,
-                 "capture": "frames 7 and 8 of the flythrough: 54.9 MB at 659,164 live, "
-                            "56.4 MB at 712,190 live"}
+FRAME_TRAFFIC = {"sources_sha256_16": "24f12dd0d2a28083", "bytes_per_live": 86.8,
+                 "capture": "frames 7 and 8 of the flythrough: 57.5 MB at 659,164 live, "
+                            "61.4 MB at 712,190 live"}
 FRAME_SOURCES = ("cbt_fused.cu", "cbt_phases.cuh", "cbt_device.cuh")
 
 
@@ -276,7 +276,8 @@ def bench_ours(args):
     del g0
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    # timed pass: the frame replayed as a CUDA graph, one event pair per frame
+    # timed pass: one cooperative launch per frame (a single fused instance
+    # launches directly even with graphs on), one event pair per frame
     g = CBT(spec.mesh, spec.D, spec.max_depth, device=dev)
     g.set_graph(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in frames]

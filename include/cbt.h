@@ -255,8 +255,10 @@ const char* cbt_phase_name(uint32_t k);
 
 /* Update through a CUDA graph (on: the frame's launches are captured once
  * and replayed; the frame parameters reach the device through a copy from
- * pinned host memory that the graph performs). Results are identical either
- * way. Host only. */
+ * pinned host memory that the graph performs). A single instance in the
+ * fused form is one launch with its parameters passed by value and is
+ * launched directly either way (sooner than a graph starting with a copy).
+ * Results are identical either way. Host only. */
 int cbt_set_graph(cbt_state* st, int on);
 
 /* ------------------------------------------------------------------ batches

@@ -414,7 +414,11 @@ int batch_update(cbt_batch* B, const cbt_frame* frames, cudaStream_t s) {
     }
     const bool tune_now = B->tuning;
     if (tune_now) cudaEventRecord(B->tune_ev[0], s);
-    if (B->use_graph) {
+    // A single instance in the fused form is one launch whose parameters
+    // travel by value: launched directly, it starts sooner than a graph
+    // whose first node copies the parameters.
+    const bool direct = B->fused && n == 1;
+    if (B->use_graph && !direct) {
         // the graph copies the frame parameters from pinned staging
         if (B->staged_pending) cudaEventSynchronize(B->staged);
         std::memcpy(B->h_fps, fps.data(), sizeof(FrameP) * n);
