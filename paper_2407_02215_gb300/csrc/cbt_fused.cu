@@ -31,6 +31,7 @@ constexpr int kFThreads = 256;
 constexpr int kFPer = 4;  // items per thread and tile: kFThreads * kFPer == kTileItems
 static_assert(kFThreads * kFPer == (int)kTileItems, "tile shape");
 constexpr uint32_t kFBuf = 4096;  // shared scratch words (lists, tree top, live slots)
+constexpr uint32_t kRelRange = 256;  // root-table entries per warp range in P0
 constexpr uint32_t kMinIpt = 4, kMaxIpt = 8;  // items per thread of a scan tile
 constexpr int kBarrierSpin = 1 << 22;
 constexpr uint32_t kBarriers = 8;  // grid barriers per frame (one more for a single instance)
@@ -229,11 +230,13 @@ __device__ void phase_prep(const BatchDev& bt, Pair* s_warp, uint32_t* s_tmp) {
             bt.bg->t[kFramePhases] = 0;
         }
     }
-    // block 0 sets up the instances; the others share the root tables
+    // block 0 sets up the instances; the others share the root tables in
+    // warp ranges of kRelRange entries
     if (gridDim.x == 1 || blockIdx.x > 0) {
         const uint32_t nb = gridDim.x > 1 ? gridDim.x - 1u : 1u, bb = gridDim.x > 1 ? blockIdx.x - 1u : 0u;
-        const uint32_t nth = nb * blockDim.x;
-        for (uint32_t e = bb * blockDim.x + threadIdx.x; e < bt.Trel; e += nth) rel_entry(bt, e);
+        const uint32_t nw = nb * (kFThreads / 32), wid = bb * (kFThreads / 32) + threadIdx.x / 32u;
+        for (uint32_t e = wid * kRelRange; e < bt.Trel; e += nw * kRelRange)
+            rel_range(bt, e, min(bt.Trel, e + kRelRange));
     }
 }
 
@@ -660,64 +663,75 @@ __device__ void phase_alloc(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32
 
 // One changed bisector: live index i, slot s, command word and free-list
 // index of its first new record (a split, or a merge group's smallest
-// member, whose command word carries no split bits).
-__device__ __forceinline__ void fill_item(const Inst& I, uint32_t i, uint32_t s, uint32_t cmd, uint32_t dest,
-                                          uint32_t* s_cnt) {
+// member, whose command word carries no split bits). Returns the number of
+// unchanged neighbours relinked.
+__device__ __forceinline__ uint32_t fill_item(const Inst& I, uint32_t i, uint32_t s, uint32_t cmd, uint32_t dest) {
     if (cmd & kSplitMask) {
         clear_bit(I, s);
-        fill_split(I, s, cmd, dest, s_cnt);
-    } else {
-        const uint4 m = I.grp[i];
-        const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) clear_bit(I, ms[q]);
-        fill_merge(I, dest, m, s_cnt);
+        return fill_split(I, s, cmd, dest);
     }
+    const uint4 m = I.grp[i];
+    const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) clear_bit(I, ms[q]);
+    return fill_merge(I, dest, m);
 }
 
-// P6: FillNewBlocks + UpdateNeighbors + UpdateBitfield for the changed items.
-// A single instance walks its compacted changed list evenly over the grid
-// (changed items cluster in slot order, so tiles would be uneven); a batch
-// walks its tiles, each densely from a list.
-__device__ void phase_fill(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_t* s_n, uint32_t* s_list) {
+// P6: FillNewBlocks + UpdateNeighbors + UpdateBitfield for the changed items,
+// from the fill records. Changed items cluster in slot order and in a few
+// instances of a batch, so the records of all instances are walked as one
+// range, evenly over the grid: a single instance directly, a batch through
+// the prefix of its instances' record counts (built by every block in
+// shared memory; warps add their relink counts per instance).
+__device__ void phase_fill(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_t* s_list, Pair* s_warp) {
+    const uint32_t stride = gridDim.x * kFThreads;
     if (bt.B == 1) {
         stats_reset(s_cnt);
         ctx_tile(bt, bt.tile_base, 0, 1, c);  // instance 0 in shared memory
         const Inst& I = c.I;
         const uint32_t C = I.g->C;
-        for (uint32_t q = blockIdx.x * kFThreads + threadIdx.x; q < C; q += gridDim.x * kFThreads) {
+        uint32_t relinked = 0;
+        for (uint32_t q = blockIdx.x * kFThreads + threadIdx.x; q < C; q += stride) {
             const uint4 r = I.chgr[q];
-            fill_item(I, r.x, r.y, r.z, r.w, s_cnt);
+            relinked += fill_item(I, r.x, r.y, r.z, r.w);
         }
+        if (relinked) atomicAdd(&s_cnt[0], relinked);
         __syncthreads();
         stats_flush(s_cnt, I.g, kStRelinked);
         __syncthreads();
         return;
     }
-    const uint32_t T = bt.bg->total_tiles;
-    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
-        if (threadIdx.x == 0) *s_n = 0;
-        stats_reset(s_cnt);
-        ctx_tile(bt, bt.tile_base, t, T, c);
-        const Inst& I = c.I;
-        const uint32_t N = c.N;
-#pragma unroll
-        for (int k = 0; k < kFPer; ++k) {
-            const uint32_t i = c.lt * kTileItems + (uint32_t)k * kFThreads + threadIdx.x;
-            if (i < N && (I.scan[i] & 7u)) s_list[atomicAdd(s_n, 1u)] = i;
+    const int lane = threadIdx.x & 31;
+    const uint32_t wfirst = blockIdx.x * kFThreads + (threadIdx.x & ~31u);
+    for (uint32_t cb = 0; cb < bt.B; cb += kFBuf) {  // kFBuf instances at a time
+        const uint32_t nb = min(kFBuf, bt.B - cb);
+        uint32_t total = 0;
+        __syncthreads();
+        for (uint32_t b0 = 0; b0 < nb; b0 += kFThreads) {
+            const uint32_t b = b0 + threadIdx.x;
+            const uint32_t n = b < nb ? __ldcg(&bt.inst[cb + b].g->C) : 0u;
+            Pair tot;
+            const Pair ex = block_scan(Pair{n, 0u}, tot, s_warp);
+            if (b < nb) s_list[b] = total + ex.a;
+            total += tot.a;
         }
         __syncthreads();
-        const uint32_t n = *s_n;
-        for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
-            const uint32_t i = s_list[q];
-            const uint32_t s = I.live[i];
-            const uint2 cd = I.cd[s];
-            fill_item(I, i, s, cd.x, cd.y, s_cnt);
+        for (uint32_t q0 = wfirst; q0 < total; q0 += stride) {  // warp-uniform trips
+            const uint32_t q = q0 + (uint32_t)lane;
+            uint32_t b = kNull, relinked = 0;
+            if (q < total) {
+                const uint32_t lb = find_inst(s_list, nb, q);
+                b = cb + lb;
+                const Inst& I = bt.inst[b];
+                const uint4 r = I.chgr[q - s_list[lb]];
+                relinked = fill_item(I, r.x, r.y, r.z, r.w);
+            }
+            __syncwarp();
+            const uint32_t same = __match_any_sync(0xFFFFFFFFu, b);
+            const uint32_t sum = __reduce_add_sync(same, relinked);
+            if (b != kNull && sum && lane == __ffs(same) - 1) atomicAdd(&bt.inst[b].g->stats[kStRelinked], sum);
         }
-        __syncthreads();
-        stats_flush(s_cnt, I.g, kStRelinked);
-        __syncthreads();
     }
 }
 
@@ -910,7 +924,7 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame(Batch
     phase_alloc(bt, s_c, s_cnt, s_red, s_warp);
     grid_sync(bt.bg, epoch, 6u);
     stamp(bt, 6);
-    phase_fill(bt, s_c, s_cnt, &s_n, s_buf);
+    phase_fill(bt, s_c, s_cnt, s_buf, s_warp);
     grid_sync(bt.bg, epoch, 7u);
     stamp(bt, 7);
     phase_reduce(bt, s_c, s_buf, &s_tmp[0]);

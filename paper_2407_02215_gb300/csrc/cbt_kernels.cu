@@ -437,17 +437,19 @@ __global__ void __launch_bounds__(kThreads) k_fill(BatchDev bt) {
             const uint32_t i = I.chg[k];
             const uint32_t s = I.live[i];
             const uint2 c = I.cd[s];
+            uint32_t relinked;
             if (c.x & kSplitMask) {
                 clear_bit(I, s);
-                fill_split(I, s, c.x, c.y, s_cnt);
+                relinked = fill_split(I, s, c.x, c.y);
             } else {
                 const uint4 m = I.grp[i];
                 const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) clear_bit(I, ms[q]);
-                fill_merge(I, c.y, m, s_cnt);
+                relinked = fill_merge(I, c.y, m);
             }
+            if (relinked) atomicAdd(&s_cnt[0], relinked);
         }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStRelinked);

@@ -200,14 +200,10 @@ __device__ __forceinline__ void tile_begin(const BatchDev& bt, const uint32_t* b
 }
 
 
-// Entry e of the batch's camera-relative root tables: the frame's eye
+// Entry le of instance I's camera-relative root table: the frame's eye
 // subtracted in FP64, then rounded to the frame's precision (FP32, fixed
-// point at 2^shift, or FP64).
-__device__ __forceinline__ void rel_entry(const BatchDev& bt, uint32_t e) {
-    const uint32_t b = find_inst(bt.rel_base, bt.B, e);
-    const Inst& I = bt.inst[b];
-    const FrameP& fp = frame_of(bt, b);
-    const uint32_t le = e - bt.rel_base[b];
+// point at 2^shift, or FP64; the sphere form keeps the absolute roots).
+__device__ __forceinline__ void rel_store(const Inst& I, const FrameP& fp, uint32_t le) {
     const double diff = __dsub_rn(I.root64[le], fp.eye[le % 3u]);
     if (fp.precision == 1) {
         const double sc = __dmul_rn(diff, pow2d(fp.shift));
@@ -223,6 +219,28 @@ __device__ __forceinline__ void rel_entry(const BatchDev& bt, uint32_t e) {
         static_cast<double*>(I.rel)[le] = I.root64[le];  // absolute: the projection needs it
     } else {
         static_cast<float*>(I.rel)[le] = __double2float_rn(diff);
+    }
+}
+
+// Entry e of the batch's root tables (instances laid out by rel_base).
+__device__ __forceinline__ void rel_entry(const BatchDev& bt, uint32_t e) {
+    const uint32_t b = find_inst(bt.rel_base, bt.B, e);
+    rel_store(bt.inst[b], frame_of(bt, b), e - bt.rel_base[b]);
+}
+
+// Entries [e, e1) of the batch's root tables, by one warp: one instance
+// lookup for the range, and the instance's descriptor and frame read once
+// per instance it crosses.
+__device__ __forceinline__ void rel_range(const BatchDev& bt, uint32_t e, uint32_t e1) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t b = find_inst(bt.rel_base, bt.B, e);
+    while (e < e1) {
+        const uint32_t lo = bt.rel_base[b], hi = min(e1, bt.rel_base[b + 1]);
+        const Inst I = bt.inst[b];
+        const FrameP fp = frame_of(bt, b);
+        for (uint32_t x = e + lane; x < hi; x += 32u) rel_store(I, fp, x - lo);
+        e = max(e, hi);
+        ++b;
     }
 }
 
@@ -654,15 +672,15 @@ static __device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, 
 
 // An unchanged neighbour across old edge E of x now faces new bisector ns
 // through ns's edge ne; that neighbour link has exactly one writer, this one.
-__device__ __forceinline__ void push_keep(const Inst& I, const Across& a, int E, uint32_t ns, uint32_t ne,
-                                          uint32_t* s_cnt) {
+// Returns the number of links written (0 or 1).
+__device__ __forceinline__ uint32_t push_keep(const Inst& I, const Across& a, int E, uint32_t ns, uint32_t ne) {
     const uint32_t y = a.y[E];
-    if (y == kNull || (a.yc[E].x & (kSplitMask | kMerged))) return;
+    if (y == kNull || (a.yc[E].x & (kSplitMask | kMerged))) return 0u;
     uint32_t* yr = reinterpret_cast<uint32_t*>(I.nb + y);
     const int Ep = (int)a.ep[E];
     yr[Ep] = ns;
     atomicXor(yr + 3, ((uint32_t)E ^ ne) << (2 * Ep));
-    atomicAdd(&s_cnt[0], 1u);
+    return 1u;
 }
 
 __device__ __forceinline__ void set_bit(const Inst& I, uint32_t s) {
@@ -672,12 +690,13 @@ __device__ __forceinline__ void clear_bit(const Inst& I, uint32_t s) {
     atomicAnd(I.bits + (s >> 5), ~(1u << (s & 31u)));
 }
 
-static __device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t dest, uint32_t* s_cnt) {
+// Both fills return the number of unchanged neighbours relinked.
+static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t dest) {
     const uint32_t sb = cmd & kSplitMask;
     const FamDesc& f = c_fam[fam_case(sb)];
     if (dest + f.n > I.g->A) {
         set_err(I.g, kErrOverflow);
-        return;
+        return 0u;
     }
     const uint64_t j = I.heap[s];
     const uint4 rx = I.nb[s];
@@ -689,7 +708,8 @@ static __device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint3
 #pragma unroll
     for (int E = 0; E < 3; ++E) across_resolve(I, a, E, halves(sb, E), xodd);
     for (int l = 0; l < f.n; ++l)
-        if (bad_slot(I, slots[l], kErrOverflow)) return;
+        if (bad_slot(I, slots[l], kErrOverflow)) return 0u;
+    uint32_t relinked = 0;
     for (int l = 0; l < f.n; ++l) {
         uint32_t lk[3], rv = 0;
         for (int e = 0; e < 3; ++e) {
@@ -702,7 +722,7 @@ static __device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint3
                 const int h = ed.b == kSecond ? 1 : 0;
                 lk[e] = a.slot[ed.a][h];
                 r = a.rev[ed.a][h];
-                if (ed.b == kWhole) push_keep(I, a, ed.a, slots[l], (uint32_t)e, s_cnt);
+                if (ed.b == kWhole) relinked += push_keep(I, a, ed.a, slots[l], (uint32_t)e);
             }
             rv |= r << (2 * e);
         }
@@ -711,27 +731,29 @@ static __device__ void fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint3
         *cmd_ptr(I, slots[l]) = 0u;  // a new record: no cached vertices
         set_bit(I, slots[l]);
     }
+    return relinked;
 }
 
 // Parents of a valid merge group (Alg. 4), written by its smallest member:
 // Next = across child 2p+1's Twin edge, Prev = across child 2p's Twin edge,
 // Twin = the other parent (Table 1 read backwards, Alg. 6). Members m0, m1
 // are the children of the smaller parent, m2, m3 of the other one.
-static __device__ void fill_merge(const Inst& I, uint32_t dest, const uint4 m, uint32_t* s_cnt) {
+static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 m) {
     const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
     const int np = m.z == kNull ? 1 : 2;
     if (dest + (uint32_t)np > I.g->A) {
         set_err(I.g, kErrOverflow);
-        return;
+        return 0u;
     }
     uint32_t ps[2] = {kNull, kNull};
     for (int k = 0; k < np; ++k) {
         ps[k] = I.freel[dest + (uint32_t)k];
-        if (bad_slot(I, ps[k], kErrOverflow)) return;
+        if (bad_slot(I, ps[k], kErrOverflow)) return 0u;
     }
+    uint32_t relinked = 0;
     for (int pk = 0; pk < np; ++pk) {
         const uint32_t u = ms[2 * pk], v = ms[2 * pk + 1];
-        if (bad_slot(I, u, kErrLink) || bad_slot(I, v, kErrLink)) return;
+        if (bad_slot(I, u, kErrLink) || bad_slot(I, v, kErrLink)) return relinked;
         const uint64_t ju = I.heap[u];
         const uint32_t a = (ju & 1ull) ? v : u;   // child 2p
         const uint32_t c1 = (ju & 1ull) ? u : v;  // child 2p+1
@@ -742,8 +764,8 @@ static __device__ void fill_merge(const Inst& I, uint32_t dest, const uint4 m, u
         across_load(I, ra, xa);
         across_resolve(I, xb, kT, false, modd);
         across_resolve(I, xa, kT, false, modd);
-        push_keep(I, xb, kT, ps[pk], (uint32_t)kNe, s_cnt);
-        push_keep(I, xa, kT, ps[pk], (uint32_t)kPe, s_cnt);
+        relinked += push_keep(I, xb, kT, ps[pk], (uint32_t)kNe);
+        relinked += push_keep(I, xa, kT, ps[pk], (uint32_t)kPe);
         const uint32_t tw = np == 2 ? ps[1 - pk] : kNull;
         const uint32_t rvT = np == 2 ? (uint32_t)kT : 3u;
         I.nb[ps[pk]] = make_uint4(tw, xb.slot[kT][0], xa.slot[kT][0],
@@ -752,6 +774,7 @@ static __device__ void fill_merge(const Inst& I, uint32_t dest, const uint4 m, u
         *cmd_ptr(I, ps[pk]) = 0u;  // a new record: no cached vertices
         set_bit(I, ps[pk]);
     }
+    return relinked;
 }
 
 // FillNewBlocks + UpdateNeighbors + UpdateBitfield for the changed
