@@ -323,9 +323,75 @@ void or_decode_weights(uint64_t j, int32_t ch, uint64_t* W9) {
         for (int c = 0; c < 3; ++c) W9[3 * r + c] = M[r][c];
 }
 
+/* ------------------------------------------------------- displacement */
+
+/* lowbias32 (Wellons, "Prospecting for Hash Functions", 2018): two
+ * xorshift-multiply rounds and a final xorshift, a bijection of 32-bit
+ * words. */
+uint32_t or_lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+/* Value of lattice point idx[0..n) at octave o (R14): the hash chained from
+ * seed ^ o over the coordinates, last to first; the top 24 bits mapped
+ * exactly onto [-1, 1) in steps of 2^-23. */
+static float lattice_value(uint32_t seed, uint32_t o, int n, const int32_t* idx) {
+    uint32_t h = or_lowbias32(seed ^ o);
+    for (int k = n - 1; k >= 0; --k) h = or_lowbias32(h ^ (uint32_t)idx[k]);
+    return (float)(h >> 8) * 0x1p-23f - 1.0f;
+}
+
+/* Fractal value noise (R14): octave o samples the lattice at frequency
+ * frequency * 2^o with weight 2^-o. In a cell the point has integer corner
+ * floor(s) and offset t = s - floor(s) per axis (s clamped to +-2^30); the
+ * 2^n corner values are blended along x, then y, then z, with
+ * a + u (b - a) and the smoothstep weight u = t t (3 - 2 t). */
+float or_fbm(const float* x, int32_t n, float frequency, uint32_t octaves, uint32_t seed) {
+    float sum = 0.0f;
+    for (uint32_t o = 0; o < octaves; ++o) {
+        const float fo = ldexpf(frequency, (int)o);
+        int32_t i0[3] = {0, 0, 0};
+        float u[3] = {0.0f, 0.0f, 0.0f};
+        for (int k = 0; k < n; ++k) {
+            float s = x[k] * fo;
+            s = fminf(fmaxf(s, -0x1p30f), 0x1p30f);
+            const float fl = floorf(s);
+            i0[k] = (int32_t)fl;
+            const float t = s - fl;
+            u[k] = (t * t) * (3.0f - 2.0f * t);
+        }
+        float c[8];
+        for (int m = 0; m < (1 << n); ++m) { /* bit k of m: the upper corner along axis k */
+            int32_t idx[3];
+            for (int k = 0; k < n; ++k) idx[k] = i0[k] + ((m >> k) & 1);
+            c[m] = lattice_value(seed, o, n, idx);
+        }
+        int cnt = 1 << n;
+        for (int k = 0; k < n; ++k) {
+            cnt >>= 1;
+            for (int m = 0; m < cnt; ++m) c[m] = c[2 * m] + u[k] * (c[2 * m + 1] - c[2 * m]);
+        }
+        sum += c[0] * ldexpf(1.0f, -(int)o);
+    }
+    return sum;
+}
+
+static int disp_valid(const or_disp* D, uint32_t precision) {
+    if (!D || D->amplitude == 0.0f) return 1;
+    return isfinite(D->amplitude) && isfinite(D->frequency) && D->frequency > 0.0f && D->octaves >= 1u &&
+           D->octaves <= 8u && (precision == OR_PREC_FP32 || precision == OR_PREC_SPHERE);
+}
+
 typedef struct {
     uint32_t precision;
     int32_t shift;
+    or_disp disp;        /* amplitude 0: no displacement */
+    float org32[3];      /* FP32 form: the origin rounded to FP32 (world x, y for the noise) */
     double radius;       /* PREC_SPHERE */
     double org[3];       /* PREC_SPHERE: the origin, subtracted after the projection */
     const double* abs64; /* PREC_SPHERE: the FP64 root vertices themselves */
@@ -335,14 +401,19 @@ typedef struct {
 } rel_roots;
 
 static int make_rel(const or_state* st, const double org[3], uint32_t precision, int32_t shift,
-                    double radius, rel_roots* R) {
+                    double radius, const or_disp* disp, rel_roots* R) {
     memset(R, 0, sizeof(*R));
     R->precision = precision;
     R->shift = shift;
     R->radius = radius;
-    for (int c = 0; c < 3; ++c) R->org[c] = org[c];
+    if (disp) R->disp = *disp;
+    for (int c = 0; c < 3; ++c) {
+        R->org[c] = org[c];
+        R->org32[c] = (float)org[c];
+    }
     R->abs64 = st->root;
     if (precision == OR_PREC_SPHERE && !(radius > 0.0)) return OR_EINVAL;
+    if (!disp_valid(disp, precision)) return OR_EINVAL;
     const size_t n = (size_t)st->H * 9u;
     R->r32 = (float*)malloc(sizeof(float) * n);
     R->x = (int64_t*)malloc(sizeof(int64_t) * n);
@@ -379,7 +450,11 @@ static void free_rel(rel_roots* R) {
  *             n2  = fma(pz, pz, fma(py, py, px px)),
  *             y   = 1 / sqrt(n2): the FP32 estimate 1/sqrtf(float(n2)),
  *                   then twice y = fma(y/2, fma(-n2, y y, 1), y) (Newton),
- *             out = float(fma(p_c, radius y, -origin_c)). */
+ *             out = float(fma(p_c, radius y, -origin_c)).
+ * With a displacement (R14) the FP32 form adds amplitude * fbm(x, y) to z,
+ * (x, y) = the vertex plus the origin rounded to FP32; the sphere form uses
+ * the radius + double(amplitude * fbm(u)) in place of the radius, u_c =
+ * float(p_c y) the unit direction. */
 static void bisector_rel(const or_state* st, const rel_roots* R, uint64_t j, float out[9]) {
     const int d = depth_of(st, j);
     const uint32_t h = root_of(st, j);
@@ -398,7 +473,14 @@ static void bisector_rel(const or_state* st, const rel_roots* R, uint64_t j, flo
             const double n2 = fma(p[2], p[2], fma(p[1], p[1], p[0] * p[0]));
             double y = (double)(1.0f / sqrtf((float)n2));
             for (int it = 0; it < 2; ++it) y = fma(y * 0.5, fma(-n2, y * y, 1.0), y);
-            const double f = R->radius * y;
+            double rad = R->radius;
+            if (R->disp.amplitude != 0.0f) {
+                const float u[3] = {(float)(p[0] * y), (float)(p[1] * y), (float)(p[2] * y)};
+                const float hgt =
+                    R->disp.amplitude * or_fbm(u, 3, R->disp.frequency, R->disp.octaves, R->disp.seed);
+                rad = rad + (double)hgt;
+            }
+            const double f = rad * y;
             for (int c = 0; c < 3; ++c) out[3 * i + c] = (float)fma(p[c], f, -R->org[c]);
         }
         return;
@@ -424,13 +506,18 @@ static void bisector_rel(const or_state* st, const rel_roots* R, uint64_t j, flo
                 out[3 * i + c] = (w0 * R->r32[b + 0] + w1 * R->r32[b + 3]) + w2 * R->r32[b + 6];
             }
         }
+        if (R->precision == OR_PREC_FP32 && R->disp.amplitude != 0.0f) {
+            const float xy[2] = {out[3 * i] + R->org32[0], out[3 * i + 1] + R->org32[1]};
+            const float hgt = R->disp.amplitude * or_fbm(xy, 2, R->disp.frequency, R->disp.octaves, R->disp.seed);
+            out[3 * i + 2] = out[3 * i + 2] + hgt;
+        }
     }
 }
 
 void or_vertices(const or_state* st, const double origin[3], uint32_t precision,
-                 int32_t fixed_shift, double sphere_radius, float* out) {
+                 int32_t fixed_shift, double sphere_radius, const or_disp* disp, float* out) {
     rel_roots R;
-    if (make_rel(st, origin, precision, fixed_shift, sphere_radius, &R) == OR_OK) {
+    if (make_rel(st, origin, precision, fixed_shift, sphere_radius, disp, &R) == OR_OK) {
         uint32_t i = 0;
         for (uint32_t s = 0; s < st->cap; ++s)
             if (st->cbt[st->cap + s]) bisector_rel(st, &R, st->heap[s], out + 9u * (size_t)i++);
@@ -859,7 +946,7 @@ int or_update(or_state* st, const or_frame* fr, or_stats* stats) {
 
     /* 2. GenerateCommands, decision part: wishes on the frame-start state. */
     if (fr->mode == OR_MODE_LOD) {
-        rc = make_rel(st, fr->eye, fr->precision, fr->fixed_shift, fr->sphere_radius, &R);
+        rc = make_rel(st, fr->eye, fr->precision, fr->fixed_shift, fr->sphere_radius, &fr->disp, &R);
         if (rc) goto done;
     }
     for (uint32_t i = 0; i < N; ++i) classify(st, fr, &R, st->heap[L[i]], &sw[L[i]], &mw[L[i]]);

@@ -28,6 +28,20 @@ enum { OR_MODE_LOD = 0, OR_MODE_FORCE_SPLIT = 1, OR_MODE_FORCE_MERGE = 2, OR_MOD
 enum { OR_PREC_FP32 = 0, OR_PREC_FIXED = 1, OR_PREC_FP64 = 2, OR_PREC_SPHERE = 3 };
 enum { OR_GATE_CHAIN = 0, OR_GATE_PAPER = 1 };
 
+/* Displacement of the LOD-tested and exported vertices (R14 reading; the
+ * paper displaces the projected vertices with wave layers or elevation data
+ * during refinement, Sec. 4): amplitude * fbm(position), fbm = fractal value
+ * noise of `octaves` octaves (1..8) at base frequency `frequency` (lattice
+ * cells per world unit), seeded by `seed`. Plain FP32 form: +z by the noise
+ * of the world (x, y); sphere form: radially, by the noise of the unit
+ * direction. amplitude 0 = off. */
+typedef struct {
+    float amplitude;
+    float frequency;
+    uint32_t octaves;
+    uint32_t seed;
+} or_disp;
+
 typedef struct {
     double eye[3];
     float planes[5][3];
@@ -43,6 +57,7 @@ typedef struct {
     const uint64_t* merge_list; /* sorted, MODE_LIST only */
     uint32_t n_merge;
     double sphere_radius;       /* PREC_SPHERE: radius of the sphere about the origin */
+    or_disp disp;               /* FP32 and sphere forms only */
 } or_frame;
 
 typedef struct {
@@ -81,7 +96,7 @@ uint32_t or_leaves(const or_state* st, uint32_t* slots, uint64_t* heap, uint32_t
 /* FP32 vertices [N][3][3] of the live bisectors relative to ``origin`` using
  * the given precision form; and the FP64 reference positions (absolute). */
 void or_vertices(const or_state* st, const double origin[3], uint32_t precision,
-                 int32_t fixed_shift, double sphere_radius, float* out);
+                 int32_t fixed_shift, double sphere_radius, const or_disp* disp, float* out);
 void or_vertices_f64(const or_state* st, double* out);
 void or_root_table(const or_state* st, double* out);
 
@@ -97,6 +112,10 @@ uint32_t or_cbt_one_to_bit(int32_t D, const uint32_t* cbt, uint32_t index);
 uint32_t or_cbt_zero_to_bit(int32_t D, const uint32_t* cbt, uint32_t index);
 void or_decode_weights(uint64_t j, int32_t ch, uint64_t* W9);
 uint64_t or_splitmix64(uint64_t x);
+/* The displacement's parts: the lowbias32 integer hash and the fractal
+ * value noise of n (2 or 3) FP32 coordinates. */
+uint32_t or_lowbias32(uint32_t x);
+float or_fbm(const float* x, int32_t n, float frequency, uint32_t octaves, uint32_t seed);
 /* LOD test on three FP32 camera-relative vertices: bit0 visible, bit1 big. */
 uint32_t or_lod_test(const float* r9, const float* planes15, uint32_t nplanes, float q);
 

@@ -28,7 +28,7 @@ def _load():
         lib.or_export.argtypes = [P, P, P, P, P, P]
         lib.or_leaves.argtypes = [P, P, P, P]
         lib.or_leaves.restype = C.c_uint32
-        lib.or_vertices.argtypes = [P, P, C.c_uint32, C.c_int32, C.c_double, P]
+        lib.or_vertices.argtypes = [P, P, C.c_uint32, C.c_int32, C.c_double, P, P]
         lib.or_vertices_f64.argtypes = [P, P]
         lib.or_root_table.argtypes = [P, P]
         lib.or_set_order_seed.argtypes = [P, C.c_uint64]
@@ -43,6 +43,10 @@ def _load():
         lib.or_splitmix64.restype = C.c_uint64
         lib.or_lod_test.argtypes = [P, P, C.c_uint32, C.c_float]
         lib.or_lod_test.restype = C.c_uint32
+        lib.or_lowbias32.argtypes = [C.c_uint32]
+        lib.or_lowbias32.restype = C.c_uint32
+        lib.or_fbm.argtypes = [P, C.c_int32, C.c_float, C.c_uint32, C.c_uint32]
+        lib.or_fbm.restype = C.c_float
         _lib = lib
     return _lib
 
@@ -51,6 +55,19 @@ class OracleError(RuntimeError):
     def __init__(self, code, what):
         super().__init__(f"oracle {what} failed with code {code}")
         self.code = code
+
+
+class _Disp(C.Structure):
+    _fields_ = [("amplitude", C.c_float), ("frequency", C.c_float), ("octaves", C.c_uint32), ("seed", C.c_uint32)]
+
+
+def _disp(fp):
+    d = _Disp()
+    d.amplitude = float(getattr(fp, "disp_amplitude", 0.0))
+    d.frequency = float(getattr(fp, "disp_frequency", 0.0))
+    d.octaves = int(getattr(fp, "disp_octaves", 0))
+    d.seed = int(getattr(fp, "disp_seed", 0))
+    return d
 
 
 class _Frame(C.Structure):
@@ -69,6 +86,7 @@ class _Frame(C.Structure):
         ("merge_list", C.c_void_p),
         ("n_merge", C.c_uint32),
         ("sphere_radius", C.c_double),
+        ("disp", _Disp),
     ]
 
 
@@ -144,6 +162,7 @@ class Oracle:
         f.fixed_shift = int(fp.fixed_shift)
         f.gate = int(fp.gate)
         f.sphere_radius = float(getattr(fp, "sphere_radius", 0.0))
+        f.disp = _disp(fp)
         keep = []
         for name, cnt, arr in (("split_list", "n_split", fp.split_list),
                                ("merge_list", "n_merge", fp.merge_list)):
@@ -193,11 +212,15 @@ class Oracle:
         _lib.or_leaves(self._h, _ptr(slots), _ptr(heap), _ptr(links))
         return slots, heap, links
 
-    def vertices(self, origin, precision=0, fixed_shift=20, sphere_radius=0.0):
+    def vertices(self, origin, precision=0, fixed_shift=20, sphere_radius=0.0, frame=None):
+        """Vertices of the live bisectors relative to ``origin``; with
+        ``frame`` (a FrameParams) its displacement is applied."""
         n = self.live_count
         out = np.zeros((n, 3, 3), np.float32)
         o = np.ascontiguousarray(origin, np.float64)
-        _lib.or_vertices(self._h, _ptr(o), precision, fixed_shift, float(sphere_radius), _ptr(out))
+        d = _disp(frame) if frame is not None else None
+        _lib.or_vertices(self._h, _ptr(o), precision, fixed_shift, float(sphere_radius),
+                         C.addressof(d) if d is not None else None, _ptr(out))
         return out
 
     def vertices_f64(self):
@@ -209,6 +232,18 @@ class Oracle:
         out = np.zeros((self.H, 3, 3), np.float64)
         _lib.or_root_table(self._h, _ptr(out))
         return out
+
+
+def lowbias32(x: int) -> int:
+    """The displacement's lattice hash on one 32-bit word."""
+    return int(_load().or_lowbias32(int(x) & 0xFFFFFFFF))
+
+
+def fbm(x, frequency: float, octaves: int, seed: int) -> float:
+    """Fractal value noise of 2 or 3 FP32 coordinates (the displacement's
+    height before the amplitude)."""
+    a = np.ascontiguousarray(x, np.float32)
+    return float(_load().or_fbm(_ptr(a), int(a.size), float(np.float32(frequency)), int(octaves), int(seed)))
 
 
 def cbt_sum_reduction(D: int, cbt: np.ndarray) -> np.ndarray:

@@ -12,8 +12,8 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import (Oracle, cbt_one_to_bit, cbt_sum_reduction, cbt_zero_to_bit, decode_weights,
-                    halfedges_from_faces, lod_test, splitmix64)
+from oracle import (Oracle, cbt_one_to_bit, cbt_sum_reduction, cbt_zero_to_bit, decode_weights, fbm,
+                    halfedges_from_faces, lod_test, lowbias32, splitmix64)
 from workloads.cameras import (MODE_FORCE_MERGE, MODE_FORCE_SPLIT, MODE_LIST, MODE_RANDOM,
                                forced_params)
 from tests.invariants import check_state, depth_of, symbolic_vertices
@@ -314,3 +314,160 @@ def test_sphere_projection_properties():
     assert np.all(np.einsum("ij,ij->i", on, flat) > 0)
     corner = np.isclose(np.linalg.norm(flat, axis=1), R, rtol=1e-12)
     assert corner.any() and np.allclose(on[corner], flat[corner], rtol=0, atol=2.0 * ulp[corner].max())
+
+
+# ------------------------------------------------- displacement (R14 reading)
+
+def _xorshift_inverse(y, k):
+    x = y
+    for _ in range(32 // k + 1):
+        x = y ^ (x >> k)
+    return x
+
+
+def test_lowbias32_is_a_bijection_of_its_published_steps():
+    """lowbias32 (Wellons 2018) is x ^= x >> 16; x *= 0x7feb352d; x ^= x >> 15;
+    x *= 0x846ca68b; x ^= x >> 16. Each step is invertible on 32-bit words
+    (odd multipliers have modular inverses), so undoing the five steps in
+    reverse order must give back every input; a dropped, reordered or
+    mistyped step does not invert."""
+    M = 1 << 32
+    inv1, inv2 = pow(0x7FEB352D, -1, M), pow(0x846CA68B, -1, M)
+    rng = np.random.default_rng(14)
+    xs = [0, 1, 2, 0xFFFFFFFF, 0x80000000] + [int(v) for v in rng.integers(0, M, 2000, dtype=np.uint64)]
+    for x in xs:
+        y = lowbias32(x)
+        y = _xorshift_inverse(y, 16)
+        y = (y * inv2) % M
+        y = _xorshift_inverse(y, 15)
+        y = (y * inv1) % M
+        y = _xorshift_inverse(y, 16)
+        assert y == x
+    assert lowbias32(0) == 0  # every step fixes 0
+
+
+def test_value_noise_cell_is_a_smoothstep_bilinear_blend():
+    """One octave of the 2-D value noise inside a cell is the bilinear blend
+    of its four corner values with the smoothstep weight 3t^2 - 2t^3 per
+    axis, the corner values being the noise at the integer points
+    themselves (closed form in FP64, against the oracle's FP32)."""
+    rng = np.random.default_rng(15)
+    for _ in range(200):
+        i, j = (int(v) for v in rng.integers(-50, 50, 2))
+        tx, ty = (float(np.float32(v)) for v in rng.uniform(0, 1, 2))
+        c00 = fbm([i, j], 1.0, 1, 7)
+        c10 = fbm([i + 1, j], 1.0, 1, 7)
+        c01 = fbm([i, j + 1], 1.0, 1, 7)
+        c11 = fbm([i + 1, j + 1], 1.0, 1, 7)
+        x = np.float32(i + tx)
+        y = np.float32(j + ty)
+        ux, uy = (3 * t * t - 2 * t ** 3 for t in (float(x) - i, float(y) - j))
+        want = (1 - ux) * (1 - uy) * c00 + ux * (1 - uy) * c10 + (1 - ux) * uy * c01 + ux * uy * c11
+        assert abs(fbm([x, y], 1.0, 1, 7) - want) <= 4e-6
+        assert -1.0 <= c00 < 1.0
+
+
+def test_value_noise_is_continuous_with_flat_lattice_points():
+    """The smoothstep blend is C1: crossing a cell face changes the 3-D noise
+    only by O(step), and at a lattice point the slope vanishes, so a step
+    of 2^-12 away changes it by O(2^-24)."""
+    rng = np.random.default_rng(16)
+    for _ in range(100):
+        p = rng.integers(-20, 20, 3).astype(np.float64)
+        k = int(rng.integers(0, 3))
+        at = fbm(p, 1.0, 1, 3)
+        for s in (-1, 1):
+            q = p.copy()
+            q[k] += s * 2.0 ** -12
+            assert abs(fbm(q, 1.0, 1, 3) - at) <= 2.0 ** -18
+        r = p.copy()
+        r[(k + 1) % 3] += 0.37
+        lo, hi = r.copy(), r.copy()
+        lo[k] -= 2.0 ** -16
+        hi[k] += 2.0 ** -16
+        assert abs(fbm(hi, 1.0, 1, 3) - fbm(lo, 1.0, 1, 3)) <= 2.0 ** -12
+
+
+def test_fbm_is_the_weighted_sum_of_its_octaves():
+    """Octave o of the fractal sum is one octave at frequency f 2^o, weight
+    2^-o, lattice seeded with seed ^ o: the K-octave value equals that sum
+    of single-octave values (to FP32 rounding of the sum)."""
+    rng = np.random.default_rng(17)
+    for _ in range(100):
+        x = rng.uniform(-3, 3, 3).astype(np.float32)
+        f = float(np.float32(rng.uniform(0.5, 4)))
+        seed = int(rng.integers(0, 1 << 32))
+        want = sum(2.0 ** -o * fbm(x, f * 2 ** o, 1, seed ^ o) for o in range(5))
+        assert abs(fbm(x, f, 5, seed) - want) <= 1e-5
+        assert abs(fbm(x, f, 5, seed)) <= 2.0 - 2.0 ** -4
+
+
+def test_value_noise_statistics():
+    """Lattice values are uniform on [-1, 1): mean 0 and variance 1/3 over
+    many integer points."""
+    rng = np.random.default_rng(18)
+    v = np.array([fbm(p, 1.0, 1, 11) for p in rng.integers(-10 ** 6, 10 ** 6, (4000, 2)).astype(np.float32)])
+    assert abs(v.mean()) < 0.04 and abs(v.var() - 1.0 / 3.0) < 0.03
+
+
+def _disp_frame(eye, precision, radius=0.0, amp=0.05, freq=4.0, octaves=4, seed=9):
+    fp = forced_params(MODE_FORCE_SPLIT)
+    fp.eye = np.asarray(eye, np.float64)
+    fp.precision = precision
+    fp.sphere_radius = radius
+    fp.disp_amplitude, fp.disp_frequency, fp.disp_octaves, fp.disp_seed = amp, freq, octaves, seed
+    return fp
+
+
+def test_displacement_plain_moves_z_only_and_ignores_the_camera():
+    """FP32 form: the displaced vertices differ from the plain ones in z
+    only; the world height (z + eye) is a function of the world position,
+    so two cameras agree on it to FP32 rounding; amplitude 0 is the
+    undisplaced form bit for bit."""
+    m = W.meshes.grid_mesh(6, 6, tri_frac=0.2, seed=3, height_sigma=0.05)
+    o = Oracle(m, 14, 12)
+    for _ in range(3):
+        o.update(forced_params(MODE_FORCE_SPLIT))
+    eyes = [np.array([0.3, 0.6, 0.4]), np.array([0.9, 0.1, 0.25])]
+    plain = [o.vertices(e, 0) for e in eyes]
+    disp = [o.vertices(e, 0, frame=_disp_frame(e, 0)) for e in eyes]
+    zero = o.vertices(eyes[0], 0, frame=_disp_frame(eyes[0], 0, amp=0.0))
+    assert np.array_equal(zero, plain[0])
+    for p, d in zip(plain, disp):
+        assert np.array_equal(p[..., :2], d[..., :2])
+        assert np.abs(d[..., 2] - p[..., 2]).max() > 1e-3
+        assert np.abs(d[..., 2] - p[..., 2]).max() <= 0.05 * (2 - 2 ** -3) + 1e-6
+    # the height added is +amplitude * fbm(world x, y), read back through fbm
+    e32 = eyes[0].astype(np.float32)
+    pts = plain[0].reshape(-1, 3)
+    hgt = np.array([0.05 * fbm([x + e32[0], y + e32[1]], 4.0, 4, 9) for x, y, _ in pts])
+    dz = (disp[0].reshape(-1, 3)[:, 2].astype(np.float64) - pts[:, 2])
+    assert np.abs(dz - hgt).max() <= 1e-6
+    w0 = disp[0].astype(np.float64) + eyes[0]
+    w1 = disp[1].astype(np.float64) + eyes[1]
+    # the noise reads world x, y rounded through FP32: positions agree to a few
+    # ulps, and the noise's slope (<= 0.05 * 1.5 * 4 * 2^4 per unit) maps them
+    assert np.abs(w0 - w1).max() <= 1e-5
+
+
+def test_displacement_sphere_is_radial():
+    """Sphere form: each displaced vertex plus the eye lies on the ray of
+    its flat FP64 vertex, at distance R + amplitude * fbm(u) from the
+    centre, u the unit direction (the noise read back through the oracle's
+    own fbm at u, in FP64 to FP32 rounding of the coordinates)."""
+    R = 6.371e6
+    m = W.meshes.dodecahedron_mesh(R)
+    o = Oracle(m, 12, 8)
+    for _ in range(3):
+        o.update(forced_params(MODE_FORCE_SPLIT))
+    eye = np.array([0.2 * R, 0.1 * R, 1.1 * R])
+    fp = _disp_frame(eye, 3, R, amp=2.0e4, freq=8.0, octaves=3, seed=5)
+    v = o.vertices(eye, 3, 20, R, frame=fp).reshape(-1, 3).astype(np.float64) + eye
+    flat = o.vertices_f64().reshape(-1, 3)
+    u = flat / np.linalg.norm(flat, axis=1, keepdims=True)
+    hgt = np.array([2.0e4 * fbm(x.astype(np.float32), 8.0, 3, 5) for x in u])
+    ulp = np.spacing(np.float32(2 * R)).astype(np.float64)
+    assert np.abs(np.linalg.norm(v, axis=1) - (R + hgt)).max() <= 4 * ulp + 2.0e4 * 2 * 8 * 8 * 1e-7
+    cross = np.linalg.norm(np.cross(v, flat), axis=1) / (np.linalg.norm(v, axis=1) * np.linalg.norm(flat, axis=1))
+    assert cross.max() < 1e-6
+    assert np.abs(hgt).max() > 1e3

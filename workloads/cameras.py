@@ -53,6 +53,12 @@ class FrameParams:
     split_list: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint64))
     merge_list: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint64))
     sphere_radius: float = 0.0  # PREC_SPHERE: radius of the sphere about the origin
+    # displacement (FP32 and sphere forms): amplitude * fractal value noise
+    # of `disp_octaves` octaves at `disp_frequency` lattice cells per unit
+    disp_amplitude: float = 0.0
+    disp_frequency: float = 0.0
+    disp_octaves: int = 0
+    disp_seed: int = 0
 
 
 def camera_basis(cam: Camera):
