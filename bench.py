@@ -563,18 +563,16 @@ def bench_reduce(args):
                        "reps": reps}}
 
 
-def bench_dodeca(args):
-    """The paper's planet scene shape (Sec. 4, Table 3: H = 60, D = 17, 0.1 ms
-    per update on its GPU): dodecahedron base on an Earth-sized sphere,
-    vertices projected onto the sphere in FP64, 14 px refinement edges, a
-    300-frame descent from 2e7 m to 2 m; one instance, CUDA graph, vertices
-    exported every frame, L2 flushed before every frame."""
+def _frames_timed(args, spec, vertices=True, busy_min=1000):
+    """One instance over its frames as a CUDA graph, L2 flushed before every
+    frame, vertices exported every frame: per-frame event times, live
+    counts, and a device-timer phase breakdown (second run) of the frames
+    with more than busy_min live bisectors."""
     import torch
 
     from paper_2407_02215_gb300 import CBT
-    spec = W.configs.config_dodeca()
+    vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device="cuda") if vertices else None
     g0 = CBT(spec.mesh, spec.D, spec.max_depth)
-    vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device="cuda")
     for fp in spec.frames[:max(args.warmup, 3)]:
         g0.update(fp, vertices_out=vbuf)
     del g0
@@ -592,8 +590,7 @@ def bench_dodeca(args):
     torch.cuda.synchronize()
     ms = np.array([a.elapsed_time(b) for a, b in ev])
     live = np.array(live)
-    busy = live > 1000  # frames with the planet in view
-    # phase breakdown of the frames with the planet in view (device timer)
+    busy = live > busy_min
     gk = CBT(spec.mesh, spec.D, spec.max_depth)
     gk.set_timing(True)
     pt, nb = {}, 0
@@ -605,16 +602,59 @@ def bench_dodeca(args):
             for name, v in gk.kernel_times().items():
                 pt[name] = pt.get(name, 0.0) + v
     del gk
-    return {"metric": METRIC + " [paper's planet shape]", "value": float(live.sum() / (ms.sum() / 1e3)),
-            "unit": UNIT, "ms_per_frame_mean": float(ms.mean()), "ms_per_frame_p50": float(np.median(ms)),
-            "ms_per_frame_p99": float(np.percentile(ms, 99)),
+    return {"value": float(live.sum() / (ms.sum() / 1e3)), "unit": UNIT, "ms_per_frame_mean": float(ms.mean()),
+            "ms_per_frame_p50": float(np.median(ms)), "ms_per_frame_p99": float(np.percentile(ms, 99)),
             "ms_per_frame_p50_in_view": float(np.median(ms[busy])) if busy.any() else None,
             "live_p50_in_view": float(np.median(live[busy])) if busy.any() else None, "live_max": int(live.max()),
-            "phase_ms_per_frame_in_view": {k: round(v / max(nb, 1), 5) for k, v in pt.items()},
-            "paper": {"ms_per_update": 0.1, "what": "Table 3, water planet (H 60, D 17), AMD 6800 XT, FP64 vertex decode"},
-            "config": {"workload": "dodeca planet: dodecahedron (60 halfedges), R 6.371e6 m, pool 2^17, max depth 50, "
-                                   "300-frame descent 2e7 m -> 2 m, sphere projection in FP64, 14 px edges, "
-                                   "L2 flushed before every frame", "frames": len(spec.frames)}}
+            "phase_ms_per_frame_in_view": {k: round(v / max(nb, 1), 5) for k, v in pt.items()}}
+
+
+def bench_dodeca(args):
+    """The paper's planet scene shape (Sec. 4, Table 3: H = 60, D = 17, 0.1 ms
+    per update on its GPU): dodecahedron base on an Earth-sized sphere,
+    vertices projected onto the sphere in FP64, 14 px refinement edges, a
+    300-frame descent from 2e7 m to 2 m; one instance, CUDA graph, vertices
+    exported every frame, L2 flushed before every frame."""
+    spec = W.configs.config_dodeca()
+    out = {"metric": METRIC + " [paper's planet shape]", **_frames_timed(args, spec)}
+    out.update({"paper": {"ms_per_update": 0.1,
+                          "what": "Table 3, water planet (H 60, D 17), AMD 6800 XT, FP64 vertex decode"},
+                "config": {"workload": "dodeca planet: dodecahedron (60 halfedges), R 6.371e6 m, pool 2^17, "
+                                       "max depth 50, 300-frame descent 2e7 m -> 2 m, sphere projection in FP64, "
+                                       "14 px edges, L2 flushed before every frame", "frames": len(spec.frames)}})
+    return out
+
+
+def bench_waves(args):
+    """The paper's water planet (Sec. 4): the dodecahedron planet of the
+    dodeca workload with the projected vertices displaced radially by a
+    4-octave value noise (2 m, cells of 1 km to 125 m) standing in for its
+    four FFT wave layers; the same descent, timing and export."""
+    spec = W.configs.config_waves()
+    out = {"metric": METRIC + " [water planet, displaced]", **_frames_timed(args, spec)}
+    out.update({"paper": {"ms_per_update": 0.1,
+                          "what": "Table 3, water planet (H 60, D 17), AMD 6800 XT, FP64 vertex decode"},
+                "config": {"workload": "wave planet: dodeca planet + radial displacement 2 m x fbm(4 octaves, "
+                                       "1 km .. 125 m cells), pool 2^17, 300-frame descent, L2 flushed before "
+                                       "every frame", "frames": len(spec.frames)}})
+    return out
+
+
+def bench_terrain(args):
+    """Displaced terrain (the grid flythrough with z displaced by a 6-octave
+    value noise, 0.02 amplitude, 4 to 128 cells per unit) beside the same
+    flythrough undisplaced: what the noise evaluation adds to classify."""
+    spec = W.configs.config_terrain()
+    flat = W.configs.config2()
+    out = {"metric": METRIC + " [displaced terrain]", **_frames_timed(args, spec)}
+    ref = _frames_timed(args, flat)
+    out.update({"undisplaced": {k: ref[k] for k in ("value", "ms_per_frame_p50", "live_p50_in_view",
+                                                     "phase_ms_per_frame_in_view")},
+                "config": {"workload": "terrain: 100 x 100 mixed grid (42k halfedges), pool 2^20, max depth 26, "
+                                       "120-frame flythrough, tau 2 px, z displaced by 0.02 x fbm(6 octaves, 4 .. 128 "
+                                       "cells per unit), vertices exported, L2 flushed before every frame",
+                           "frames": len(spec.frames)}})
+    return out
 
 
 def bench_planet(args):
@@ -650,7 +690,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
-    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "serve", "planet", "reduce", "dodeca"],
+    ap.add_argument("--workload", default="grid",
+                    choices=["grid", "batch", "serve", "planet", "reduce", "dodeca", "waves", "terrain"],
                     help="grid = the headline workload; the others are extra measurements")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--planets", type=int, default=8)
@@ -663,7 +704,8 @@ def main():
         import paper_2407_02215_gb300 as P
         P.build_library()
         fn = {"batch": bench_batch, "serve": bench_serve, "planet": bench_planet,
-              "reduce": bench_reduce, "dodeca": bench_dodeca}[args.workload]
+              "reduce": bench_reduce, "dodeca": bench_dodeca, "waves": bench_waves,
+              "terrain": bench_terrain}[args.workload]
         print(json.dumps(fn(args)))
         return
     if args.impl == "reference":

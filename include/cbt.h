@@ -91,7 +91,17 @@ enum { CBT_GATE_CHAIN = 0, CBT_GATE_PAPER = 1 };
  * rows beyond vertices_cap are not written (size it 2^D rows to be safe).
  * sphere_radius: CBT_PREC_SPHERE only, the radius (> 0) of the sphere about
  * the world origin onto which the vertices (LOD test and export) are
- * projected. */
+ * projected.
+ * disp_*: displacement of the vertices (LOD test and export) by seeded
+ * fractal value noise, standing in for the paper's wave layers and elevation
+ * data (Sec. 4). disp_amplitude 0 turns it off; otherwise CBT_PREC_FP32 or
+ * CBT_PREC_SPHERE, disp_frequency > 0 (lattice cells per world unit at the
+ * first octave; per unit of direction on the sphere) and disp_octaves in
+ * 1..8, else CBT_EINVAL. FP32 form: z += amplitude * fbm(world x, y); sphere
+ * form: the radius grows by amplitude * fbm(unit direction). The noise:
+ * lowbias32 lattice hash chained from seed ^ octave over the coordinates
+ * (last to first), values (h >> 8) 2^-23 - 1, smoothstep-weighted blends
+ * along x, then y, then z, octave o at frequency f 2^o and weight 2^-o. */
 typedef struct {
     double eye[3];
     float planes[5][3];
@@ -109,6 +119,10 @@ typedef struct {
     float* vertices_out;
     uint32_t vertices_cap;
     double sphere_radius; /* CBT_PREC_SPHERE: the sphere's radius (> 0), else unused */
+    float disp_amplitude; /* displacement height scale, world units; 0 = off */
+    float disp_frequency; /* lattice cells per unit at the first octave */
+    uint32_t disp_octaves;
+    uint32_t disp_seed;
 } cbt_frame;
 
 /* Per-frame counters (read with cbt_stats). */

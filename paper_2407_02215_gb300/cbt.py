@@ -112,6 +112,10 @@ class Frame(C.Structure):
         ("vertices_out", C.c_void_p),
         ("vertices_cap", C.c_uint32),
         ("sphere_radius", C.c_double),
+        ("disp_amplitude", C.c_float),
+        ("disp_frequency", C.c_float),
+        ("disp_octaves", C.c_uint32),
+        ("disp_seed", C.c_uint32),
     ]
 
 
@@ -185,6 +189,10 @@ def frame_struct(fp, device, vertices_out=None) -> tuple:
     f.fixed_shift = int(fp.fixed_shift)
     f.gate = int(fp.gate)
     f.sphere_radius = float(getattr(fp, "sphere_radius", 0.0))
+    f.disp_amplitude = float(getattr(fp, "disp_amplitude", 0.0))
+    f.disp_frequency = float(getattr(fp, "disp_frequency", 0.0))
+    f.disp_octaves = int(getattr(fp, "disp_octaves", 0))
+    f.disp_seed = int(getattr(fp, "disp_seed", 0))
     keep = []
     for name, cnt, arr in (("split_list", "n_split", getattr(fp, "split_list", ())),
                            ("merge_list", "n_merge", getattr(fp, "merge_list", ()))):

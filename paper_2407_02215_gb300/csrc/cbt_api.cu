@@ -6,6 +6,7 @@
 // for many instances in a caller-provided workspace, so that one launch per
 // kernel updates them all.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -125,6 +126,10 @@ bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
     if (f->mode == CBT_MODE_LIST && ((f->n_split && !f->split_list) || (f->n_merge && !f->merge_list)))
         return false;
     if (f->vertices_out && f->vertices_cap == 0) return false;
+    if (f->disp_amplitude != 0.0f &&
+        !(std::isfinite(f->disp_amplitude) && std::isfinite(f->disp_frequency) && f->disp_frequency > 0.0f &&
+          f->disp_octaves >= 1u && f->disp_octaves <= 8u && (f->precision == 0u || f->precision == 3u)))
+        return false;
     std::memset(&fp, 0, sizeof(fp));
     for (int c = 0; c < 3; ++c) fp.eye[c] = f->eye[c];
     for (int p = 0; p < 5; ++p)
@@ -144,6 +149,12 @@ bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
     fp.frame = frame;
     fp.vout = f->vertices_out;
     fp.vcap = f->vertices_cap;
+    if (f->disp_amplitude != 0.0f) {
+        fp.damp = f->disp_amplitude;
+        fp.dfreq = f->disp_frequency;
+        fp.doct = f->disp_octaves;
+        fp.dseed = f->disp_seed;
+    }
     return true;
 }
 

@@ -17,7 +17,7 @@
 //                    smallest member it is, or of a split wish's chain
 //   chg[cap]   u32   live indices of the frame's changed bisectors, ascending
 //   chgr[cap]  uint4 the same as records {live index, slot, cmd, dest}
-//   vc[cap]    9 x f32 in the sphere form, the vertices the LOD test
+//   vc[cap]    9 x f32 in the sphere and displaced forms, the vertices the LOD test
 //                    evaluated this frame (valid while the slot's cmd has
 //                    kVcValid), copied by the vertex export
 //   root64[H*9], rel[H*9]: root vertices (FP64) and their per-frame offsets
@@ -44,7 +44,7 @@ constexpr uint32_t kDepthOdd = 1u << 7;
 constexpr uint32_t kHeapOdd = 1u << 8;
 constexpr uint32_t kCand = 1u << 9;    // smallest member of a mergeable group (members in grp[i])
 constexpr uint32_t kGrpMin = 1u << 10; // smallest member of a merge group whose members are in grp[i]
-constexpr uint32_t kVcValid = 1u << 11; // vc[slot] holds this frame's vertices (sphere form, one-launch frame)
+constexpr uint32_t kVcValid = 1u << 11; // vc[slot] holds this frame's vertices (sphere or displaced form, one-launch frame)
 
 // Edge indices of a bisector: Twin (v0,v1), Next (v1,v2), Prev (v2,v0).
 constexpr int kT = 0, kNe = 1, kPe = 2;
@@ -117,6 +117,10 @@ struct FrameP {
     float* vout;     // optional vertex export, vcap rows of 9 floats
     uint32_t vcap;
     double radius;   // precision 3: radius of the sphere about the world origin
+    float damp;      // displacement amplitude (0: none), precisions 0 and 3
+    float dfreq;     // displacement base frequency (lattice cells per unit)
+    uint32_t doct;   // displacement octaves (1..8)
+    uint32_t dseed;  // displacement lattice seed
 };
 
 constexpr int kFramePhases = 10;  // phases of the one-launch frame (a batch skips the last)
@@ -304,6 +308,94 @@ __device__ __forceinline__ float i128_to_float(__int128 s) {
     return neg ? -f : f;
 }
 
+// ------------------------------------------------------------ displacement
+
+// Displacement of the tested and exported vertices by seeded fractal value
+// noise, standing in for the wave layers and elevation data with which the
+// paper displaces the projected vertices during refinement (Sec. 4; R14
+// reading):
+//   lattice value of integer point i at octave o: lowbias32 (Wellons,
+//     "Prospecting for Hash Functions", 2018) chained from seed ^ o over the
+//     coordinates, last to first; the top 24 bits give (h >> 8) 2^-23 - 1;
+//   octave o: per axis s = x f 2^o clamped to +-2^30, corner floor(s),
+//     weight u = t t (3 - 2 t) with t = s - floor(s); the 2^n corner values
+//     blended along x, then y, then z, as a + u (b - a);
+//   fbm = the sum over o < octaves of 2^-o times octave o, in order.
+// Every FP32 operation rounds separately.
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ float lattice_unit(uint32_t h) {
+    return __fsub_rn(__fmul_rn(__uint2float_rn(h >> 8), 0x1p-23f), 1.0f);
+}
+__device__ __forceinline__ float blend(float a, float b, float u) {
+    return __fadd_rn(a, __fmul_rn(u, __fsub_rn(b, a)));
+}
+// Corner index and weight of one axis at frequency fo.
+__device__ __forceinline__ float noise_axis(float x, float fo, uint32_t& i) {
+    const float s = fminf(fmaxf(__fmul_rn(x, fo), -0x1p30f), 0x1p30f);
+    const float fl = floorf(s);
+    i = (uint32_t)(int)fl;
+    const float t = __fsub_rn(s, fl);
+    return __fmul_rn(__fmul_rn(t, t), __fsub_rn(3.0f, __fmul_rn(2.0f, t)));
+}
+
+// 2-D fbm of (x0, x1); the hash prefix of each y corner is shared.
+static __device__ __noinline__ float fbm2(float x0, float x1, float freq, uint32_t octaves, uint32_t seed) {
+    float sum = 0.0f;
+    for (uint32_t o = 0; o < octaves; ++o) {
+        const float fo = __fmul_rn(freq, pow2f((int)o));
+        uint32_t ix, iy;
+        const float ux = noise_axis(x0, fo, ix), uy = noise_axis(x1, fo, iy);
+        const uint32_t h0 = lowbias32(seed ^ o);
+        const uint32_t hy0 = lowbias32(h0 ^ iy), hy1 = lowbias32(h0 ^ (iy + 1u));
+        const float a = blend(lattice_unit(lowbias32(hy0 ^ ix)), lattice_unit(lowbias32(hy0 ^ (ix + 1u))), ux);
+        const float b = blend(lattice_unit(lowbias32(hy1 ^ ix)), lattice_unit(lowbias32(hy1 ^ (ix + 1u))), ux);
+        sum = __fadd_rn(sum, __fmul_rn(blend(a, b, uy), pow2f(-(int)o)));
+    }
+    return sum;
+}
+
+// 3-D fbm of (x0, x1, x2); hash prefixes shared per z and per (z, y).
+static __device__ __noinline__ float fbm3(float x0, float x1, float x2, float freq, uint32_t octaves, uint32_t seed) {
+    float sum = 0.0f;
+    for (uint32_t o = 0; o < octaves; ++o) {
+        const float fo = __fmul_rn(freq, pow2f((int)o));
+        uint32_t ix, iy, iz;
+        const float ux = noise_axis(x0, fo, ix), uy = noise_axis(x1, fo, iy), uz = noise_axis(x2, fo, iz);
+        const uint32_t h0 = lowbias32(seed ^ o);
+        float zc[2];
+#pragma unroll
+        for (uint32_t bz = 0; bz < 2; ++bz) {
+            const uint32_t hz = lowbias32(h0 ^ (iz + bz));
+            const uint32_t hzy0 = lowbias32(hz ^ iy), hzy1 = lowbias32(hz ^ (iy + 1u));
+            const float a = blend(lattice_unit(lowbias32(hzy0 ^ ix)), lattice_unit(lowbias32(hzy0 ^ (ix + 1u))), ux);
+            const float b = blend(lattice_unit(lowbias32(hzy1 ^ ix)), lattice_unit(lowbias32(hzy1 ^ (ix + 1u))), ux);
+            zc[bz] = blend(a, b, uy);
+        }
+        sum = __fadd_rn(sum, __fmul_rn(blend(zc[0], zc[1], uz), pow2f(-(int)o)));
+    }
+    return sum;
+}
+
+// Forms whose vertices the one-launch frame caches from its LOD test for the
+// export (a sphere projection or a displacement costs more to evaluate again
+// than 36 bytes cost to store and load).
+__device__ __forceinline__ bool vc_form(const FrameP& fp) { return fp.precision == 3u || fp.damp != 0.0f; }
+
+// FP32 form: z += amplitude * fbm2 of the world (x, y), the vertex plus the
+// origin rounded to FP32.
+__device__ __forceinline__ void displace_plain(float r[3], const FrameP& fp) {
+    const float wx = __fadd_rn(r[0], __double2float_rn(fp.eye[0]));
+    const float wy = __fadd_rn(r[1], __double2float_rn(fp.eye[1]));
+    r[2] = __fadd_rn(r[2], __fmul_rn(fp.damp, fbm2(wx, wy, fp.dfreq, fp.doct, fp.dseed)));
+}
+
 // Vertex v (0..2) of a bisector relative to the frame's origin, rounded to
 // FP32, into r[0..2]:
 //   FP32:   (w0 R0 + w1 R1) + w2 R2, w = float(W) 2^-d (no contraction);
@@ -317,6 +409,9 @@ __device__ __forceinline__ float i128_to_float(__int128 s) {
 //             y   = 1 / sqrt(n2): the FP32 estimate 1 / sqrtf(float(n2)),
 //                   then twice y = fma(y/2, fma(-n2, y y, 1), y) (Newton),
 //             r_c = float(fma(p_c, radius y, -eye_c)).
+// With a displacement the FP32 form adds amplitude * fbm2(world x, y) to z
+// (displace_plain) and the sphere form takes radius + double(amplitude *
+// fbm3(u)) for the radius, u_c = float(p_c y) the unit direction.
 template <typename T>
 __device__ __forceinline__ void eval_vertex(const T W[9], int v, int d, const FrameP& fp, const void* rel,
                                             uint32_t h, float r[3]) {
@@ -334,7 +429,15 @@ __device__ __forceinline__ void eval_vertex(const T W[9], int v, int d, const Fr
         double y = (double)__frcp_rn(__fsqrt_rn(__double2float_rn(n2)));
 #pragma unroll
         for (int it = 0; it < 2; ++it) y = __fma_rn(__dmul_rn(y, 0.5), __fma_rn(-n2, __dmul_rn(y, y), 1.0), y);
-        const double f = __dmul_rn(fp.radius, y);
+        double rad = fp.radius;
+        if (fp.damp != 0.0f) {
+            const float hgt = __fmul_rn(fp.damp, fbm3(__double2float_rn(__dmul_rn(p[0], y)),
+                                                     __double2float_rn(__dmul_rn(p[1], y)),
+                                                     __double2float_rn(__dmul_rn(p[2], y)), fp.dfreq, fp.doct,
+                                                     fp.dseed));
+            rad = __dadd_rn(rad, (double)hgt);
+        }
+        const double f = __dmul_rn(rad, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c) r[c] = __double2float_rn(__fma_rn(p[c], f, -fp.eye[c]));
     } else if (precision == 1) {
@@ -367,6 +470,7 @@ __device__ __forceinline__ void eval_vertex(const T W[9], int v, int d, const Fr
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             r[c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])), __fmul_rn(w2, R[6 + c]));
+        if (fp.damp != 0.0f) displace_plain(r, fp);
     }
 }
 
@@ -417,6 +521,9 @@ __device__ __forceinline__ void eval_vertices(const T W[9], int d, const FrameP&
             for (int c = 0; c < 3; ++c)
                 r[3 * i + c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])), __fmul_rn(w2, R[6 + c]));
         }
+        if (fp.damp != 0.0f)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) displace_plain(r + 3 * i, fp);
     }
 }
 

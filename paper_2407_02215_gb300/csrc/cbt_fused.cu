@@ -231,12 +231,13 @@ __device__ void phase_prep(const BatchDev& bt, Pair* s_warp, uint32_t* s_tmp) {
         }
     }
     // block 0 sets up the instances; the others share the root tables in
-    // warp ranges of kRelRange entries
+    // warp ranges (a multiple of 32 entries, at most kRelRange, enough ranges
+    // for every warp)
     if (gridDim.x == 1 || blockIdx.x > 0) {
         const uint32_t nb = gridDim.x > 1 ? gridDim.x - 1u : 1u, bb = gridDim.x > 1 ? blockIdx.x - 1u : 0u;
         const uint32_t nw = nb * (kFThreads / 32), wid = bb * (kFThreads / 32) + threadIdx.x / 32u;
-        for (uint32_t e = wid * kRelRange; e < bt.Trel; e += nw * kRelRange)
-            rel_range(bt, e, min(bt.Trel, e + kRelRange));
+        const uint32_t per = min(kRelRange, ((bt.Trel + nw - 1u) / nw + 31u) & ~31u);
+        for (uint32_t e = wid * per; e < bt.Trel; e += nw * per) rel_range(bt, e, min(bt.Trel, e + per));
     }
 }
 
@@ -265,7 +266,7 @@ __device__ __forceinline__ void walk_list(const Inst& I, const uint2* s_list, ui
 __device__ __forceinline__ void classify_one(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i, uint32_t s,
                                              uint64_t j, const uint32_t* s_tab, uint32_t* s_cnt, bool chain,
                                              uint32_t* s_n, uint2* s_list) {
-    const uint32_t cmd = classify_item(I, fp, key, i, s, j, s_tab, s_cnt, fp.precision == 3 && fp.vout);
+    const uint32_t cmd = classify_item(I, fp, key, i, s, j, s_tab, s_cnt, vc_form(fp) && fp.vout);
     const bool split = (cmd & kSplitWish) && chain;
     const bool group = (cmd & kMergeWish) && !(cmd & kHeapOdd);
     if (split || group) s_list[atomicAdd(s_n, 1u)] = make_uint2(i | (split ? 0x80000000u : 0u), s);
@@ -865,20 +866,52 @@ __device__ void phase_compact(const BatchDev& bt, FCtx& c, const uint32_t* s_tab
 #endif
 
 // P9 (single instance): the vertices of the new live list, strided over the
-// whole grid (word tiles hold very different live counts). In the sphere
-// form the unchanged bisectors' vertices are copied from the cache P1 filled
-// (each costs three FP64 projections to evaluate); otherwise the slot and
+// whole grid (word tiles hold very different live counts). In the sphere and
+// displaced forms the unchanged bisectors' vertices are copied from the
+// cache P1 filled (each costs three FP64 projections or three noise sums to
+// evaluate), and the new ones are listed and evaluated densely by the block
+// (so that no warp idles beside one evaluating lane); otherwise the slot and
 // heap ID of the next round are loaded while the current one is evaluated.
-__device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_tab) {
+__device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_tab, uint32_t* s_list,
+                               uint32_t* s_n) {
     ctx_tile(bt, bt.tile_base, 0, 1, c);
     const Inst& I = c.I;
     const FrameP& fp = c.fp;
     if (!fp.vout) return;
     const uint32_t n = min(__ldcg(I.sums + 1), fp.vcap);
     const uint32_t stride = gridDim.x * kFThreads;
-    if (fp.precision == 3) {  // the LOD test's vertices are cached for the unchanged bisectors
-        for (uint32_t i = blockIdx.x * kFThreads + threadIdx.x; i < n; i += stride)
-            vertex_item_cached(I, fp, i, I.live[i], s_tab, fp.vout);
+    if (vc_form(fp)) {
+        auto evaluate = [&](uint32_t cnt) {
+            for (uint32_t q = threadIdx.x; q < cnt; q += kFThreads) {
+                const uint32_t i = s_list[q];
+                vertex_item(I, fp, i, I.heap[I.live[i]], s_tab, fp.vout);
+            }
+        };
+        if (threadIdx.x == 0) *s_n = 0;
+        __syncthreads();
+        for (uint32_t base = blockIdx.x * kFThreads; base < n; base += stride) {
+            const uint32_t i = base + threadIdx.x;
+            if (i < n) {
+                const uint32_t s = I.live[i];
+                if (*cmd_ptr(I, s) & kVcValid) {
+                    const float* src = I.vc + 9ull * s;
+                    float* o = fp.vout + 9ull * i;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) o[k] = src[k];
+                } else {
+                    s_list[atomicAdd(s_n, 1u)] = i;
+                }
+            }
+            __syncthreads();
+            const uint32_t cnt = *s_n;
+            if (cnt > kFBuf - kFThreads) {  // block-uniform: make room
+                evaluate(cnt);
+                __syncthreads();
+                if (threadIdx.x == 0) *s_n = 0;
+                __syncthreads();
+            }
+        }
+        evaluate(*s_n);
         return;
     }
     uint32_t i = blockIdx.x * kFThreads + threadIdx.x;
@@ -934,7 +967,7 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame(Batch
     if (bt.B == 1) {
         grid_sync(bt.bg, epoch, 9u);
         stamp(bt, 9);
-        phase_vertices(bt, s_c, s_tab);
+        phase_vertices(bt, s_c, s_tab, s_buf, &s_n);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

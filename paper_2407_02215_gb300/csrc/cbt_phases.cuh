@@ -438,9 +438,9 @@ __device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uin
     return true;
 }
 
-// With `cache` (the one-launch frame exporting sphere-form vertices) the LOD
-// test's vertices go to vc[s] and the command word says so (kVcValid): the
-// export then copies them instead of projecting again in FP64.
+// With `cache` (the one-launch frame exporting sphere-form or displaced
+// vertices) the LOD test's vertices go to vc[s] and the command word says so
+// (kVcValid): the export then copies them instead of evaluating them again.
 __device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
                                                   uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt,
                                                   bool cache = false) {
@@ -807,11 +807,11 @@ __device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uin
 }
 
 // Vertices of the live bisector in slot s at output row i: in the sphere
-// form copied from the frame's cache when the LOD test stored them, else
-// evaluated.
+// and displaced forms copied from the frame's cache when the LOD test stored
+// them, else evaluated.
 __device__ __forceinline__ void vertex_item_cached(const Inst& I, const FrameP& fp, uint32_t i, uint32_t s,
                                                    const uint32_t* tab, float* out) {
-    if (fp.precision == 3 && (*cmd_ptr(I, s) & kVcValid)) {
+    if (vc_form(fp) && (*cmd_ptr(I, s) & kVcValid)) {
         const float* src = I.vc + 9ull * s;
         float* o = out + 9ull * i;
 #pragma unroll

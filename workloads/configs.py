@@ -109,3 +109,33 @@ def config5(n_inst: int = 1024, n_planets: int = 8, n_frames: int = 64, seed: in
         p.name = f"planet{k}"
         specs.append(p)
     return specs
+
+
+def _displaced(spec: InstanceSpec, amp: float, freq: float, octaves: int, seed: int) -> InstanceSpec:
+    for fp in spec.frames:
+        fp.disp_amplitude, fp.disp_frequency, fp.disp_octaves, fp.disp_seed = amp, freq, octaves, seed
+    return spec
+
+
+def config_terrain(n_frames: int = 120, tau_px: float = 2.0, nx: int = 100, D: int = 20, amp: float = 0.02,
+                   freq: float = 4.0, octaves: int = 6, seed: int = 23) -> InstanceSpec:
+    """Config 2's grid flythrough with the surface displaced: z grows by
+    amp * fbm(world x, y), a 6-octave value noise from 4 to 128 cells per
+    unit, standing in for the paper's elevation data plus noise octaves
+    (Sec. 4). The LOD test sees the displaced vertices."""
+    mesh = M.grid_mesh(nx, nx, tri_frac=0.1, seed=2, height_sigma=0.05)
+    cams = C.flythrough_path(n_frames, seed=2)
+    frames = [C.frame_params(c, tau_px) for c in cams]
+    return _displaced(InstanceSpec("terrain", mesh, D, 26, frames), amp, freq, octaves, seed)
+
+
+def config_waves(n_frames: int = 300, tau_px: float = 14.0, D: int = 17, max_depth: int = 50,
+                 radius: float = 6.371e6, amp: float = 2.0, freq: float = 6371.0, octaves: int = 4,
+                 seed: int = 29) -> InstanceSpec:
+    """The paper's water planet (Sec. 4): the dodecahedron planet with the
+    projected vertices displaced radially by amp * fbm(unit direction), a
+    4-octave value noise with cells of 1 km down to 125 m, standing in for
+    its four FFT wave layers."""
+    spec = config_dodeca(n_frames, tau_px, D, max_depth, radius)
+    spec.name = "wave-planet"
+    return _displaced(spec, amp, freq, octaves, seed)
