@@ -520,13 +520,14 @@ def bench_serve(args):
 
 
 def bench_reduce(args):
-    """SumReduction (Sec. 3.1) alone at 2^27 slots, the size at which the paper
-    times the prior method's reduction (0.4 ms on its GPU; context, not a
-    ratio): a seeded random bitfield of 16 MB in, the 32 MB sum tree out, L2
-    flushed before every timed run."""
+    """SumReduction (Sec. 3.1) alone, and with CachePointers (Alg. 7 for every
+    index), at 2^27 slots, the size at which the paper times the prior
+    method's reduction (0.4 ms on its GPU; context, not a ratio): a seeded
+    random bitfield of 16 MB in, the 32 MB sum tree out, then the 256 MB live
+    list; L2 flushed before every timed run."""
     import torch
 
-    from paper_2407_02215_gb300 import sum_reduce
+    from paper_2407_02215_gb300 import compact, sum_reduce
     D = 27
     W = 1 << (D - 5)
     g = torch.Generator(device="cuda").manual_seed(27)
@@ -535,28 +536,52 @@ def bench_reduce(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
         sum_reduce(bits, D, sums)
-    reps = 50
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    for a, b in ev:
-        flush.zero_()
-        a.record()
-        sum_reduce(bits, D, sums)
-        b.record()
     torch.cuda.synchronize()
-    ms = np.array([a.elapsed_time(b) for a, b in ev])
-    # the bitfield is read once; every node of the tree (2W words) is written once
+    n = int(sums[1].item())
+    live = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        compact(bits, sums, D, live)
+    reps = 50
+
+    def timed(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in ev]) * 1e3
+
+    us = timed(lambda: sum_reduce(bits, D, sums))
+    us_c = timed(lambda: compact(bits, sums, D, live))
+    us_rc = timed(lambda: (sum_reduce(bits, D, sums), compact(bits, sums, D, live)))
+    # reduction: the bitfield is read once, every node of the tree (2W words)
+    # written once; compaction: the bitfield read, 4 bytes per set bit written
     alg = 4.0 * W + 8.0 * W
+    alg_c = 4.0 * W + 4.0 * n
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    gbs = alg / (ms.mean() / 1e3) / 1e9
+    gbs = alg / (us.mean() / 1e6) / 1e9
+    gbs_c = alg_c / (us_c.mean() / 1e6) / 1e9
     root = int(sums[1].item())
-    want = int(np.unpackbits(bits.cpu().numpy().view(np.uint8)).sum())
+    host = bits.cpu().numpy().view(np.uint32)
+    want = int(np.unpackbits(host.view(np.uint8)).sum())
+    lv = live.cpu().numpy().view(np.uint32).astype(np.int64)
+    ok = bool(lv.size == want and np.all(np.diff(lv) > 0) and np.all((host[lv >> 5] >> (lv & 31).astype(np.uint32)) & 1))
     return {"metric": "CBT sum reduction over 2^27 slots (Sec. 3.1), us per reduction", "unit": "us",
-            "value": float(ms.mean() * 1e3), "p50": float(np.median(ms) * 1e3), "p99": float(np.percentile(ms, 99) * 1e3),
+            "value": float(us.mean()), "p50": float(np.median(us)), "p99": float(np.percentile(us, 99)),
             "higher_is_better": False,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                          "algorithmic_bytes": alg, "peak_source": "measured" if peaks else "fallback"},
             "root": root, "root_equals_popcount": root == want,
+            "compaction": {"us_mean": float(us_c.mean()), "us_p50": float(np.median(us_c)),
+                           "us_p99": float(np.percentile(us_c, 99)), "live": n,
+                           "roofline": {"bound": "hbm", "achieved": gbs_c, "peak": peak, "unit": "GB/s",
+                                        "frac": gbs_c / peak, "algorithmic_bytes": alg_c},
+                           "live_list_valid": ok},
+            "reduce_plus_compact": {"us_mean": float(us_rc.mean()), "us_p50": float(np.median(us_rc)),
+                                    "us_p99": float(np.percentile(us_rc, 99))},
             "paper": {"value_us": 400.0, "what": "original implicit CBT sum reduction at 2^27 on an AMD 6800 XT",
                       "cite": "Sec. 4 (reduction cost of the prior method)"},
             "config": {"workload": "reduce: random bitfield (seeded), 2^27 slots, L2 flushed before every run",

@@ -394,6 +394,21 @@ void cbt_server_destroy(cbt_server* sv);
  * CBT_ECUDA. Asynchronous. */
 int cbt_sum_reduce(const uint32_t* d_bitfield, int32_t D, uint32_t* d_sums, cbt_stream_t stream);
 
+/* CachePointers (Alg. 7, OneToBitID for every index) alone over a caller's
+ * bitfield: d_live[i] = the position of the i-th set bit (from 0), for every
+ * i below the number of set bits; with cbt_sum_reduce, the prior method's
+ * reduction plus compaction that the paper times at 2^27 slots (Sec. 4).
+ *   d_bitfield: DEVICE u32[2^D / 32], read only;
+ *   d_sums: DEVICE u32[2W], the sum tree of d_bitfield as cbt_sum_reduce
+ *           wrote it (read only; its root sums[1] is the output count);
+ *   D: 5 <= D <= 28;
+ *   d_live: DEVICE u32[cap], caller-owned; positions at index >= cap are
+ *           not written (read the count from sums[1]).
+ * One launch on `stream`; allocates nothing. Errors: CBT_EINVAL (NULL
+ * pointer, D < 5), CBT_ECAPACITY (D > 28), CBT_ECUDA. Asynchronous. */
+int cbt_compact(const uint32_t* d_bitfield, const uint32_t* d_sums, int32_t D, uint32_t* d_live, uint32_t cap,
+                cbt_stream_t stream);
+
 /* The reduction and live-slot compaction step of cbt_update (the CBT sum
  * tree and the ascending list of set bits) over a caller's bitfield, for
  * callers that cannot allocate device memory: a real-time frame loop in which

@@ -97,6 +97,12 @@ uint32_t or_cbt_one_to_bit(int32_t D, const uint32_t* cbt, uint32_t index) {
     return bit - n;
 }
 
+/* CachePointers (Alg. 7 for every index): out[i] = OneToBitID(i) for every
+ * i below the root. */
+void or_cbt_compact(int32_t D, const uint32_t* cbt, uint32_t* out) {
+    for (uint32_t i = 0; i < cbt[1]; ++i) out[i] = or_cbt_one_to_bit(D, cbt, i);
+}
+
 /* Alg. 8: slot of the index-th bit set to zero; c is the leaf count of the
  * subtree being examined, so c - CBT[node] counts its zeros. */
 uint32_t or_cbt_zero_to_bit(int32_t D, const uint32_t* cbt, uint32_t index) {

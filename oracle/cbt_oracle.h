@@ -109,6 +109,7 @@ int or_chain_cost(const or_state* st, uint32_t slot, uint32_t* cost);
 /* Building blocks exposed for the pins. */
 void or_cbt_sum_reduction(int32_t D, uint32_t* cbt);
 uint32_t or_cbt_one_to_bit(int32_t D, const uint32_t* cbt, uint32_t index);
+void or_cbt_compact(int32_t D, const uint32_t* cbt, uint32_t* out);
 uint32_t or_cbt_zero_to_bit(int32_t D, const uint32_t* cbt, uint32_t index);
 void or_decode_weights(uint64_t j, int32_t ch, uint64_t* W9);
 uint64_t or_splitmix64(uint64_t x);

@@ -36,6 +36,7 @@ def _load():
         lib.or_cbt_sum_reduction.argtypes = [C.c_int32, P]
         lib.or_cbt_one_to_bit.argtypes = [C.c_int32, P, C.c_uint32]
         lib.or_cbt_one_to_bit.restype = C.c_uint32
+        lib.or_cbt_compact.argtypes = [C.c_int32, P, P]
         lib.or_cbt_zero_to_bit.argtypes = [C.c_int32, P, C.c_uint32]
         lib.or_cbt_zero_to_bit.restype = C.c_uint32
         lib.or_decode_weights.argtypes = [C.c_uint64, C.c_int32, P]
@@ -255,6 +256,14 @@ def cbt_sum_reduction(D: int, cbt: np.ndarray) -> np.ndarray:
 def cbt_one_to_bit(D: int, cbt: np.ndarray, i: int) -> int:
     c = np.ascontiguousarray(cbt, np.uint32)
     return int(_load().or_cbt_one_to_bit(D, _ptr(c), i))
+
+
+def cbt_compact(D: int, cbt: np.ndarray) -> np.ndarray:
+    """OneToBitID(i) for every i below the root (CachePointers, Alg. 7)."""
+    c = np.ascontiguousarray(cbt, np.uint32)
+    out = np.zeros(max(int(c[1]), 1), np.uint32)
+    _load().or_cbt_compact(D, _ptr(c), _ptr(out))
+    return out[:int(c[1])]
 
 
 def cbt_zero_to_bit(D: int, cbt: np.ndarray, i: int) -> int:

@@ -82,6 +82,7 @@ def load(path: str | None = None):
     lib.cbt_phase_name.argtypes = [U32]
     lib.cbt_phase_name.restype = C.c_char_p
     lib.cbt_sum_reduce.argtypes = [P, I32, P, P]
+    lib.cbt_compact.argtypes = [P, P, I32, P, C.c_uint32, P]
     lib.cbt_server_set_fused.argtypes = [P, C.c_int]
     lib.cbt_selftest_bounded_wait.argtypes = [P, I32, I32, P]
     lib.cbt_set_fused.argtypes = [P, C.c_int, P]
@@ -162,6 +163,16 @@ def sum_reduce(bits, D: int, sums, stream=None):
     rc = load().cbt_sum_reduce(_t_ptr(bits), int(D), _t_ptr(sums), _stream_ptr(stream))
     if rc:
         raise CBTError(rc, "cbt_sum_reduce")
+
+
+def compact(bits, sums, D: int, live, stream=None):
+    """CachePointers (Alg. 7) of a device bitfield with its sum tree (from
+    sum_reduce): live[i] = position of the i-th set bit, for i < sums[1]
+    (entries beyond live's length are dropped)."""
+    rc = load().cbt_compact(_t_ptr(bits), _t_ptr(sums), int(D), _t_ptr(live), int(live.numel()),
+                            _stream_ptr(stream))
+    if rc:
+        raise CBTError(rc, "cbt_compact")
 
 
 def workspace_bytes(H: int, D: int) -> int:

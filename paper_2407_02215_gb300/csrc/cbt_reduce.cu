@@ -1,4 +1,5 @@
-// SumReduction (Sec. 3.1) over a caller's bitfield, as a streaming kernel:
+// SumReduction (Sec. 3.1) over a caller's bitfield, as a streaming kernel
+// (and CachePointers over the same bitfield, further below):
 // the per-level uint32 sums of the CBT above its bitfield words (the layout
 // of cbt_cbt: sums[W + w] = popc(word w), sums[n] = sums[2n] + sums[2n+1],
 // sums[1] = the number of set bits). One launch: each block reduces chunks
@@ -120,7 +121,115 @@ __global__ void __launch_bounds__(1024) k_sum_small(const uint32_t* __restrict__
     top_levels(s, W, sums);
 }
 
+// CachePointers (Alg. 7 for every index) over a caller's bitfield and the
+// sum tree k_sum_chunks wrote for it: live[i] = the position of the i-th set
+// bit. Every warp takes 128-word segments (level-7 nodes; small enough that
+// the warps share them evenly) in turn, with no block-wide step: the
+// segment's first output index is read off the tree (the left siblings along
+// its node's path, one level per lane), its 4 rows of 32 words are loaded at
+// once, and each row is compacted: every lane writes the
+// positions of its word's set bits into the warp's staging row at its scan
+// offset, and the warp copies the row out with coalesced stores. Positions at
+// index >= cap are dropped.
+constexpr int kStage = 32 * 32;  // positions of 32 words, at most
+constexpr uint32_t kSegLog = 7;
+constexpr uint32_t kSegWords = 1u << kSegLog;
+constexpr int kSegRows = (int)kSegWords / 32;
+__global__ void __launch_bounds__(kRThreads) k_compact_segments(const uint32_t* __restrict__ bits,
+                                                                const uint32_t* __restrict__ sums, uint32_t W,
+                                                                uint32_t* __restrict__ live, uint32_t cap) {
+    __shared__ uint32_t s_stage[kRThreads / 32][kStage];
+    const uint32_t nseg = W / kSegWords;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* stage = s_stage[warp];
+    const uint32_t nwarps = gridDim.x * (kRThreads / 32);
+    for (uint32_t sg = blockIdx.x * (kRThreads / 32) + (uint32_t)warp; sg < nseg; sg += nwarps) {
+        const uint32_t w0 = sg * kSegWords;
+        uint32_t x[kSegRows];
+#pragma unroll
+        for (int r = 0; r < kSegRows; ++r) x[r] = __ldcs(bits + w0 + 32u * r + (uint32_t)lane);
+        const uint32_t n = ((W + w0) >> kSegLog) >> lane;  // the segment's node, `lane` levels up
+        uint32_t base = (n > 1u && (n & 1u)) ? __ldg(sums + n - 1u) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) base += __shfl_xor_sync(0xFFFFFFFFu, base, o);
+#pragma unroll
+        for (int r = 0; r < kSegRows; ++r) {
+            const uint32_t w = w0 + 32u * r + (uint32_t)lane;
+            uint32_t m = x[r];
+            const uint32_t p = (uint32_t)__popc(m);
+            uint32_t inc = p;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            uint32_t k = inc - p;
+            while (m) {
+                stage[k++] = w * 32u + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+            }
+            __syncwarp();
+            for (uint32_t q = (uint32_t)lane; q < tot; q += 32u)
+                if (base + q < cap) __stcs(live + base + q, stage[q]);
+            __syncwarp();
+            base += tot;
+        }
+    }
+}
+
+// W < kSegWords: one warp walks the words 32 at a time.
+__global__ void __launch_bounds__(32) k_compact_small(const uint32_t* __restrict__ bits, uint32_t W,
+                                                      uint32_t* __restrict__ live, uint32_t cap) {
+    __shared__ uint32_t stage[kStage];
+    const int lane = threadIdx.x;
+    uint32_t base = 0;
+    for (uint32_t w0 = 0; w0 < W; w0 += 32u) {
+        const uint32_t w = w0 + (uint32_t)lane;
+        uint32_t x = w < W ? bits[w] : 0u;
+        const uint32_t p = (uint32_t)__popc(x);
+        uint32_t inc = p;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        uint32_t k = inc - p;
+        while (x) {
+            stage[k++] = w * 32u + (uint32_t)(__ffs(x) - 1);
+            x &= x - 1u;
+        }
+        __syncwarp();
+        for (uint32_t q = (uint32_t)lane; q < tot; q += 32u)
+            if (base + q < cap) live[base + q] = stage[q];
+        __syncwarp();
+        base += tot;
+    }
+}
+
 }  // namespace
+
+extern "C" int cbt_compact(const uint32_t* d_bitfield, const uint32_t* d_sums, int32_t D, uint32_t* d_live,
+                           uint32_t cap, cbt_stream_t stream) {
+    if (!d_bitfield || !d_sums || (!d_live && cap) || D < 5) return CBT_EINVAL;
+    if (D > 28) return CBT_ECAPACITY;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const uint32_t W = 1u << (D - 5);
+    if (cap == 0) return CBT_OK;
+    if (W < kSegWords) {
+        k_compact_small<<<1, 32, 0, s>>>(d_bitfield, W, d_live, cap);
+    } else {
+        const uint32_t blocks = W / kSegWords / (kRThreads / 32);  // one segment per warp at most
+        int dev = 0, sms = 1, per = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_compact_segments, kRThreads, 0);
+        const uint32_t grid = static_cast<uint32_t>(sms) * static_cast<uint32_t>(per > 0 ? per : 1);
+        const uint32_t g = blocks < 1u ? 1u : (blocks < grid ? blocks : grid);
+        k_compact_segments<<<g, kRThreads, 0, s>>>(d_bitfield, d_sums, W, d_live, cap);
+    }
+    return cudaGetLastError() == cudaSuccess ? CBT_OK : CBT_ECUDA;
+}
 
 extern "C" int cbt_sum_reduce(const uint32_t* d_bitfield, int32_t D, uint32_t* d_sums, cbt_stream_t stream) {
     if (!d_bitfield || !d_sums || D < 5) return CBT_EINVAL;

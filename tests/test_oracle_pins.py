@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle import (Oracle, cbt_one_to_bit, cbt_sum_reduction, cbt_zero_to_bit, decode_weights, fbm,
+from oracle import (Oracle, cbt_compact, cbt_one_to_bit, cbt_sum_reduction, cbt_zero_to_bit, decode_weights, fbm,
                     halfedges_from_faces, lod_test, lowbias32, splitmix64)
 from workloads.cameras import (MODE_FORCE_MERGE, MODE_FORCE_SPLIT, MODE_LIST, MODE_RANDOM,
                                forced_params)
@@ -94,6 +94,7 @@ def test_cbt_search_brute_force(D):
             assert cbt_one_to_bit(D, cbt, int(i)) == ones[i]
         for i in rng.choice(max(1, zeros.size), size=min(50, zeros.size), replace=False) if zeros.size else []:
             assert cbt_zero_to_bit(D, cbt, int(i)) == zeros[i]
+        assert np.array_equal(cbt_compact(D, cbt), ones)
 
 
 def test_memory_formula_d17():
