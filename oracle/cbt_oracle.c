@@ -52,6 +52,7 @@ struct or_state {
     uint32_t* nxt;
     uint32_t* prv;
     double* root; /* [H][3 vertices][xyz] */
+    uint32_t* corner_id; /* [H][3] global point of each root corner: vert[h], vert[next h], V + face[h] */
     uint64_t order_seed; /* 0: textbook step in slot order; else a seeded permutation */
 };
 
@@ -224,9 +225,11 @@ int or_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_t
     st->nxt = (uint32_t*)malloc(sizeof(uint32_t) * st->cap);
     st->prv = (uint32_t*)malloc(sizeof(uint32_t) * st->cap);
     st->root = (double*)calloc((size_t)H * 9u, sizeof(double));
+    st->corner_id = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)H * 3u);
     double* cen = (double*)calloc((size_t)H * 3u, sizeof(double));
     int32_t* first = (int32_t*)malloc(sizeof(int32_t) * (size_t)H);
-    if (!st->cbt || !st->heap || !st->twn || !st->nxt || !st->prv || !st->root || !cen || !first) {
+    if (!st->cbt || !st->heap || !st->twn || !st->nxt || !st->prv || !st->root || !st->corner_id || !cen ||
+        !first) {
         free(cen);
         free(first);
         or_destroy(st);
@@ -254,6 +257,9 @@ int or_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_t
             st->root[9 * h + 3 + c] = pos[3 * vert[next[h]] + c];
             st->root[9 * h + 6 + c] = cen[3 * face[h] + c];
         }
+        st->corner_id[3 * h + 0] = (uint32_t)vert[h];
+        st->corner_id[3 * h + 1] = (uint32_t)vert[next[h]];
+        st->corner_id[3 * h + 2] = (uint32_t)V + (uint32_t)face[h];
     }
     free(cen);
     free(first);
@@ -280,6 +286,7 @@ void or_destroy(or_state* st) {
     free(st->nxt);
     free(st->prv);
     free(st->root);
+    free(st->corner_id);
     free(st);
 }
 
@@ -549,6 +556,116 @@ void or_vertices_f64(const or_state* st, double* out) {
             }
         ++i;
     }
+}
+
+/* ------------------------------------------------------ indexed export */
+
+/* Identity of a bisector corner as a point of the subdivided surface (R15
+ * reading): the exact integer weights of its row (R9, over 2^d) reduced to
+ * lowest terms (halved while all are even and d > 0), each nonzero weight
+ * paired with the global point of its root corner (mesh vertex, or V + face
+ * for a face centroid), the pairs in ascending point order. Corners of two
+ * bisectors are the same vertex exactly when these are equal. */
+typedef struct {
+    uint32_t d, n;
+    uint32_t id[3];
+    uint64_t w[3];
+    uint32_t occ; /* 3 i + corner */
+} vkey;
+
+static void corner_key(const or_state* st, uint64_t j, int v, uint32_t occ, vkey* k) {
+    int d = depth_of(st, j);
+    const uint32_t h = root_of(st, j);
+    uint64_t W[9];
+    or_decode_weights(j, st->ch, W);
+    uint64_t w[3] = {W[3 * v + 0], W[3 * v + 1], W[3 * v + 2]};
+    while (d > 0 && !((w[0] | w[1] | w[2]) & 1u)) {
+        for (int c = 0; c < 3; ++c) w[c] >>= 1;
+        --d;
+    }
+    memset(k, 0, sizeof(*k));
+    k->d = (uint32_t)d;
+    k->occ = occ;
+    for (int c = 0; c < 3; ++c) k->id[c] = OR_NULL;
+    for (int c = 0; c < 3; ++c) {
+        if (!w[c]) continue;
+        /* insert (id, w) keeping the ids ascending */
+        const uint32_t id = st->corner_id[3 * h + (uint32_t)c];
+        int p = (int)k->n;
+        while (p > 0 && k->id[p - 1] > id) {
+            k->id[p] = k->id[p - 1];
+            k->w[p] = k->w[p - 1];
+            --p;
+        }
+        k->id[p] = id;
+        k->w[p] = w[c];
+        ++k->n;
+    }
+}
+
+static int vkey_cmp(const void* pa, const void* pb) {
+    const vkey* a = (const vkey*)pa;
+    const vkey* b = (const vkey*)pb;
+    if (a->d != b->d) return a->d < b->d ? -1 : 1;
+    if (a->n != b->n) return a->n < b->n ? -1 : 1;
+    for (int c = 0; c < 3; ++c) {
+        if (a->id[c] != b->id[c]) return a->id[c] < b->id[c] ? -1 : 1;
+        if (a->w[c] != b->w[c]) return a->w[c] < b->w[c] ? -1 : 1;
+    }
+    if (a->occ != b->occ) return a->occ < b->occ ? -1 : 1;
+    return 0;
+}
+
+static int vkey_same(const vkey* a, const vkey* b) {
+    if (a->d != b->d || a->n != b->n) return 0;
+    for (int c = 0; c < 3; ++c)
+        if (a->id[c] != b->id[c] || a->w[c] != b->w[c]) return 0;
+    return 1;
+}
+
+int or_export_indexed(const or_state* st, const float* tri_vertices, float* vertices, uint32_t* indices,
+                      uint64_t* tri_ids, uint32_t* n_vertices) {
+    const uint32_t N = st->cbt[1];
+    const uint32_t n3 = 3u * N;
+    vkey* keys = (vkey*)malloc(sizeof(vkey) * (n3 ? n3 : 1u));
+    uint32_t* rep = (uint32_t*)malloc(sizeof(uint32_t) * (n3 ? n3 : 1u));
+    uint32_t* vid = (uint32_t*)malloc(sizeof(uint32_t) * (n3 ? n3 : 1u));
+    if (!keys || !rep || !vid) {
+        free(keys);
+        free(rep);
+        free(vid);
+        return OR_ENOMEM;
+    }
+    uint32_t i = 0;
+    for (uint32_t s = 0; s < st->cap; ++s) {
+        if (!st->cbt[st->cap + s]) continue;
+        for (int c = 0; c < 3; ++c) corner_key(st, st->heap[s], c, 3u * i + (uint32_t)c, &keys[3u * i + (uint32_t)c]);
+        if (tri_ids) tri_ids[i] = st->heap[s];
+        ++i;
+    }
+    /* each corner's vertex is represented by its first occurrence */
+    qsort(keys, n3, sizeof(vkey), vkey_cmp);
+    for (uint32_t a = 0; a < n3;) {
+        uint32_t b = a + 1u;
+        while (b < n3 && vkey_same(&keys[a], &keys[b])) ++b;
+        for (uint32_t k = a; k < b; ++k) rep[keys[k].occ] = keys[a].occ;
+        a = b;
+    }
+    /* vertices numbered in order of first occurrence */
+    uint32_t nv = 0;
+    for (uint32_t o = 0; o < n3; ++o)
+        if (rep[o] == o) {
+            vid[o] = nv;
+            if (vertices && tri_vertices)
+                for (int c = 0; c < 3; ++c) vertices[3u * nv + (uint32_t)c] = tri_vertices[3u * o + (uint32_t)c];
+            ++nv;
+        }
+    for (uint32_t o = 0; o < n3; ++o) indices[o] = vid[rep[o]];
+    *n_vertices = nv;
+    free(keys);
+    free(rep);
+    free(vid);
+    return OR_OK;
 }
 
 /* ------------------------------------------------------------ LOD test */

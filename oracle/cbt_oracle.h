@@ -98,6 +98,14 @@ uint32_t or_leaves(const or_state* st, uint32_t* slots, uint64_t* heap, uint32_t
 void or_vertices(const or_state* st, const double origin[3], uint32_t precision,
                  int32_t fixed_shift, double sphere_radius, const or_disp* disp, float* out);
 void or_vertices_f64(const or_state* st, double* out);
+/* Indexed form of the live bisectors (R15 reading): corners that are the
+ * same point of the subdivided surface share one vertex; vertices are
+ * numbered in order of first occurrence over (live index, corner).
+ * indices[N][3]; vertices[nv][3] copied from tri_vertices[N][3][3] (the
+ * per-bisector vertices, as or_vertices writes them) at each vertex's first
+ * occurrence (both may be NULL); tri_ids[N] = heap IDs (may be NULL). */
+int or_export_indexed(const or_state* st, const float* tri_vertices, float* vertices, uint32_t* indices,
+                      uint64_t* tri_ids, uint32_t* n_vertices);
 void or_root_table(const or_state* st, double* out);
 
 /* Test hooks: the order in which the textbook step applies the requests

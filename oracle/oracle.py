@@ -30,6 +30,7 @@ def _load():
         lib.or_leaves.restype = C.c_uint32
         lib.or_vertices.argtypes = [P, P, C.c_uint32, C.c_int32, C.c_double, P, P]
         lib.or_vertices_f64.argtypes = [P, P]
+        lib.or_export_indexed.argtypes = [P, P, P, P, P, C.POINTER(C.c_uint32)]
         lib.or_root_table.argtypes = [P, P]
         lib.or_set_order_seed.argtypes = [P, C.c_uint64]
         lib.or_chain_cost.argtypes = [P, C.c_uint32, C.POINTER(C.c_uint32)]
@@ -223,6 +224,20 @@ class Oracle:
         _lib.or_vertices(self._h, _ptr(o), precision, fixed_shift, float(sphere_radius),
                          C.addressof(d) if d is not None else None, _ptr(out))
         return out
+
+    def export_indexed(self, tri_vertices=None):
+        """Indexed form of the live bisectors: (vertices [nv, 3] from
+        tri_vertices [N, 3, 3] or None, indices [N, 3], heap IDs [N])."""
+        n = self.live_count
+        idx = np.zeros((n, 3), np.uint32)
+        ids = np.zeros(n, np.uint64)
+        tv = np.ascontiguousarray(tri_vertices, np.float32) if tri_vertices is not None else None
+        vb = np.zeros((3 * n, 3), np.float32) if tv is not None else None
+        nv = C.c_uint32()
+        rc = _lib.or_export_indexed(self._h, _ptr(tv), _ptr(vb), _ptr(idx), _ptr(ids), C.byref(nv))
+        if rc:
+            raise OracleError(rc, "export_indexed")
+        return (vb[:nv.value] if vb is not None else None), idx, ids
 
     def vertices_f64(self):
         out = np.zeros((self.live_count, 3, 3), np.float64)

@@ -472,3 +472,56 @@ def test_displacement_sphere_is_radial():
     cross = np.linalg.norm(np.cross(v, flat), axis=1) / (np.linalg.norm(v, axis=1) * np.linalg.norm(flat, axis=1))
     assert cross.max() < 1e-6
     assert np.abs(hgt).max() > 1e3
+
+
+# ------------------------------------------------ indexed export (R15 reading)
+
+def _random_refine(o, frames, seed):
+    from workloads.cameras import forced_params as fp_
+    for k in range(frames):
+        o.update(fp_(MODE_RANDOM, seed=seed + k))
+
+
+@pytest.mark.parametrize("mesh_name", ["cube", "dodeca"])
+def test_indexed_export_euler_closed(mesh_name):
+    """A closed surface (sphere topology) keeps Euler characteristic 2 under
+    conforming bisection: with F triangles and E = 3F/2 edges the indexed
+    form must have exactly V = 2 + F/2 vertices (a missed merge of two
+    corners, or a wrong one, changes V); each triangle has three distinct
+    vertices; vertices are numbered in order of first appearance."""
+    m = W.meshes.cube_mesh() if mesh_name == "cube" else W.meshes.dodecahedron_mesh(1.0)
+    o = Oracle(m, 13, 12)
+    for k in range(6):
+        _random_refine(o, 2, 40 + 3 * k)
+        _, idx, ids = o.export_indexed()
+        F = idx.shape[0]
+        assert idx.max() + 1 == 2 + F // 2
+        assert np.all((idx[:, 0] != idx[:, 1]) & (idx[:, 1] != idx[:, 2]) & (idx[:, 0] != idx[:, 2]))
+        flat = idx.reshape(-1).astype(np.int64)
+        assert np.all(np.diff(np.maximum.accumulate(flat)) <= 1) and flat[0] == 0
+        assert np.array_equal(ids, o.leaves()[1])
+
+
+def test_indexed_export_euler_open_and_geometry():
+    """An open grid (disk topology): V - E + F = 1 with E = (3F + B) / 2, B
+    the border edges (null links of the leaves). And geometry decides
+    identity: corners given one index have the same FP64 position, and
+    different indices are different points."""
+    m = W.meshes.grid_mesh(5, 4, tri_frac=0.3, seed=8, height_sigma=0.05)
+    o = Oracle(m, 14, 14)
+    for k in range(5):
+        _random_refine(o, 2, 70 + 5 * k)
+        _, idx, _ = o.export_indexed()
+        F = idx.shape[0]
+        B = int((o.leaves()[2] == 0xFFFFFFFF).sum())
+        assert (3 * F + B) % 2 == 0
+        E = (3 * F + B) // 2
+        V = int(idx.max()) + 1
+        assert V - E + F == 1
+    pos = o.vertices_f64().reshape(-1, 3)
+    flat = idx.reshape(-1)
+    first = np.zeros((V, 3))
+    first[flat[::-1]] = pos[::-1]  # the first occurrence's position per index
+    assert np.abs(pos - first[flat]).max() <= 1e-12
+    q = np.round(first * 2 ** 30).astype(np.int64)
+    assert np.unique(q, axis=0).shape[0] == V
