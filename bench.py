@@ -682,6 +682,40 @@ def bench_terrain(args):
     return out
 
 
+def bench_index(args):
+    """Indexed export (cbt_index: deduplicated vertex buffer, index buffer and
+    triangle heap IDs for a visibility buffer) after every frame of the grid
+    flythrough; the export is timed alone (CUDA events around the call, which
+    returns the counts)."""
+    import torch
+
+    from paper_2407_02215_gb300 import CBT
+    spec = W.configs.config2()
+    g = CBT(spec.mesh, spec.D, spec.max_depth)
+    vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device="cuda")
+    ws = g.index_workspace(1 << spec.D)
+    ms, tris, verts = [], [], []
+    for k, fp in enumerate(spec.frames):
+        g.update(fp, vertices_out=vbuf)
+        n = g.live_count()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        v, idx, _ = g.index(vbuf[:n], workspace=ws)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= max(args.warmup, 3):
+            ms.append(a.elapsed_time(b))
+            tris.append(n)
+            verts.append(v.shape[0])
+    ms, tris = np.array(ms), np.array(tris)
+    return {"metric": "indexed export (vertex + index buffers), triangles/s", "unit": "triangles/s",
+            "value": float(tris.sum() / (ms.sum() / 1e3)), "ms_p50": float(np.median(ms)),
+            "ms_p99": float(np.percentile(ms, 99)), "triangles_p50": float(np.median(tris)),
+            "vertices_per_triangle": float(np.sum(verts) / tris.sum()),
+            "config": {"workload": "grid flythrough (100 x 100, pool 2^20, 120 frames): cbt_index after every "
+                                   "update, inputs resident", "frames_timed": int(ms.size)}}
+
+
 def bench_planet(args):
     """Planet descent (pool 2^22, max depth 48, fixed point): frame times."""
     import torch
@@ -716,7 +750,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
     ap.add_argument("--workload", default="grid",
-                    choices=["grid", "batch", "serve", "planet", "reduce", "dodeca", "waves", "terrain"],
+                    choices=["grid", "batch", "serve", "planet", "reduce", "dodeca", "waves", "terrain", "index"],
                     help="grid = the headline workload; the others are extra measurements")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--planets", type=int, default=8)
@@ -730,7 +764,7 @@ def main():
         P.build_library()
         fn = {"batch": bench_batch, "serve": bench_serve, "planet": bench_planet,
               "reduce": bench_reduce, "dodeca": bench_dodeca, "waves": bench_waves,
-              "terrain": bench_terrain}[args.workload]
+              "terrain": bench_terrain, "index": bench_index}[args.workload]
         print(json.dumps(fn(args)))
         return
     if args.impl == "reference":

@@ -198,6 +198,35 @@ int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_
  * Asynchronous. */
 int cbt_update(cbt_state* st, const cbt_frame* frame, cbt_stream_t stream);
 
+/* Indexed export of the live bisectors, the input of a visibility buffer
+ * (the paper exports its triangulation into one, Sec. 4). Corners that are
+ * the same point of the subdivided surface share one vertex: a corner's
+ * identity is its exact weight row (Eq. 1) in lowest terms over the global
+ * mesh vertices and face centroids of its root, so shared corners match
+ * across bisectors, roots and faces and the indexed mesh is watertight.
+ * Vertices are numbered in order of first occurrence over (live index,
+ * corner); triangle i is live bisector i (ascending slot, as cbt_leaves).
+ *   d_tri_vertices: DEVICE float[N][3][3], the per-bisector vertices of the
+ *           current live list (cbt_update's vertices_out or cbt_vertices);
+ *           may be NULL when d_vertices is NULL;
+ *   d_workspace: DEVICE scratch of cbt_index_workspace_bytes(N) bytes at
+ *           least, caller-owned, 256-byte aligned;
+ *   d_vertices: DEVICE float[vertices_cap][3] or NULL: each vertex's
+ *           position, copied from its first occurrence;
+ *   d_indices: DEVICE u32[triangles_cap][3];
+ *   d_heap: DEVICE u64[triangles_cap] or NULL: the triangles' heap IDs (the
+ *           visibility buffer's triangle payload);
+ *   *h_nvertices / *h_ntriangles receive the counts (either may be NULL).
+ * Errors: CBT_EINVAL (NULL state, workspace or indices; vertices without
+ * d_tri_vertices), CBT_ENOMEM (N > triangles_cap, workspace too small, or
+ * more vertices than vertices_cap: the counts are still returned),
+ * CBT_EDEVICE (two identities with one 64-bit hash: reported, never merged),
+ * CBT_ECUDA. Five launches on `stream`; synchronous (returns the counts). */
+size_t cbt_index_workspace_bytes(uint32_t max_live);
+int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_workspace, size_t bytes, float* d_vertices,
+              uint32_t vertices_cap, uint32_t* d_indices, uint32_t triangles_cap, uint64_t* d_heap,
+              uint32_t* h_nvertices, uint32_t* h_ntriangles, cbt_stream_t stream);
+
 /* Number of live bisectors (CBT root). Synchronous. */
 int cbt_live_count(cbt_state* st, uint32_t* h_count, cbt_stream_t stream);
 

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcbt.so")
-SOURCES = ["cbt_kernels.cu", "cbt_fused.cu", "cbt_reduce.cu", "cbt_api.cu", "cbt_static.cu", "ingest.cpp"]
+SOURCES = ["cbt_kernels.cu", "cbt_fused.cu", "cbt_reduce.cu", "cbt_index.cu", "cbt_api.cu", "cbt_static.cu",
+           "ingest.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",

@@ -46,6 +46,9 @@ def load(path: str | None = None):
     lib.cbt_live_count.argtypes = [P, C.POINTER(U32), P]
     lib.cbt_leaves.argtypes = [P, P, P, P, U32, C.POINTER(U32), P]
     lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
+    lib.cbt_index_workspace_bytes.argtypes = [U32]
+    lib.cbt_index_workspace_bytes.restype = C.c_size_t
+    lib.cbt_index.argtypes = [P, P, P, C.c_size_t, P, U32, P, U32, P, C.POINTER(U32), C.POINTER(U32), P]
     lib.cbt_cbt.argtypes = [P, P, P, P]
     lib.cbt_stats.argtypes = [P, P, P]
     lib.cbt_destroy.argtypes = [P]
@@ -326,6 +329,31 @@ class CBT:
         if rc:
             raise CBTError(rc, "cbt_vertices")
         return out[:int(cnt.value)]
+
+    def index_workspace(self, max_live: int):
+        """Device scratch for index() with up to max_live live bisectors."""
+        return torch.empty(int(_lib.cbt_index_workspace_bytes(int(max_live))), dtype=torch.uint8, device=self.device)
+
+    def index(self, tri_vertices=None, workspace=None, stream=None):
+        """Indexed export (cbt_index): (vertices [nv, 3] or None, indices
+        [N, 3] int32, heap IDs [N] int64). tri_vertices: the per-bisector
+        vertices [N, 3, 3] of the current live list."""
+        n = self.live_count(stream)
+        if workspace is None:
+            workspace = self.index_workspace(n)
+        m = max(n, 1)
+        idx = torch.empty((m, 3), dtype=torch.int32, device=self.device)
+        heap = torch.empty(m, dtype=torch.int64, device=self.device)
+        verts = torch.empty((3 * m, 3), dtype=torch.float32, device=self.device) if tri_vertices is not None else None
+        nv, nt = C.c_uint32(), C.c_uint32()
+        rc = _lib.cbt_index(self._h, _t_ptr(tri_vertices) if tri_vertices is not None else None, _t_ptr(workspace),
+                            workspace.numel(), _t_ptr(verts) if verts is not None else None,
+                            verts.shape[0] if verts is not None else 0, _t_ptr(idx), m, _t_ptr(heap),
+                            C.byref(nv), C.byref(nt), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_index")
+        k = int(nt.value)
+        return (verts[:int(nv.value)] if verts is not None else None), idx[:k], heap[:k]
 
     def cbt(self, stream=None):
         W = max(1, self.cap // 32)

@@ -45,7 +45,8 @@ uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems;
 
 // Per-instance arrays.
 struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, root64, rel, batch, total;
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, root64, rel, corner, batch,
+        total;
     uint32_t cap, W, ch;
 };
 
@@ -110,6 +111,7 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.vc = take(36u * cap);
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
+    L.corner = take(12u * h);
     const uint32_t Hh = static_cast<uint32_t>(H);
     const BatchLayout B = batch_layout(1, &L.cap, &L.W, &Hh);
     L.batch = take(B.total);
@@ -194,6 +196,7 @@ struct cbt_batch {
 
 struct cbt_state {
     Inst inst;
+    uint32_t* corner;  // [H][3] global points of the root corners: vert[h], vert[next h], V + face[h]
     void* workspace;
     size_t bytes;
     int sms;
@@ -545,18 +548,24 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     const size_t h = static_cast<size_t>(H);
     std::vector<int32_t> ints(3u * h);
     std::vector<double> hpos(3u * h);
+    std::vector<uint32_t> corner(3u * h);
     for (size_t k = 0; k < h; ++k) {
         ints[k] = twin[k];
         ints[h + k] = next[k];
         ints[2u * h + k] = prev[k];
         for (int c = 0; c < 3; ++c) hpos[3u * k + c] = pos[3u * static_cast<size_t>(vert[k]) + c];
+        corner[3u * k] = static_cast<uint32_t>(vert[k]);
+        corner[3u * k + 1u] = static_cast<uint32_t>(vert[next[k]]);
+        corner[3u * k + 2u] = static_cast<uint32_t>(V) + static_cast<uint32_t>(face[k]);
     }
+    st->corner = reinterpret_cast<uint32_t*>(b + L.corner);
     int32_t* d_ints = reinterpret_cast<int32_t*>(b + L.rel);
     double* d_hpos = reinterpret_cast<double*>(b + L.rel + align256(12u * h));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaMemsetAsync(I.g, 0, sizeof(Globals), s);
     cudaMemcpyAsync(d_ints, ints.data(), 12u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_hpos, hpos.data(), 24u * h, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(st->corner, corner.data(), 12u * h, cudaMemcpyHostToDevice, s);
     const int grid = static_cast<int>(std::min<uint32_t>((std::max(L.W, static_cast<uint32_t>(H)) + 255u) / 256u,
                                                          static_cast<uint32_t>(st->sms) * 4u));
     launch_init(I, d_ints, d_ints + h, d_ints + 2u * h, d_hpos, std::max(1, grid), s);
@@ -640,6 +649,21 @@ extern "C" int cbt_vertices(cbt_state* st, float* d_out, const double h_origin[3
     rc = check_launch();
     if (rc) return rc;
     return cudaStreamSynchronize(s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
+}
+
+extern "C" size_t cbt_index_workspace_bytes(uint32_t max_live) { return index_workspace_bytes(max_live); }
+
+extern "C" int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_workspace, size_t bytes,
+                         float* d_vertices, uint32_t vertices_cap, uint32_t* d_indices, uint32_t triangles_cap,
+                         uint64_t* d_heap, uint32_t* h_nvertices, uint32_t* h_ntriangles, cbt_stream_t stream) {
+    if (!st || !d_workspace || !d_indices || (d_vertices && !d_tri_vertices)) return CBT_EINVAL;
+    uint32_t n = 0;
+    int rc = cbt_live_count(st, &n, stream);
+    if (rc) return rc;
+    if (h_ntriangles) *h_ntriangles = n;
+    if (n > triangles_cap) return CBT_ENOMEM;
+    return launch_index(st->inst, st->corner, n, d_workspace, bytes, d_tri_vertices, d_vertices, vertices_cap,
+                        d_indices, d_heap, st->sms, reinterpret_cast<cudaStream_t>(stream), h_nvertices);
 }
 
 extern "C" int cbt_cbt(cbt_state* st, uint32_t* d_bitfield, uint32_t* d_sums, cbt_stream_t stream) {

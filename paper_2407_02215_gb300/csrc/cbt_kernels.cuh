@@ -19,6 +19,11 @@ void launch_free(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_fill(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_cbt(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_vertices(const BatchDev& bt, int grid, cudaStream_t s);
+// Indexed export (cbt_index.cu).
+size_t index_workspace_bytes(uint32_t max_live);
+int launch_index(const Inst& I, const uint32_t* corner, uint32_t N, void* workspace, size_t bytes,
+                 const float* tri, float* verts, uint32_t vcap, uint32_t* idx, uint64_t* ids, int sms,
+                 cudaStream_t s, uint32_t* h_nvert);
 // The one-launch frame (cbt_fused.cu): blocks of it resident per SM, and its
 // cooperative launch over `grid` blocks.
 int frame_blocks_per_sm();
