@@ -200,45 +200,54 @@ __device__ __forceinline__ void tile_begin(const BatchDev& bt, const uint32_t* b
 }
 
 
-// Entry le of instance I's camera-relative root table: the frame's eye
+// Entry le of an instance's camera-relative root table: the frame's eye
 // subtracted in FP64, then rounded to the frame's precision (FP32, fixed
 // point at 2^shift, or FP64; the sphere form keeps the absolute roots).
-__device__ __forceinline__ void rel_store(const Inst& I, const FrameP& fp, uint32_t le) {
-    const double diff = __dsub_rn(I.root64[le], fp.eye[le % 3u]);
-    if (fp.precision == 1) {
-        const double sc = __dmul_rn(diff, pow2d(fp.shift));
+__device__ __forceinline__ void rel_store(const double* root64, void* rel, Globals* g, const double* eye,
+                                          uint32_t precision, int32_t shift, uint32_t le) {
+    const double diff = __dsub_rn(root64[le], eye[le % 3u]);
+    if (precision == 1) {
+        const double sc = __dmul_rn(diff, pow2d(shift));
         long long x = 0;
         if (fabs(sc) < 4.611686018427387904e18)
             x = __double2ll_rn(sc);
         else
-            set_err(I.g, kErrRange);
-        static_cast<long long*>(I.rel)[le] = x;
-    } else if (fp.precision == 2) {
-        static_cast<double*>(I.rel)[le] = diff;
-    } else if (fp.precision == 3) {
-        static_cast<double*>(I.rel)[le] = I.root64[le];  // absolute: the projection needs it
+            set_err(g, kErrRange);
+        static_cast<long long*>(rel)[le] = x;
+    } else if (precision == 2) {
+        static_cast<double*>(rel)[le] = diff;
+    } else if (precision == 3) {
+        static_cast<double*>(rel)[le] = root64[le];  // absolute: the projection needs it
     } else {
-        static_cast<float*>(I.rel)[le] = __double2float_rn(diff);
+        static_cast<float*>(rel)[le] = __double2float_rn(diff);
     }
 }
 
 // Entry e of the batch's root tables (instances laid out by rel_base).
 __device__ __forceinline__ void rel_entry(const BatchDev& bt, uint32_t e) {
     const uint32_t b = find_inst(bt.rel_base, bt.B, e);
-    rel_store(bt.inst[b], frame_of(bt, b), e - bt.rel_base[b]);
+    const Inst& I = bt.inst[b];
+    const FrameP& fp = frame_of(bt, b);
+    rel_store(I.root64, I.rel, I.g, fp.eye, fp.precision, fp.shift, e - bt.rel_base[b]);
 }
 
 // Entries [e, e1) of the batch's root tables, by one warp: one instance
-// lookup for the range, and the instance's descriptor and frame read once
-// per instance it crosses.
+// lookup for the range, and the fields of the instance and its frame read
+// once per instance the range crosses.
 __device__ __forceinline__ void rel_range(const BatchDev& bt, uint32_t e, uint32_t e1) {
     const uint32_t lane = threadIdx.x & 31u;
     uint32_t b = find_inst(bt.rel_base, bt.B, e);
     while (e < e1) {
         const uint32_t lo = bt.rel_base[b], hi = min(e1, bt.rel_base[b + 1]);
-        const Inst I = bt.inst[b];
-        const FrameP fp = frame_of(bt, b);
-        for (uint32_t x = e + lane; x < hi; x += 32u) rel_store(I, fp, x - lo);
+        const Inst& I = bt.inst[b];
+        const FrameP& fp = frame_of(bt, b);
+        const double* root64 = I.root64;
+        void* rel = I.rel;
+        Globals* g = I.g;
+        const double eye[3] = {fp.eye[0], fp.eye[1], fp.eye[2]};
+        const uint32_t precision = fp.precision;
+        const int32_t shift = fp.shift;
+        for (uint32_t x = e + lane; x < hi; x += 32u) rel_store(root64, rel, g, eye, precision, shift, x - lo);
         e = max(e, hi);
         ++b;
     }
