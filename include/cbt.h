@@ -198,6 +198,25 @@ int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_
  * Asynchronous. */
 int cbt_update(cbt_state* st, const cbt_frame* frame, cbt_stream_t stream);
 
+/* Device address of page-locked, mapped host memory (cudaHostAlloc'd or
+ * registered; every pinned allocation is mapped under unified addressing),
+ * for outputs that kernels write straight into host memory: e.g.
+ * cbt_frame.vertices_out, so that the frame's vertex export lands in the
+ * host buffer with no separate copy. CBT_EINVAL for other pointers. */
+int cbt_host_device_pointer(void* h_ptr, void** d_ptr);
+
+/* The frame's vertex export, moved to the host in one call: rows [0, N) of
+ * d_vertices (float[N][3][3], as cbt_update's vertices_out wrote them for
+ * the current live list; N = the live count, read on the device) are
+ * copied into h_vertices by a kernel with 16-byte stores through the mapped
+ * address of the pinned buffer, and N is stored at *h_count (also pinned),
+ * so that one stream synchronisation covers the frame, the count and the
+ * copy. At most cap rows are copied; CBT_ENOMEM when N > cap (*h_count
+ * still holds N). CBT_EINVAL for NULL or unpinned host pointers.
+ * Synchronous. */
+int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, float* h_vertices, uint32_t cap,
+                         uint32_t* h_count, cbt_stream_t stream);
+
 /* Indexed export of the live bisectors, the input of a visibility buffer
  * (the paper exports its triangulation into one, Sec. 4). Corners that are
  * the same point of the subdivided surface share one vertex: a corner's

@@ -46,6 +46,8 @@ def load(path: str | None = None):
     lib.cbt_live_count.argtypes = [P, C.POINTER(U32), P]
     lib.cbt_leaves.argtypes = [P, P, P, P, U32, C.POINTER(U32), P]
     lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
+    lib.cbt_host_device_pointer.argtypes = [P, C.POINTER(P)]
+    lib.cbt_vertices_to_host.argtypes = [P, P, P, U32, P, P]
     lib.cbt_index_workspace_bytes.argtypes = [U32]
     lib.cbt_index_workspace_bytes.restype = C.c_size_t
     lib.cbt_index.argtypes = [P, P, P, C.c_size_t, P, U32, P, U32, P, C.POINTER(U32), C.POINTER(U32), P]
@@ -182,13 +184,28 @@ def workspace_bytes(H: int, D: int) -> int:
     return int(load().cbt_workspace_bytes(H, D))
 
 
+def device_address(t) -> int:
+    """Address a kernel writes `t` at: its own for a device tensor, the
+    mapped device alias for a pinned host tensor (cbt_host_device_pointer)."""
+    if t.device.type == "cuda":
+        return t.data_ptr()
+    if not t.is_pinned():
+        raise CBTError(1, "host outputs must be pinned (page-locked) tensors")
+    d = C.c_void_p()
+    rc = load().cbt_host_device_pointer(C.c_void_p(t.data_ptr()), C.byref(d))
+    if rc:
+        raise CBTError(rc, "cbt_host_device_pointer")
+    return int(d.value)
+
+
 def frame_struct(fp, device, vertices_out=None) -> tuple:
     """Packs a frame-parameter object (fields as in cbt_frame) into the C
     struct; LIST-mode heap IDs are uploaded to the device; vertices_out is an
-    optional float32 [rows, 3, 3] device tensor for the fused export."""
+    optional float32 [rows, 3, 3] tensor for the frame's vertex export, on
+    the device or pinned in host memory (written there directly)."""
     f = Frame()
     if vertices_out is not None:
-        f.vertices_out = vertices_out.data_ptr()
+        f.vertices_out = device_address(vertices_out)
         f.vertices_cap = int(vertices_out.shape[0])
     for i in range(3):
         f.eye[i] = float(fp.eye[i])
@@ -329,6 +346,16 @@ class CBT:
         if rc:
             raise CBTError(rc, "cbt_vertices")
         return out[:int(cnt.value)]
+
+    def vertices_to_host(self, d_vertices, h_vertices, h_count, stream=None) -> int:
+        """Copies the frame's exported vertices (device [N, 3, 3]) into the
+        pinned host tensor h_vertices with one synchronisation; h_count is a
+        pinned int32 tensor of one element. Returns N."""
+        rc = _lib.cbt_vertices_to_host(self._h, _t_ptr(d_vertices), _t_ptr(h_vertices), int(h_vertices.shape[0]),
+                                       _t_ptr(h_count), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_vertices_to_host")
+        return int(h_count[0])
 
     def index_workspace(self, max_live: int):
         """Device scratch for index() with up to max_live live bisectors."""

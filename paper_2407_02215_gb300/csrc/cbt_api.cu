@@ -651,6 +651,30 @@ extern "C" int cbt_vertices(cbt_state* st, float* d_out, const double h_origin[3
     return cudaStreamSynchronize(s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
 }
 
+extern "C" int cbt_host_device_pointer(void* h_ptr, void** d_ptr) {
+    if (!h_ptr || !d_ptr) return CBT_EINVAL;
+    *d_ptr = nullptr;
+    if (cudaHostGetDevicePointer(d_ptr, h_ptr, 0) != cudaSuccess) {
+        cudaGetLastError();  // not page-locked and mapped: clear the error
+        return CBT_EINVAL;
+    }
+    return CBT_OK;
+}
+
+extern "C" int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, float* h_vertices, uint32_t cap,
+                                    uint32_t* h_count, cbt_stream_t stream) {
+    if (!st || !d_vertices || !h_vertices || !h_count) return CBT_EINVAL;
+    void* dv = nullptr;
+    void* dc = nullptr;
+    if (cbt_host_device_pointer(h_vertices, &dv) || cbt_host_device_pointer(h_count, &dc)) return CBT_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rc = launch_rows_to_host(st->inst.sums + 1, d_vertices, static_cast<float*>(dv), cap,
+                                       static_cast<uint32_t*>(dc), st->sms, s);
+    if (rc) return rc;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CBT_ECUDA;
+    return *h_count > cap ? CBT_ENOMEM : CBT_OK;
+}
+
 extern "C" size_t cbt_index_workspace_bytes(uint32_t max_live) { return index_workspace_bytes(max_live); }
 
 extern "C" int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_workspace, size_t bytes,

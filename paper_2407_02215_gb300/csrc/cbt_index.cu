@@ -253,7 +253,33 @@ size_t carve(uint32_t n, char* base, IndexWs* ws) {
     return off;
 }
 
+// Rows [0, n) of 36-byte vertex records into mapped host memory, n = the
+// live count read on the device (capped at cap rows): 16-byte vector loads
+// and stores over the grid (aligned pointers), the tail words by block 0;
+// thread 0 of block 0 also stores the live count at h_count.
+__global__ void __launch_bounds__(kIThreads) k_rows_to_host(const uint32_t* count, const float* src, float* dst,
+                                                            uint32_t cap, uint32_t* h_count, bool vec) {
+    const uint32_t total = __ldg(count), n = min(total, cap);
+    const size_t words = 9ull * n;
+    const size_t q = vec ? words / 4u : 0u;
+    const size_t stride = (size_t)gridDim.x * kIThreads;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    for (size_t k = (size_t)blockIdx.x * kIThreads + threadIdx.x; k < q; k += stride) d4[k] = __ldcs(s4 + k);
+    if (blockIdx.x == 0) {
+        for (size_t k = 4u * q + threadIdx.x; k < words; k += kIThreads) dst[k] = src[k];
+        if (threadIdx.x == 0) *h_count = total;
+    }
+}
+
 }  // namespace
+
+int launch_rows_to_host(const uint32_t* count, const float* src, float* dst, uint32_t cap, uint32_t* h_count,
+                        int sms, cudaStream_t s) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0u;
+    k_rows_to_host<<<static_cast<unsigned>(sms) * 4u, kIThreads, 0, s>>>(count, src, dst, cap, h_count, vec);
+    return cudaGetLastError() == cudaSuccess ? CBT_OK : CBT_ECUDA;
+}
 
 size_t index_workspace_bytes(uint32_t n) { return carve(n, nullptr, nullptr); }
 

@@ -19,6 +19,9 @@ void launch_free(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_fill(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_cbt(const BatchDev& bt, int grid, cudaStream_t s);
 void launch_vertices(const BatchDev& bt, int grid, cudaStream_t s);
+// Vertex rows into mapped host memory (cbt_index.cu).
+int launch_rows_to_host(const uint32_t* count, const float* src, float* dst, uint32_t cap, uint32_t* h_count,
+                        int sms, cudaStream_t s);
 // Indexed export (cbt_index.cu).
 size_t index_workspace_bytes(uint32_t max_live);
 int launch_index(const Inst& I, const uint32_t* corner, uint32_t N, void* workspace, size_t bytes,
