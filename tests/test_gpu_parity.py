@@ -121,3 +121,37 @@ def test_vertices_bit_exact(CBT, prec):
     vo = o.vertices(eye, prec, 20)
     assert vg.shape == vo.shape
     assert np.array_equal(vg.view(np.uint32), vo.view(np.uint32))
+
+
+def test_single_triangle_all_border(CBT):
+    """The smallest mesh: one triangle (3 halfedges, every edge on the
+    border, so every chain ends at a null twin), split, merged and randomly
+    requested on pools of 2^3 and 2^10."""
+    m = W.meshes._mesh("triangle", [[0, 1, 2]], [(0, 0, 0), (1, 0, 0), (0.2, 0.9, 0)])
+    frames = ([forced_params(MODE_FORCE_SPLIT)] * 6 + [forced_params(MODE_FORCE_MERGE)] * 7 +
+              [forced_params(MODE_RANDOM, seed=5)] * 30)
+    for D in (3, 10):
+        run_pair(m, D, 12, frames, CBT, Oracle)
+
+
+def test_deepest_heap_ids(CBT):
+    """The longest heap IDs the index width allows (Sec. 3.3: ceil(log2 H) +
+    1 + max depth <= 63): the cube (H = 24) with max depth 57, refined under a
+    2-degree view descending to 1e-11 above a face in the FP64 form, reaches
+    depth 57 (63-bit heap IDs) with the oracle's states every 10 frames, and
+    the FP64-form vertices of the deepest bisectors are bit-identical."""
+    from workloads.cameras import Camera, frame_params
+    target = np.array([0.1037, 0.2981, 0.5])
+    frames = []
+    for k in range(70):
+        alt = np.exp(np.log(2.0) + (np.log(1e-11) - np.log(2.0)) * k / 69)
+        cam = Camera(eye=target + np.array([0, 0, alt]), target=target, up=np.array([0.0, 1.0, 0.0]),
+                     fovy_rad=np.radians(2.0), aspect=1.0)
+        frames.append(frame_params(cam, 14.0, precision=PREC_FP64))
+    g, o = run_pair(W.meshes.cube_mesh(), 16, 57, frames, CBT, Oracle, check_every=10)
+    heap = o.leaves()[1]
+    assert max(int(j).bit_length() for j in heap) == 63
+    eye = frames[-1].eye
+    vg = g.vertices(eye, PREC_FP64, 20).cpu().numpy()
+    vo = o.vertices(eye, PREC_FP64, 20)
+    assert np.array_equal(vg.view(np.uint32), vo.view(np.uint32))
