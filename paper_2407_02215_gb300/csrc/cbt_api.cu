@@ -31,6 +31,7 @@ constexpr uint32_t kLaunchesPerStep[kNumKernels] = {1, 1, 1, 1, 1, 1, 1, 1, 2, 1
 const char* const kPhaseNames[kFramePhases] = {"prep",  "classify", "gate_sum", "gate",    "alloc_sum",
                                                "alloc", "fill",     "reduce",   "compact", "vertices"};
 constexpr uint32_t kFusedTileWords = 64;
+constexpr uint32_t kFusedMaxTileWords = 128;
 
 size_t align256(size_t x) { return (x + 255u) & ~static_cast<size_t>(255u); }
 
@@ -209,6 +210,18 @@ namespace {
 const uint32_t kTuneTw[3] = {64, 128, 256};
 const uint32_t kTuneMult[3] = {4, 8, 16};
 
+// Word tile of the one-launch frame: 64 words, unless the batch's bitfields
+// make more than four tiles per resident block, where each tile's setup
+// (instance lookup, block synchronisations) would dominate: then 128, the
+// most its compaction can stage (32 positions per word in a 4096-word
+// shared buffer).
+uint32_t fused_tile_words(const cbt_batch* B) {
+    uint64_t tiles = 0;
+    for (uint32_t b = 0; b < B->n; ++b) tiles += word_tiles(B->W[b], kFusedTileWords);
+    const uint64_t grid = static_cast<uint64_t>(B->sms) * static_cast<uint64_t>(frame_blocks_per_sm());
+    return tiles > 4u * grid ? kFusedMaxTileWords : kFusedTileWords;
+}
+
 int upload_static_prefixes(cbt_batch* B, cudaStream_t s) {
     std::vector<uint32_t> w(B->n + 1), v(B->n + 1), r(B->n + 1);
     w[0] = v[0] = r[0] = 0;
@@ -262,6 +275,7 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
         cudaMallocHost(reinterpret_cast<void**>(&B->h_fps), sizeof(FrameP) * n) ||
         cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming))
         rc = CBT_ECUDA;
+    B->tw = fused_tile_words(B);  // the one-launch frame is the default form
     if (!rc) rc = upload_static_prefixes(B, s);
     if (!rc) {
         const int per_sm = frame_blocks_per_sm();
@@ -368,8 +382,9 @@ int set_fused(cbt_batch* B, bool on, cudaStream_t s) {
         B->fused = false;
         return CBT_OK;
     }
-    if (B->tw != kFusedTileWords) {
-        B->tw = kFusedTileWords;
+    const uint32_t tw = fused_tile_words(B);
+    if (B->tw != tw) {
+        B->tw = tw;
         const int rc = upload_static_prefixes(B, s);
         if (rc) return rc;
     }

@@ -812,6 +812,10 @@ __device__ void phase_compact(const BatchDev& bt, FCtx& c, const uint32_t* s_tab
         const uint32_t W = I.W;
         const uint32_t TW = min(W, bt.tw);
         const uint32_t nt = W / TW;
+        if (32u * TW > kFBuf) {  // block-uniform: a tile's positions must fit the staging buffer
+            if (threadIdx.x == 0) set_err(I.g, kErrOverflow);
+            continue;
+        }
         uint32_t before = 0;
         for (uint32_t n = nt + lt; n > 1; n >>= 1)
             if (n & 1u) before += __ldcg(I.sums + n - 1);
