@@ -22,6 +22,8 @@
 //                    kVcValid), copied by the vertex export
 //   root64[H*9], rel[H*9]: root vertices (FP64) and their per-frame offsets
 //                    from the camera (FP32, fixed point or FP64)
+//   corner[H*3] u32  global points of the root corners (mesh vertex ids, and
+//                    V + face id for the face centroid), for the indexed export
 // and, per batch (a single instance carries a batch of one), the instance
 // table, per-instance frame parameters, tile prefixes and the look-back
 // tile descriptors of the two scans and the reduction.
