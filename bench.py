@@ -67,7 +67,7 @@ STEP_KERNELS = ("prep", "classify", "walk", "gate", "scatter", "alloc", "free", 
 # + dram__bytes_write, L2 flushed before each pass), per live bisector at
 # frame start, valid only for the kernel sources it was taken on
 # (profiles/grid_flythrough_k_frame.md has the capture and its command).
-FRAME_TRAFFIC = {"sources_sha256_16": "0d1855a923ab9fd0", "bytes_per_live": 91.3,
+FRAME_TRAFFIC = {"sources_sha256_16": "edc1879fdc396781", "bytes_per_live": 91.3,
                  "capture": "frames 7 and 8 of the flythrough: 60.5 MB at 659,164 live, "
                             "64.7 MB at 712,190 live"}
 FRAME_SOURCES = ("cbt_fused.cu", "cbt_phases.cuh", "cbt_device.cuh")
