@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(1024) k_sum_small(const uint32_t* __restrict__
 // its node's path, one level per lane), its 4 rows of 32 words are loaded at
 // once, and each row is compacted: every lane writes the
 // positions of its word's set bits into the warp's staging row at its scan
-// offset, and the warp copies the row out with coalesced stores. Positions at
+// offset (two set bits per loop step), and the warp copies the row out with
+// coalesced stores. Positions at
 // index >= cap are dropped.
 constexpr int kStage = 32 * 32;  // positions of 32 words, at most
 constexpr uint32_t kSegLog = 7;
@@ -165,13 +166,23 @@ __global__ void __launch_bounds__(kRThreads) k_compact_segments(const uint32_t* 
             }
             const uint32_t tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
             uint32_t k = inc - p;
-            while (m) {
-                stage[k++] = w * 32u + (uint32_t)(__ffs(m) - 1);
+            const uint32_t wb = w * 32u;
+            while (m) {  // two set bits per step
+                stage[k] = wb + (uint32_t)(__ffs(m) - 1);
                 m &= m - 1u;
+                if (m) {
+                    stage[k + 1u] = wb + (uint32_t)(__ffs(m) - 1);
+                    m &= m - 1u;
+                }
+                k += 2u;
             }
             __syncwarp();
-            for (uint32_t q = (uint32_t)lane; q < tot; q += 32u)
-                if (base + q < cap) __stcs(live + base + q, stage[q]);
+            if (base + tot <= cap) {  // warp-uniform
+                for (uint32_t q = (uint32_t)lane; q < tot; q += 32u) __stcs(live + base + q, stage[q]);
+            } else {
+                for (uint32_t q = (uint32_t)lane; q < tot; q += 32u)
+                    if (base + q < cap) __stcs(live + base + q, stage[q]);
+            }
             __syncwarp();
             base += tot;
         }
