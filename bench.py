@@ -713,16 +713,20 @@ def bench_index(args):
     spec = W.configs.config2()
     g = CBT(spec.mesh, spec.D, spec.max_depth)
     vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device="cuda")
-    ws = g.index_workspace(1 << spec.D)
+    cap = 1 << spec.D
+    ws = g.index_workspace(cap)
+    out = (torch.empty((3 * cap, 3), dtype=torch.float32, device="cuda"),
+           torch.empty((cap, 3), dtype=torch.int32, device="cuda"), torch.empty(cap, dtype=torch.int64, device="cuda"))
     ms, tris, verts = [], [], []
     for k, fp in enumerate(spec.frames):
         g.update(fp, vertices_out=vbuf)
-        n = g.live_count()
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        v, idx, _ = g.index(vbuf[:n], workspace=ws)
+        v, idx, _ = g.index(vbuf, workspace=ws, out=out)
         b.record()
         torch.cuda.synchronize()
+        n = idx.shape[0]
         if k >= max(args.warmup, 3):
             ms.append(a.elapsed_time(b))
             tris.append(n)

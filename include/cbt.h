@@ -228,14 +228,16 @@ int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, float* h_vertic
  *   d_tri_vertices: DEVICE float[N][3][3], the per-bisector vertices of the
  *           current live list (cbt_update's vertices_out or cbt_vertices);
  *           may be NULL when d_vertices is NULL;
- *   d_workspace: DEVICE scratch of cbt_index_workspace_bytes(N) bytes at
- *           least, caller-owned, 256-byte aligned;
+ *   d_workspace: DEVICE scratch of cbt_index_workspace_bytes(triangles_cap)
+ *           bytes at least, caller-owned, 256-byte aligned;
  *   d_vertices: DEVICE float[vertices_cap][3] or NULL: each vertex's
  *           position, copied from its first occurrence;
  *   d_indices: DEVICE u32[triangles_cap][3];
  *   d_heap: DEVICE u64[triangles_cap] or NULL: the triangles' heap IDs (the
  *           visibility buffer's triangle payload);
  *   *h_nvertices / *h_ntriangles receive the counts (either may be NULL).
+ * The live count N is read on the device: the launches are sized for
+ * triangles_cap and the call synchronises once, at the end.
  * Errors: CBT_EINVAL (NULL state, workspace or indices; vertices without
  * d_tri_vertices), CBT_ENOMEM (N > triangles_cap, workspace too small, or
  * more vertices than vertices_cap: the counts are still returned),

@@ -361,21 +361,27 @@ class CBT:
         """Device scratch for index() with up to max_live live bisectors."""
         return torch.empty(int(_lib.cbt_index_workspace_bytes(int(max_live))), dtype=torch.uint8, device=self.device)
 
-    def index(self, tri_vertices=None, workspace=None, stream=None):
+    def index(self, tri_vertices=None, workspace=None, out=None, stream=None):
         """Indexed export (cbt_index): (vertices [nv, 3] or None, indices
         [N, 3] int32, heap IDs [N] int64). tri_vertices: the per-bisector
-        vertices [N, 3, 3] of the current live list."""
-        n = self.live_count(stream)
+        vertices [N, 3, 3] of the current live list. out: optional reusable
+        buffers (vertices [rows, 3] or None, indices [cap, 3], heap IDs
+        [cap]); the workspace must cover their capacity. One synchronisation."""
+        if out is None:
+            cap = self.cap
+            verts = (torch.empty((3 * cap, 3), dtype=torch.float32, device=self.device)
+                     if tri_vertices is not None else None)
+            idx = torch.empty((cap, 3), dtype=torch.int32, device=self.device)
+            heap = torch.empty(cap, dtype=torch.int64, device=self.device)
+        else:
+            verts, idx, heap = out
+            cap = idx.shape[0]
         if workspace is None:
-            workspace = self.index_workspace(n)
-        m = max(n, 1)
-        idx = torch.empty((m, 3), dtype=torch.int32, device=self.device)
-        heap = torch.empty(m, dtype=torch.int64, device=self.device)
-        verts = torch.empty((3 * m, 3), dtype=torch.float32, device=self.device) if tri_vertices is not None else None
+            workspace = self.index_workspace(cap)
         nv, nt = C.c_uint32(), C.c_uint32()
         rc = _lib.cbt_index(self._h, _t_ptr(tri_vertices) if tri_vertices is not None else None, _t_ptr(workspace),
                             workspace.numel(), _t_ptr(verts) if verts is not None else None,
-                            verts.shape[0] if verts is not None else 0, _t_ptr(idx), m, _t_ptr(heap),
+                            verts.shape[0] if verts is not None else 0, _t_ptr(idx), cap, _t_ptr(heap),
                             C.byref(nv), C.byref(nt), _stream_ptr(stream))
         if rc:
             raise CBTError(rc, "cbt_index")

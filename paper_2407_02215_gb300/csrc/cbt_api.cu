@@ -696,13 +696,9 @@ extern "C" int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_wor
                          float* d_vertices, uint32_t vertices_cap, uint32_t* d_indices, uint32_t triangles_cap,
                          uint64_t* d_heap, uint32_t* h_nvertices, uint32_t* h_ntriangles, cbt_stream_t stream) {
     if (!st || !d_workspace || !d_indices || (d_vertices && !d_tri_vertices)) return CBT_EINVAL;
-    uint32_t n = 0;
-    int rc = cbt_live_count(st, &n, stream);
-    if (rc) return rc;
-    if (h_ntriangles) *h_ntriangles = n;
-    if (n > triangles_cap) return CBT_ENOMEM;
-    return launch_index(st->inst, st->corner, n, d_workspace, bytes, d_tri_vertices, d_vertices, vertices_cap,
-                        d_indices, d_heap, st->sms, reinterpret_cast<cudaStream_t>(stream), h_nvertices);
+    return launch_index(st->inst, st->corner, triangles_cap, d_workspace, bytes, d_tri_vertices, d_vertices,
+                        vertices_cap, d_indices, d_heap, st->sms, reinterpret_cast<cudaStream_t>(stream),
+                        h_nvertices, h_ntriangles);
 }
 
 extern "C" int cbt_cbt(cbt_state* st, uint32_t* d_bitfield, uint32_t* d_sums, cbt_stream_t stream) {

@@ -124,10 +124,23 @@ __device__ __forceinline__ void insert_corners(const Inst& I, const uint32_t* co
     }
 }
 
-__global__ void __launch_bounds__(kIThreads) k_index_insert(Inst I, const uint32_t* corner, IndexWs ws, uint32_t N) {
+// The live count N is read on the device (the CBT root); a count above the
+// capacity the workspace was carved for is reported and nothing is done.
+__device__ __forceinline__ uint32_t live_n(const Inst& I, uint32_t cap) {
+    const uint32_t n = __ldg(I.sums + 1);
+    return n <= cap ? n : 0u;
+}
+
+__global__ void __launch_bounds__(kIThreads) k_index_insert(Inst I, const uint32_t* corner, IndexWs ws,
+                                                            uint32_t cap) {
     __shared__ uint32_t s_tab[64 * 9];
     load_dec6(s_tab);
     __syncthreads();
+    const uint32_t N = live_n(I, cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ws.cnt[2] = __ldg(I.sums + 1);
+        if (ws.cnt[2] > cap) atomicOr(ws.cnt, 8u);
+    }
     for (uint32_t i = blockIdx.x * kIThreads + threadIdx.x; i < N; i += gridDim.x * kIThreads) {
         const uint64_t j = I.heap[I.live[i]];
         const int d = depth_of(j, I.ch);
@@ -143,8 +156,9 @@ __global__ void __launch_bounds__(kIThreads) k_index_insert(Inst I, const uint32
     }
 }
 
-__global__ void __launch_bounds__(kIThreads) k_index_mark(IndexWs ws, uint32_t n3) {
+__global__ void __launch_bounds__(kIThreads) k_index_mark(Inst I, IndexWs ws, uint32_t cap) {
     __shared__ uint32_t s_cnt;
+    const uint32_t n3 = 3u * live_n(I, cap);
     for (uint32_t t = blockIdx.x; t * kITile < n3; t += gridDim.x) {
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
@@ -166,8 +180,9 @@ __global__ void __launch_bounds__(kIThreads) k_index_mark(IndexWs ws, uint32_t n
     }
 }
 
-__global__ void __launch_bounds__(1024) k_index_tiles(IndexWs ws, uint32_t ntiles) {
+__global__ void __launch_bounds__(1024) k_index_tiles(Inst I, IndexWs ws, uint32_t cap) {
     __shared__ Pair s_warp[1024 / 32 + 1];
+    const uint32_t ntiles = (3u * live_n(I, cap) + kITile - 1u) / kITile;
     uint32_t run = 0;
     for (uint32_t t0 = 0; t0 < ntiles; t0 += blockDim.x) {
         const uint32_t t = t0 + threadIdx.x;
@@ -183,8 +198,9 @@ __global__ void __launch_bounds__(1024) k_index_tiles(IndexWs ws, uint32_t ntile
     }
 }
 
-__global__ void __launch_bounds__(kIThreads) k_index_ids(IndexWs ws, uint32_t n3) {
+__global__ void __launch_bounds__(kIThreads) k_index_ids(Inst I, IndexWs ws, uint32_t cap) {
     __shared__ Pair s_warp[kIThreads / 32 + 1];
+    const uint32_t n3 = 3u * live_n(I, cap);
     constexpr uint32_t kPer = kITile / kIThreads;
     for (uint32_t t = blockIdx.x; t * kITile < n3; t += gridDim.x) {
         // thread k holds occurrences t kITile + k kPer .. + kPer - 1
@@ -203,9 +219,10 @@ __global__ void __launch_bounds__(kIThreads) k_index_ids(IndexWs ws, uint32_t n3
     }
 }
 
-__global__ void __launch_bounds__(kIThreads) k_index_write(Inst I, IndexWs ws, uint32_t N, const float* tri,
+__global__ void __launch_bounds__(kIThreads) k_index_write(Inst I, IndexWs ws, uint32_t cap, const float* tri,
                                                            float* verts, uint32_t vcap, uint32_t* idx,
                                                            uint64_t* ids) {
+    const uint32_t N = live_n(I, cap);
     for (uint32_t i = blockIdx.x * kIThreads + threadIdx.x; i < N; i += gridDim.x * kIThreads) {
 #pragma unroll
         for (uint32_t v = 0; v < 3; ++v) {
@@ -283,32 +300,33 @@ int launch_rows_to_host(const uint32_t* count, const float* src, float* dst, uin
 
 size_t index_workspace_bytes(uint32_t n) { return carve(n, nullptr, nullptr); }
 
-int launch_index(const Inst& I, const uint32_t* corner, uint32_t N, void* workspace, size_t bytes,
+int launch_index(const Inst& I, const uint32_t* corner, uint32_t cap, void* workspace, size_t bytes,
                  const float* tri, float* verts, uint32_t vcap, uint32_t* idx, uint64_t* ids, int sms,
-                 cudaStream_t s, uint32_t* h_nvert) {
+                 cudaStream_t s, uint32_t* h_nvert, uint32_t* h_ntri) {
     IndexWs ws;
-    if (carve(N, static_cast<char*>(workspace), &ws) > bytes) return CBT_ENOMEM;
-    const uint32_t n3 = 3u * N, ntiles = (n3 + kITile - 1u) / kITile;
+    if (carve(cap, static_cast<char*>(workspace), &ws) > bytes) return CBT_ENOMEM;
+    const uint32_t n3 = 3u * cap, ntiles = (n3 + kITile - 1u) / kITile;
     if (cudaMemsetAsync(ws.tag, 0, 8ull * ws.T, s) != cudaSuccess ||
         cudaMemsetAsync(ws.rep, 0xFF, 4ull * ws.T, s) != cudaSuccess ||
         cudaMemsetAsync(ws.cnt, 0, 16u, s) != cudaSuccess)
         return CBT_ECUDA;
-    const uint32_t cap = static_cast<uint32_t>(sms) * 8u;
-    auto grid = [&](uint32_t work) { return work == 0 ? 1u : (work < cap ? work : cap); };
-    if (N) {
-        k_index_insert<<<grid((N + kIThreads - 1u) / kIThreads), kIThreads, 0, s>>>(I, corner, ws, N);
-        k_index_mark<<<grid(ntiles), kIThreads, 0, s>>>(ws, n3);
-        k_index_tiles<<<1, 1024, 0, s>>>(ws, ntiles);
-        k_index_ids<<<grid(ntiles), kIThreads, 0, s>>>(ws, n3);
-        k_index_write<<<grid((N + kIThreads - 1u) / kIThreads), kIThreads, 0, s>>>(I, ws, N, tri, verts, vcap,
-                                                                                  idx, ids);
-    }
+    const uint32_t most = static_cast<uint32_t>(sms) * 8u;
+    auto grid = [&](uint32_t work) { return work == 0 ? 1u : (work < most ? work : most); };
+    // sized for the capacity; every kernel reads the live count on the device
+    k_index_insert<<<grid((cap + kIThreads - 1u) / kIThreads), kIThreads, 0, s>>>(I, corner, ws, cap);
+    k_index_mark<<<grid(ntiles), kIThreads, 0, s>>>(I, ws, cap);
+    k_index_tiles<<<1, 1024, 0, s>>>(I, ws, cap);
+    k_index_ids<<<grid(ntiles), kIThreads, 0, s>>>(I, ws, cap);
+    k_index_write<<<grid((cap + kIThreads - 1u) / kIThreads), kIThreads, 0, s>>>(I, ws, cap, tri, verts, vcap,
+                                                                                 idx, ids);
     if (cudaGetLastError() != cudaSuccess) return CBT_ECUDA;
     uint32_t cnt[4] = {0, 0, 0, 0};
     if (cudaMemcpyAsync(cnt, ws.cnt, 16u, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return CBT_ECUDA;
     if (h_nvert) *h_nvert = cnt[1];
+    if (h_ntri) *h_ntri = cnt[2];
+    if (cnt[0] & 8u) return CBT_ENOMEM;  // more live bisectors than the capacity
     if (cnt[0]) return CBT_EDEVICE;
     if (cnt[1] > vcap && verts) return CBT_ENOMEM;
     return CBT_OK;
