@@ -293,9 +293,20 @@ static __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
         g.n = 4;
         g.np = 2;
     }
+    // the member with the smallest heap ID, by selects (the first of equal ones)
+    uint64_t jm = g.j[0];
     g.imin = 0;
-    for (int k = 1; k < g.n; ++k)
-        if (g.j[k] < g.j[g.imin]) g.imin = k;
+    if (g.j[1] < jm) {
+        jm = g.j[1];
+        g.imin = 1;
+    }
+    if (g.n == 4) {
+        if (g.j[2] < jm) {
+            jm = g.j[2];
+            g.imin = 2;
+        }
+        if (g.j[3] < jm) g.imin = 3;
+    }
     return true;
 }
 
@@ -559,7 +570,7 @@ struct FamDesc {
 
 #define INT_(a, b) {0, a, b}
 #define EXT_(a, b) {1, a, b}
-__constant__ FamDesc c_fam[4] = {
+constexpr FamDesc kFam[4] = {
     // R: 2j, 2j+1
     {2, {1, 1, 0, 0}, {0, 1, 0, 0},
      {{EXT_(kPe, kWhole), INT_(1, kPe), EXT_(kT, kFirst)},
@@ -587,6 +598,45 @@ __constant__ FamDesc c_fam[4] = {
 #undef INT_
 #undef EXT_
 
+// The family tables packed into immediates, so that a lane reads its case
+// from registers instead of a constant-memory table indexed differently by
+// every lane: per case, the 12 edge descriptors as 5-bit codes (ext << 4 |
+// a << 2 | b) at bit 5 (3 l + e); the leaf count and the per-leaf heap-ID
+// shift and offset (n | shift[l] << (3 + 2 l) | off[l] << (11 + 2 l)); and
+// the inverse map, old edge E and portion p to (leaf, edge) as 5-bit codes
+// (valid << 4 | leaf << 2 | edge) at bit 5 (3 E + p).
+constexpr uint64_t fam_edges(int c) {
+    uint64_t w = 0;
+    for (int l = 0; l < 4; ++l)
+        for (int e = 0; e < 3; ++e) {
+            const EdgeDesc d = kFam[c].e[l][e];
+            w |= (uint64_t)((d.ext << 4) | (d.a << 2) | d.b) << (5 * (3 * l + e));
+        }
+    return w;
+}
+constexpr uint32_t fam_misc(int c) {
+    uint32_t w = kFam[c].n;
+    for (int l = 0; l < 4; ++l) w |= (uint32_t)kFam[c].shift[l] << (3 + 2 * l) | (uint32_t)kFam[c].off[l] << (11 + 2 * l);
+    return w;
+}
+constexpr uint64_t fam_leafof(int c) {
+    uint64_t w = 0;
+    for (int l = 0; l < kFam[c].n; ++l)
+        for (int e = 0; e < 3; ++e) {
+            const EdgeDesc d = kFam[c].e[l][e];
+            if (d.ext) w |= (uint64_t)(16 | (l << 2) | e) << (5 * (3 * d.a + d.b));
+        }
+    return w;
+}
+constexpr uint64_t kFamE0 = fam_edges(0), kFamE1 = fam_edges(1), kFamE2 = fam_edges(2), kFamE3 = fam_edges(3);
+constexpr uint32_t kFamM0 = fam_misc(0), kFamM1 = fam_misc(1), kFamM2 = fam_misc(2), kFamM3 = fam_misc(3);
+constexpr uint64_t kFamL0 = fam_leafof(0), kFamL1 = fam_leafof(1), kFamL2 = fam_leafof(2), kFamL3 = fam_leafof(3);
+
+template <typename T>
+__device__ __forceinline__ T pick_case(int c, T v0, T v1, T v2, T v3) {
+    return c == 0 ? v0 : (c == 1 ? v1 : (c == 2 ? v2 : v3));
+}
+
 __device__ __forceinline__ int fam_case(uint32_t sb) { return (int)((sb >> 1) & 3u); }
 
 // Does a family with split bits sb cover old edge E by halves?
@@ -596,15 +646,11 @@ __device__ __forceinline__ bool halves(uint32_t sb, int E) {
 
 // Leaf of family `sb` covering portion p of old edge Ep, and that leaf's edge.
 __device__ __forceinline__ bool family_leaf(uint32_t sb, int Ep, int p, uint32_t& leaf, uint32_t& edge) {
-    const FamDesc& f = c_fam[fam_case(sb)];
-    for (int l = 0; l < f.n; ++l)
-        for (int e = 0; e < 3; ++e)
-            if (f.e[l][e].ext && f.e[l][e].a == Ep && f.e[l][e].b == p) {
-                leaf = (uint32_t)l;
-                edge = (uint32_t)e;
-                return true;
-            }
-    return false;
+    const uint32_t code =
+        (uint32_t)(pick_case(fam_case(sb), kFamL0, kFamL1, kFamL2, kFamL3) >> (5 * (3 * Ep + p))) & 31u;
+    leaf = (code >> 2) & 3u;
+    edge = code & 3u;
+    return (code & 16u) != 0u;
 }
 
 // What lies across the old edges of a changed bisector x on the new mesh:
@@ -651,7 +697,9 @@ static __device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, 
     }
     if (ysb) {
         const bool same = ((yc.x & kDepthOdd) != 0u) == xodd;
-        for (int h = 0; h < (hv ? 2 : 1); ++h) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // unrolled: a.slot and a.rev stay in registers
+            if (h == 1 && !hv) break;
             int p = hv ? (h == 0 ? kFirst : kSecond) : kWhole;
             if (p != kWhole && same) p = p == kFirst ? kSecond : kFirst;
             uint32_t leaf, edge;
@@ -679,16 +727,23 @@ static __device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, 
     }
 }
 
+// Element i (0..2) of three values, by selects (no indexed local array).
+__device__ __forceinline__ uint32_t sel3(uint32_t i, uint32_t v0, uint32_t v1, uint32_t v2) {
+    return i == 0u ? v0 : (i == 1u ? v1 : v2);
+}
+
 // An unchanged neighbour across old edge E of x now faces new bisector ns
 // through ns's edge ne; that neighbour link has exactly one writer, this one.
 // Returns the number of links written (0 or 1).
 __device__ __forceinline__ uint32_t push_keep(const Inst& I, const Across& a, int E, uint32_t ns, uint32_t ne) {
-    const uint32_t y = a.y[E];
-    if (y == kNull || (a.yc[E].x & (kSplitMask | kMerged))) return 0u;
+    const uint32_t e = (uint32_t)E;
+    const uint32_t y = sel3(e, a.y[0], a.y[1], a.y[2]);
+    const uint32_t ycx = sel3(e, a.yc[0].x, a.yc[1].x, a.yc[2].x);
+    if (y == kNull || (ycx & (kSplitMask | kMerged))) return 0u;
     uint32_t* yr = reinterpret_cast<uint32_t*>(I.nb + y);
-    const int Ep = (int)a.ep[E];
+    const uint32_t Ep = sel3(e, a.ep[0], a.ep[1], a.ep[2]);
     yr[Ep] = ns;
-    atomicXor(yr + 3, ((uint32_t)E ^ ne) << (2 * Ep));
+    atomicXor(yr + 3, (e ^ ne) << (2u * Ep));
     return 1u;
 }
 
@@ -702,41 +757,53 @@ __device__ __forceinline__ void clear_bit(const Inst& I, uint32_t s) {
 // Both fills return the number of unchanged neighbours relinked.
 static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t dest) {
     const uint32_t sb = cmd & kSplitMask;
-    const FamDesc& f = c_fam[fam_case(sb)];
-    if (dest + f.n > I.g->A) {
+    const int fc = fam_case(sb);
+    const uint64_t edges = pick_case(fc, kFamE0, kFamE1, kFamE2, kFamE3);
+    const uint32_t misc = pick_case(fc, kFamM0, kFamM1, kFamM2, kFamM3);
+    const uint32_t n = misc & 7u;
+    if (dest + n > I.g->A) {
         set_err(I.g, kErrOverflow);
         return 0u;
     }
     const uint64_t j = I.heap[s];
     const uint4 rx = I.nb[s];
     uint32_t slots[4];
-    for (int l = 0; l < f.n; ++l) slots[l] = I.freel[dest + (uint32_t)l];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) slots[l] = (uint32_t)l < n ? I.freel[dest + (uint32_t)l] : 0u;
     Across a;
     across_load(I, rx, a);
     const bool xodd = (cmd & kDepthOdd) != 0u;
 #pragma unroll
     for (int E = 0; E < 3; ++E) across_resolve(I, a, E, halves(sb, E), xodd);
-    for (int l = 0; l < f.n; ++l)
-        if (bad_slot(I, slots[l], kErrOverflow)) return 0u;
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+        if ((uint32_t)l < n && bad_slot(I, slots[l], kErrOverflow)) return 0u;
     uint32_t relinked = 0;
-    for (int l = 0; l < f.n; ++l) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if ((uint32_t)l >= n) break;
         uint32_t lk[3], rv = 0;
+#pragma unroll
         for (int e = 0; e < 3; ++e) {
-            const EdgeDesc ed = f.e[l][e];
+            const uint32_t code = (uint32_t)(edges >> (5 * (3 * l + e))) & 31u;
+            const uint32_t ea = (code >> 2) & 3u, eb = code & 3u;
             uint32_t r;
-            if (!ed.ext) {
-                lk[e] = slots[ed.a];
-                r = ed.b;
+            if (!(code & 16u)) {
+                lk[e] = ea == 0u ? slots[0] : (ea == 1u ? slots[1] : (ea == 2u ? slots[2] : slots[3]));
+                r = eb;
             } else {
-                const int h = ed.b == kSecond ? 1 : 0;
-                lk[e] = a.slot[ed.a][h];
-                r = a.rev[ed.a][h];
-                if (ed.b == kWhole) relinked += push_keep(I, a, ed.a, slots[l], (uint32_t)e);
+                const bool h = eb == (uint32_t)kSecond;
+                lk[e] = sel3(ea, h ? a.slot[0][1] : a.slot[0][0], h ? a.slot[1][1] : a.slot[1][0],
+                             h ? a.slot[2][1] : a.slot[2][0]);
+                r = sel3(ea, h ? a.rev[0][1] : a.rev[0][0], h ? a.rev[1][1] : a.rev[1][0],
+                         h ? a.rev[2][1] : a.rev[2][0]);
+                if (eb == (uint32_t)kWhole) relinked += push_keep(I, a, (int)ea, slots[l], (uint32_t)e);
             }
             rv |= r << (2 * e);
         }
+        const uint32_t sh = (misc >> (3 + 2 * l)) & 3u, off = (misc >> (11 + 2 * l)) & 3u;
         I.nb[slots[l]] = make_uint4(lk[0], lk[1], lk[2], rv);
-        I.heap[slots[l]] = (j << f.shift[l]) + f.off[l];
+        I.heap[slots[l]] = (j << sh) + off;
         *cmd_ptr(I, slots[l]) = 0u;  // a new record: no cached vertices
         set_bit(I, slots[l]);
     }
@@ -755,12 +822,16 @@ static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 
         return 0u;
     }
     uint32_t ps[2] = {kNull, kNull};
-    for (int k = 0; k < np; ++k) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {  // unrolled loops keep ms and ps in registers
+        if (k == np) break;
         ps[k] = I.freel[dest + (uint32_t)k];
         if (bad_slot(I, ps[k], kErrOverflow)) return 0u;
     }
     uint32_t relinked = 0;
-    for (int pk = 0; pk < np; ++pk) {
+#pragma unroll
+    for (int pk = 0; pk < 2; ++pk) {
+        if (pk == np) break;
         const uint32_t u = ms[2 * pk], v = ms[2 * pk + 1];
         if (bad_slot(I, u, kErrLink) || bad_slot(I, v, kErrLink)) return relinked;
         const uint64_t ju = I.heap[u];
