@@ -918,11 +918,25 @@ __device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_ta
         evaluate(*s_n);
         return;
     }
-    uint32_t i = blockIdx.x * kFThreads + threadIdx.x;
-    uint64_t j = i < n ? I.heap[I.live[i]] : 0ull;
-    for (; i < n; i += stride) {
+    // warp-uniform rounds of 32 consecutive rows, staged per warp in s_list
+    // (8 warps x 288 floats) and stored 16 bytes wide
+    const uint32_t lane = threadIdx.x & 31u;
+    float* stage = reinterpret_cast<float*>(s_list) + 288u * (threadIdx.x >> 5);
+    uint32_t w0 = blockIdx.x * kFThreads + (threadIdx.x & ~31u);
+    uint64_t j = w0 + lane < n ? I.heap[I.live[w0 + lane]] : 0ull;
+    for (; w0 < n; w0 += stride) {
+        const uint32_t i = w0 + lane;
         const uint64_t jn = i + stride < n ? I.heap[I.live[i + stride]] : 0ull;
-        vertex_item(I, fp, i, j, s_tab, fp.vout);
+        float r[9];
+        bool ok = true;
+        if (i < n) ok = vertex_eval(I, fp, j, s_tab, r);
+        if (__all_sync(0xFFFFFFFFu, ok)) {
+            warp_rows_out(r, stage, fp.vout, w0, min(32u, n - w0));
+        } else if (i < n && ok) {  // a row the decode refused stays unwritten
+            float* o = fp.vout + 9ull * i;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) o[k] = r[k];
+        }
         j = jn;
     }
 }

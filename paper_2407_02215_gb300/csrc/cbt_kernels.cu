@@ -640,7 +640,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_vertices(BatchDev bt) {
     __shared__ Inst s_I;
     __shared__ FrameP s_fp;
     __shared__ uint32_t s_tab[64 * 9];
+    __shared__ __align__(16) float s_stage[kThreads / 32][288];  // per warp: 32 rows of 9 floats
     load_dec6(s_tab);
+    const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t t = blockIdx.x; t < bt.Titems; t += gridDim.x) {
         uint32_t b, lt;
         tile_begin(bt, bt.vtile_base, t, &s_b, &s_I, &s_fp, nullptr, b, lt);
@@ -655,9 +657,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_vertices(BatchDev bt) {
                 hj[k] = i < N ? I.heap[I.live[i]] : 0ull;
             }
 #pragma unroll 1
-            for (int k = 0; k < kItemsPerThread; ++k) {
+            for (int k = 0; k < kItemsPerThread; ++k) {  // warp-uniform: 32 consecutive rows per warp
                 const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
-                if (i < N) vertex_item(I, fp, i, hj[k], s_tab, fp.vout);
+                const uint32_t w0 = i - lane;
+                if (w0 >= N) continue;
+                float r[9];
+                bool ok = true;
+                if (i < N) ok = vertex_eval(I, fp, hj[k], s_tab, r);
+                if (__all_sync(0xFFFFFFFFu, ok)) {
+                    warp_rows_out(r, s_stage[threadIdx.x >> 5], fp.vout, w0, min(32u, N - w0));
+                } else if (i < N && ok) {  // a row the decode refused stays unwritten
+                    float* o = fp.vout + 9ull * i;
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) o[q] = r[q];
+                }
             }
         }
         __syncthreads();

@@ -863,14 +863,15 @@ static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 
 // writes its family; the smallest member of a merge group clears its
 // members' bits and writes the parents.
 
-__device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uint32_t i, uint64_t j,
-                                            const uint32_t* tab, float* out) {
+// The three vertices of bisector j into r; false (error word set, r not
+// written) when j does not decode to a root of this mesh.
+__device__ __forceinline__ bool vertex_eval(const Inst& I, const FrameP& fp, uint64_t j, const uint32_t* tab,
+                                            float r[9]) {
     const int d = depth_of(j, I.ch);
     const uint32_t h = (uint32_t)((j >> d) - (1ull << I.ch));
-    float r[9];
     if (d < 0 || h >= I.H) {
         set_err(I.g, kErrLink);
-        return;
+        return false;
     }
     if (d <= 31) {
         uint32_t W[9], Wp[9];
@@ -881,9 +882,42 @@ __device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uin
         decode_weights<unsigned long long>(j, d, W, Wp, tab);
         eval_vertices<unsigned long long>(W, d, fp, I.rel, h, r);
     }
+    return true;
+}
+
+__device__ __forceinline__ void vertex_item(const Inst& I, const FrameP& fp, uint32_t i, uint64_t j,
+                                            const uint32_t* tab, float* out) {
+    float r[9];
+    if (!vertex_eval(I, fp, j, tab, r)) return;
     float* o = out + 9ull * i;
 #pragma unroll
     for (int k = 0; k < 9; ++k) o[k] = r[k];
+}
+
+// A warp's 32 consecutive output rows of 9 floats (rows row0 .. row0 + 31,
+// the first `valid` of them real), written through the warp's 288-float
+// staging area (16-byte aligned): lane l's row goes to stage[9 l ..] (odd
+// stride, no bank conflicts), then the warp stores the rows' words with
+// 16-byte stores when their first word is 16-byte aligned (else word by
+// word). One row of 36 bytes per lane would take nine strided stores per
+// warp.
+__device__ __forceinline__ void warp_rows_out(const float r[9], float* stage, float* out, uint64_t row0,
+                                              uint32_t valid) {
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) stage[9u * lane + (uint32_t)k] = r[k];
+    __syncwarp();
+    const uint32_t words = 9u * valid;
+    float* dst = out + 9ull * row0;
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0u) {
+        const uint32_t nv = words >> 2;
+        for (uint32_t v = lane; v < nv; v += 32u)
+            reinterpret_cast<float4*>(dst)[v] = reinterpret_cast<const float4*>(stage)[v];
+        done = nv << 2;
+    }
+    for (uint32_t w = done + lane; w < words; w += 32u) dst[w] = stage[w];
+    __syncwarp();
 }
 
 // Vertices of the live bisector in slot s at output row i: in the sphere
