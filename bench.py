@@ -28,6 +28,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -136,7 +137,8 @@ class ClockSampler:
 
     def __init__(self, device_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        out_dir = os.environ.get("CBT_BENCH_OUT", os.path.join(tempfile.gettempdir(), "cbt_bench"))
+        self.path = os.path.join(out_dir, f"clocks_rank{device_index}.csv")
         try:
             import torch
             uuid = str(torch.cuda.get_device_properties(device_index).uuid)
