@@ -893,22 +893,35 @@ __device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_ta
         };
         if (threadIdx.x == 0) *s_n = 0;
         __syncthreads();
+        // the cached rows of a warp's 32 consecutive rows leave through the
+        // warp's staging area (the list of uncached rows uses the front of
+        // s_list, the staging its back) with one coalesced store per word
+        const uint32_t lane = threadIdx.x & 31u;
+        float* stage = reinterpret_cast<float*>(s_list) + (kFBuf - 288u * (kFThreads / 32)) + 288u * (threadIdx.x >> 5);
         for (uint32_t base = blockIdx.x * kFThreads; base < n; base += stride) {
             const uint32_t i = base + threadIdx.x;
+            bool cached = false;
             if (i < n) {
                 const uint32_t s = I.live[i];
                 if (*cmd_ptr(I, s) & kVcValid) {
                     const float* src = I.vc + 9ull * s;
-                    float* o = fp.vout + 9ull * i;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) o[k] = src[k];
+                    for (int k = 0; k < 9; ++k) stage[9u * lane + (uint32_t)k] = src[k];
+                    cached = true;
                 } else {
                     s_list[atomicAdd(s_n, 1u)] = i;
                 }
             }
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, cached);
+            __syncwarp();
+            const uint32_t w0 = i - lane;
+            float* dst = fp.vout + 9ull * w0;
+            for (uint32_t w = lane; w < 288u; w += 32u)
+                if ((m >> (w / 9u)) & 1u) dst[w] = stage[w];
+            __syncwarp();
             __syncthreads();
             const uint32_t cnt = *s_n;
-            if (cnt > kFBuf - kFThreads) {  // block-uniform: make room
+            if (cnt > kFBuf - 288u * (kFThreads / 32) - kFThreads) {  // block-uniform: keep clear of the staging
                 evaluate(cnt);
                 __syncthreads();
                 if (threadIdx.x == 0) *s_n = 0;
