@@ -85,10 +85,12 @@ enum { CBT_GATE_CHAIN = 0, CBT_GATE_PAPER = 1 };
  * planes: inward normals of up to five planes through the eye, FP32.
  * q: ((viewport height / (2 tan(fovy / 2))) / threshold_px)^2 in FP32.
  * split_list / merge_list: sorted DEVICE arrays of heap IDs (LIST mode).
- * vertices_out: optional DEVICE buffer of vertices_cap * 9 floats; when set,
- * the frame ends by writing the vertices of the new live bisectors (ascending
- * slot order) relative to eye in the frame's precision, as cbt_vertices does;
- * rows beyond vertices_cap are not written (size it 2^D rows to be safe).
+ * vertices_out: optional DEVICE buffer of vertices_cap * 9 floats (4-byte
+ * aligned; 16-byte aligned lets the export store 16 bytes at a time); when
+ * set, the frame ends by writing the vertices of the new live bisectors
+ * (ascending slot order) relative to eye in the frame's precision, as
+ * cbt_vertices does; rows beyond vertices_cap are not written (size it 2^D
+ * rows to be safe).
  * sphere_radius: CBT_PREC_SPHERE only, the radius (> 0) of the sphere about
  * the world origin onto which the vertices (LOD test and export) are
  * projected.
@@ -212,7 +214,8 @@ int cbt_host_device_pointer(void* h_ptr, void** d_ptr);
  * address of the pinned buffer, and N is stored at *h_count (also pinned),
  * so that one stream synchronisation covers the frame, the count and the
  * copy. At most cap rows are copied; CBT_ENOMEM when N > cap (*h_count
- * still holds N). CBT_EINVAL for NULL or unpinned host pointers.
+ * still holds N). CBT_EINVAL for NULL, misaligned or unpinned host
+ * pointers.
  * Synchronous. */
 int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, float* h_vertices, uint32_t cap,
                          uint32_t* h_count, cbt_stream_t stream);
@@ -239,7 +242,8 @@ int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, float* h_vertic
  * The live count N is read on the device: the launches are sized for
  * triangles_cap and the call synchronises once, at the end.
  * Errors: CBT_EINVAL (NULL state, workspace or indices; vertices without
- * d_tri_vertices), CBT_ENOMEM (N > triangles_cap, workspace too small, or
+ * d_tri_vertices; a workspace not 256-byte aligned or an output not aligned
+ * to its element), CBT_ENOMEM (N > triangles_cap, workspace too small, or
  * more vertices than vertices_cap: the counts are still returned),
  * CBT_EDEVICE (two identities with one 64-bit hash: reported, never merged),
  * CBT_ECUDA. Five launches on `stream`; synchronous (returns the counts). */
@@ -454,8 +458,9 @@ int cbt_sum_reduce(const uint32_t* d_bitfield, int32_t D, uint32_t* d_sums, cbt_
  *   D: 5 <= D <= 28;
  *   d_live: DEVICE u32[cap], caller-owned; positions at index >= cap are
  *           not written (read the count from sums[1]).
- * One launch on `stream`; allocates nothing. Errors: CBT_EINVAL (NULL
- * pointer, D < 5), CBT_ECAPACITY (D > 28), CBT_ECUDA. Asynchronous. */
+ * One launch on `stream`; allocates nothing. Errors: CBT_EINVAL (NULL or
+ * misaligned pointer, D < 5), CBT_ECAPACITY (D > 28), CBT_ECUDA.
+ * Asynchronous. */
 int cbt_compact(const uint32_t* d_bitfield, const uint32_t* d_sums, int32_t D, uint32_t* d_live, uint32_t cap,
                 cbt_stream_t stream);
 

@@ -128,7 +128,7 @@ bool frame_from_api(const cbt_frame* f, uint32_t frame, FrameP& fp) {
     if (f->fixed_shift < 0 || f->fixed_shift > 62) return false;
     if (f->mode == CBT_MODE_LIST && ((f->n_split && !f->split_list) || (f->n_merge && !f->merge_list)))
         return false;
-    if (f->vertices_out && f->vertices_cap == 0) return false;
+    if (f->vertices_out && (f->vertices_cap == 0 || (reinterpret_cast<uintptr_t>(f->vertices_out) & 3u))) return false;
     if (f->disp_amplitude != 0.0f &&
         !(std::isfinite(f->disp_amplitude) && std::isfinite(f->disp_frequency) && f->disp_frequency > 0.0f &&
           f->disp_octaves >= 1u && f->disp_octaves <= 8u && (f->precision == 0u || f->precision == 3u)))
@@ -679,6 +679,9 @@ extern "C" int cbt_host_device_pointer(void* h_ptr, void** d_ptr) {
 extern "C" int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, float* h_vertices, uint32_t cap,
                                     uint32_t* h_count, cbt_stream_t stream) {
     if (!st || !d_vertices || !h_vertices || !h_count) return CBT_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_vertices) | reinterpret_cast<uintptr_t>(h_vertices) |
+         reinterpret_cast<uintptr_t>(h_count)) & 3u)
+        return CBT_EINVAL;
     void* dv = nullptr;
     void* dc = nullptr;
     if (cbt_host_device_pointer(h_vertices, &dv) || cbt_host_device_pointer(h_count, &dc)) return CBT_EINVAL;
@@ -696,6 +699,11 @@ extern "C" int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_wor
                          float* d_vertices, uint32_t vertices_cap, uint32_t* d_indices, uint32_t triangles_cap,
                          uint64_t* d_heap, uint32_t* h_nvertices, uint32_t* h_ntriangles, cbt_stream_t stream) {
     if (!st || !d_workspace || !d_indices || (d_vertices && !d_tri_vertices)) return CBT_EINVAL;
+    // the workspace holds 64-bit words and 32-byte identities; the outputs their element types
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255u) || (reinterpret_cast<uintptr_t>(d_indices) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_heap) & 7u) || (reinterpret_cast<uintptr_t>(d_vertices) & 3u) ||
+        (reinterpret_cast<uintptr_t>(d_tri_vertices) & 3u))
+        return CBT_EINVAL;
     return launch_index(st->inst, st->corner, triangles_cap, d_workspace, bytes, d_tri_vertices, d_vertices,
                         vertices_cap, d_indices, d_heap, st->sms, reinterpret_cast<cudaStream_t>(stream),
                         h_nvertices, h_ntriangles);

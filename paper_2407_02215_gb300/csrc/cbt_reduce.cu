@@ -223,6 +223,9 @@ __global__ void __launch_bounds__(32) k_compact_small(const uint32_t* __restrict
 extern "C" int cbt_compact(const uint32_t* d_bitfield, const uint32_t* d_sums, int32_t D, uint32_t* d_live,
                            uint32_t cap, cbt_stream_t stream) {
     if (!d_bitfield || !d_sums || (!d_live && cap) || D < 5) return CBT_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_bitfield) | reinterpret_cast<uintptr_t>(d_sums) |
+         reinterpret_cast<uintptr_t>(d_live)) & 3u)
+        return CBT_EINVAL;
     if (D > 28) return CBT_ECAPACITY;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const uint32_t W = 1u << (D - 5);

@@ -125,6 +125,9 @@ def test_index_errors(P):
     assert lib.cbt_index(g._h, None, p(ws.data_ptr()), ws.numel(), None, 0, p(idx.data_ptr()), 4, None,
                          ctypes.byref(nv), ctypes.byref(nt), None) == 4
     assert nt.value == 24
+    # a workspace off its 256-byte alignment
+    assert lib.cbt_index(g._h, None, p(ws.data_ptr() + 8), ws.numel() - 8, None, 0, p(idx.data_ptr()), 4, None,
+                         ctypes.byref(nv), ctypes.byref(nt), None) == 1
     # a workspace sized for fewer live bisectors
     small = g.index_workspace(2)
     big = torch.empty((24, 3), dtype=torch.int32, device="cuda")
