@@ -190,9 +190,10 @@ def measured_peaks():
 
 # -------------------------------------------------------------- CPU oracle
 
-def run_oracle(spec, frames, budget_s):
+def run_oracle(spec, frames, budget_s, lives=None):
     """Times the CPU oracle (one core) on frames until budget_s is spent;
-    returns (bisectors, seconds, frames done)."""
+    returns (bisectors, seconds, frames done); appends each frame's live
+    count after the update to `lives` when given."""
     from oracle import Oracle
     o = Oracle(spec.mesh, spec.D, spec.max_depth)
     bis, secs, done = 0, 0.0, 0
@@ -202,16 +203,25 @@ def run_oracle(spec, frames, budget_s):
         secs += time.perf_counter() - t
         bis += st["live_before"]
         done += 1
+        if lives is not None:
+            lives.append(st["live_after"])
         if secs >= budget_s:
             break
     return bis, secs, done
 
 
-def cpu_baseline(spec, frames, budget_s=15.0):
-    bis, secs, done = run_oracle(spec, frames, budget_s)
-    return {"value": bis / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} frames of the same flythrough ({bis} bisector updates, "
-                      f"{secs:.1f} s, sequential C oracle on one host core)"}
+def cpu_baseline(spec, frames, budget_s=15.0, gpu_lives=None):
+    """The oracle timed on a bounded sample of the frames; with the timed
+    GPU run's per-frame live counts, also whether they equal the oracle's
+    over that sample (the timed run doubles as a parity run)."""
+    lives = []
+    bis, secs, done = run_oracle(spec, frames, budget_s, lives)
+    out = {"value": bis / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"first {done} frames of the same flythrough ({bis} bisector updates, "
+                     f"{secs:.1f} s, sequential C oracle on one host core)"}
+    if gpu_lives is not None:
+        out["timed_run_live_counts_equal_oracle"] = list(gpu_lives[:done]) == lives
+    return out
 
 
 # -------------------------------------------------------------------- main
@@ -422,7 +432,7 @@ def bench_ours(args):
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(spec, frames, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(spec, frames, args.cpu_budget, [st["live_after"] for st in stats])
     return line
 
 
