@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
 __global__ void __launch_bounds__(kThreads) k_walk(BatchDev bt) {
     __shared__ uint32_t s_b, s_n;
     __shared__ Inst s_I;
-    __shared__ uint32_t s_list[kTileItems];
+    __shared__ uint2 s_list[kTileItems];  // {live index | split << 31, slot}
     const uint32_t T = ld_volatile(&bt.bg->total_tiles);
     for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
         uint32_t b, lt;
@@ -96,17 +96,18 @@ __global__ void __launch_bounds__(kThreads) k_walk(BatchDev bt) {
         for (int k = 0; k < kItemsPerThread; ++k) {
             const uint32_t i = lt * kTileItems + (uint32_t)k * kThreads + threadIdx.x;
             if (i >= N) continue;
-            const uint32_t cmd = *cmd_ptr(I, I.live[i]);
-            const bool need = ((cmd & kSplitWish) && chain) || ((cmd & kMergeWish) && !(cmd & kHeapOdd));
-            if (need) s_list[atomicAdd(&s_n, 1u)] = i;
+            const uint32_t s = I.live[i];
+            const uint32_t cmd = *cmd_ptr(I, s);
+            const bool split = (cmd & kSplitWish) != 0u;
+            const bool need = (split && chain) || ((cmd & kMergeWish) && !(cmd & kHeapOdd));
+            if (need) s_list[atomicAdd(&s_n, 1u)] = make_uint2(i | (split ? 0x80000000u : 0u), s);
         }
         __syncthreads();
         const uint32_t n = s_n;
         for (uint32_t q = threadIdx.x; q < n; q += kThreads) {
-            const uint32_t i = s_list[q];
-            const uint32_t s = I.live[i];
-            const uint32_t cmd = *cmd_ptr(I, s);
-            if (cmd & kSplitWish) {
+            const uint2 e = s_list[q];
+            const uint32_t i = e.x & 0x7FFFFFFFu, s = e.y;
+            if (e.x & 0x80000000u) {
                 I.scan[i] = chain_walk(I, s, depth_of(I.heap[s], I.ch), false);
             } else {
                 Group g;
