@@ -60,3 +60,50 @@ def test_host_ingest_rejects_bad_faces():
         assert e.code == 1
     else:
         raise AssertionError("expected CBT_EINVAL")
+
+
+def _c_layout(struct: str, fields):
+    """Offsets of `fields` and the size of `struct` as a C compiler lays out
+    include/cbt.h (gcc on this host)."""
+    import subprocess
+    import tempfile
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cbt.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of cbt_frame and cbt_frame_stats have the header's
+    field offsets and sizes, so frames and counters cross the ABI intact."""
+    from paper_2407_02215_gb300.cbt import Frame, Stats
+    for cls, name in ((Frame, "cbt_frame"), (Stats, "cbt_frame_stats")):
+        fields = [f for f, _ in cls._fields_]
+        size, offs = _c_layout(name, fields)
+        assert size == ctypes.sizeof(cls), name
+        assert offs == [getattr(cls, f).offset for f in fields], name
+
+
+def test_oracle_binding_structs_match_its_header():
+    """The same for the oracle's or_frame (test infrastructure)."""
+    import subprocess
+    import tempfile
+    from oracle.oracle import _Frame
+    fields = [f for f, _ in _Frame._fields_]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cbt_oracle.h"', "int main(void) {",
+             '  printf("%zu\\n", sizeof(or_frame));']
+    lines += [f'  printf("%zu\\n", offsetof(or_frame, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "oracle"), src, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).decode().split()]
+    assert out[0] == ctypes.sizeof(_Frame)
+    assert out[1:] == [getattr(_Frame, f).offset for f in fields]
