@@ -525,3 +525,26 @@ def test_indexed_export_euler_open_and_geometry():
     assert np.abs(pos - first[flat]).max() <= 1e-12
     q = np.round(first * 2 ** 30).astype(np.int64)
     assert np.unique(q, axis=0).shape[0] == V
+
+
+@pytest.mark.parametrize("form", ["plain", "sphere"])
+def test_zero_amplitude_displacement_is_the_plain_update(form):
+    """R14 reduces to the undisplaced update when the amplitude is zero (the
+    other displacement parameters set): the frames give the same leaves and
+    links as the plain configuration, for the FP32 and the sphere forms."""
+    if form == "plain":
+        a = W.configs.config_terrain(n_frames=12, nx=10, D=14, amp=0.0)
+        b = W.configs.config2(n_frames=12, nx=10)
+        D, frames_a, frames_b = 14, a.frames, b.frames
+    else:
+        a = W.configs.config_waves(n_frames=300, D=13, amp=0.0)
+        b = W.configs.config_dodeca(n_frames=300, D=13)
+        D, frames_a, frames_b = 13, a.frames[60:300:12], b.frames[60:300:12]
+    assert frames_a[0].disp_octaves > 0 and frames_a[0].disp_amplitude == 0.0
+    oa, ob = Oracle(a.mesh, D, a.max_depth), Oracle(b.mesh, D, b.max_depth)
+    for fa, fb in zip(frames_a, frames_b):
+        oa.update(fa)
+        ob.update(fb)
+    for x, y in zip(oa.leaves(), ob.leaves()):
+        assert np.array_equal(x, y)
+    assert oa.live_count > len(a.mesh.face_sizes)
