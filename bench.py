@@ -68,9 +68,9 @@ STEP_KERNELS = ("prep", "classify", "walk", "gate", "scatter", "alloc", "free", 
 # + dram__bytes_write, L2 flushed before each pass), per live bisector at
 # frame start, valid only for the kernel sources it was taken on
 # (profiles/grid_flythrough_k_frame.md has the capture and its command).
-FRAME_TRAFFIC = {"sources_sha256_16": "9e07d5d551af55f0", "bytes_per_live": 79.0,
-                 "capture": "frames 7 and 8 of the flythrough: 52.1 MB at 659,164 live, "
-                            "56.3 MB at 712,190 live"}
+FRAME_TRAFFIC = {"sources_sha256_16": "382a0c6386655379", "bytes_per_live": 75.3,
+                 "capture": "frames 7 and 8 of the flythrough: 50.4 MB at 659,164 live, "
+                            "52.9 MB at 712,190 live"}
 FRAME_SOURCES = ("cbt_fused.cu", "cbt_phases.cuh", "cbt_device.cuh")
 
 

@@ -240,7 +240,7 @@ class CBT:
     """One instance: a halfedge mesh and a pool of 2^D bisectors on a GPU."""
 
     def __init__(self, mesh=None, D: int = 16, max_depth: int = 14, halfedges=None, pos=None,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, workspace=None):
         lib = load()
         if halfedges is None:
             halfedges = halfedges_from_faces(mesh)
@@ -255,7 +255,14 @@ class CBT:
         nbytes = lib.cbt_workspace_bytes(H, D)
         if nbytes == 0:
             raise CBTError(1, "cbt_workspace_bytes")
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        elif (workspace.dtype != torch.uint8 or not workspace.is_cuda or not workspace.is_contiguous()
+              or workspace.numel() < nbytes):
+            raise ValueError(f"workspace: a contiguous uint8 CUDA tensor of at least {nbytes} bytes")
+        else:
+            self.device = workspace.device
+        self.workspace = workspace  # caller memory is reused as it is (cbt_create initialises what it reads)
         h = C.c_void_p()
         he = {k: np.ascontiguousarray(v, np.int32) for k, v in halfedges.items()}
         rc = lib.cbt_create(H, _np_ptr(he["twin"]), _np_ptr(he["next"]), _np_ptr(he["prev"]),

@@ -46,7 +46,7 @@ uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems;
 
 // Per-instance arrays.
 struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, root64, rel, corner, batch,
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, pc, pct, root64, rel, corner, batch,
         total;
     uint32_t cap, W, ch;
 };
@@ -110,6 +110,8 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.chg = take(4u * cap);
     L.chgr = take(16u * cap);
     L.vc = take(36u * cap);
+    L.pc = take(128u * cap);
+    L.pct = take(16u * cap);
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
     L.corner = take(12u * h);
@@ -548,6 +550,8 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     I.chg = reinterpret_cast<uint32_t*>(b + L.chg);
     I.chgr = reinterpret_cast<uint4*>(b + L.chgr);
     I.vc = reinterpret_cast<float*>(b + L.vc);
+    I.pc = reinterpret_cast<double*>(b + L.pc);
+    I.pct = reinterpret_cast<ulonglong2*>(b + L.pct);
     I.root64 = reinterpret_cast<double*>(b + L.root64);
     I.rel = b + L.rel;
     I.cap = L.cap;
@@ -578,6 +582,7 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     double* d_hpos = reinterpret_cast<double*>(b + L.rel + align256(12u * h));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaMemsetAsync(I.g, 0, sizeof(Globals), s);
+    cudaMemsetAsync(I.pct, 0, 16u * static_cast<size_t>(L.cap), s);  // no tag matches (heap ID 0)
     cudaMemcpyAsync(d_ints, ints.data(), 12u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_hpos, hpos.data(), 24u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(st->corner, corner.data(), 12u * h, cudaMemcpyHostToDevice, s);

@@ -20,6 +20,11 @@
 //   vc[cap]    9 x f32 in the sphere and displaced forms, the vertices the LOD test
 //                    evaluated this frame (valid while the slot's cmd has
 //                    kVcValid), copied by the vertex export
+//   pc[16][cap] f64  sphere form: per slot the frame-independent part of the
+//                    LOD test's four vertices (its three and the parent's new
+//                    one), {p_x, p_y, p_z, f} each (component-major: entry k
+//                    of slot s at pc[k cap + s])
+//   pct[cap]   u64x2 the tag of pc[.][s]: {heap ID, cache generation}
 //   root64[H*9], rel[H*9]: root vertices (FP64) and their per-frame offsets
 //                    from the camera (FP32, fixed point or FP64)
 //   corner[H*3] u32  global points of the root corners (mesh vertex ids, and
@@ -78,9 +83,14 @@ struct Globals {
     uint32_t nstiles;   // scan tiles of this frame: ceil(N / kScanItems)
     uint32_t Stot;      // total split cost requested this frame (one-launch frame)
     uint32_t stats[kStCount];
-    uint32_t pad[64 - 10 - kStCount];
+    uint32_t pc_pad;
+    unsigned long long pc_gen;     // sphere-point cache generation (0: none made yet)
+    unsigned long long pc_radius;  // the shape it was made with: radius (FP64 bits),
+    uint32_t pc_damp, pc_dfreq, pc_doct, pc_dseed;  // displacement (FP32 bits)
+    uint32_t pad[64 - 32];
 };
 static_assert(sizeof(Globals) == 256, "Globals must be 256 bytes");
+static_assert(10 + kStCount + 1 == 24, "pc_gen must sit at byte 96");
 
 // Per-instance device arrays and sizes.
 struct Inst {
@@ -96,6 +106,8 @@ struct Inst {
     uint32_t* chg;  // live indices of the changed bisectors, in ascending slot order
     uint4* chgr;    // one-launch frame: per changed bisector {live index, slot, cmd, dest}
     float* vc;      // per slot, the frame's FP32 vertices [3][3] (sphere form, one-launch frame)
+    double* pc;     // sphere form: per slot {p, f} of the LOD test's four vertices, [16][cap]
+    ulonglong2* pct;  // tag of pc[.][s]: {heap ID, generation}
     double* root64;
     void* rel;
     Globals* g;
@@ -414,34 +426,52 @@ __device__ __forceinline__ void displace_plain(float r[3], const FrameP& fp) {
 // With a displacement the FP32 form adds amplitude * fbm2(world x, y) to z
 // (displace_plain) and the sphere form takes radius + double(amplitude *
 // fbm3(u)) for the radius, u_c = float(p_c y) the unit direction.
+// The sphere form's frame-independent part of vertex v: pf = {p_x, p_y, p_z,
+// f}, f = radius' y (V: the root triangle's absolute FP64 vertices). It
+// depends on the heap ID, the mesh, the radius and the displacement only.
+template <typename T>
+__device__ __forceinline__ void sphere_point(const T W[9], int v, int d, const FrameP& fp, const double* V,
+                                             double pf[4]) {
+    const double sc = pow2d(-d);
+    const double w0 = __dmul_rn(__ull2double_rn(W[3 * v + 0]), sc);
+    const double w1 = __dmul_rn(__ull2double_rn(W[3 * v + 1]), sc);
+    const double w2 = __dmul_rn(__ull2double_rn(W[3 * v + 2]), sc);
+    double p[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c] = __fma_rn(w2, V[6 + c], __fma_rn(w1, V[3 + c], __dmul_rn(w0, V[c])));
+    const double n2 = __fma_rn(p[2], p[2], __fma_rn(p[1], p[1], __dmul_rn(p[0], p[0])));
+    double y = (double)__frcp_rn(__fsqrt_rn(__double2float_rn(n2)));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) y = __fma_rn(__dmul_rn(y, 0.5), __fma_rn(-n2, __dmul_rn(y, y), 1.0), y);
+    double rad = fp.radius;
+    if (fp.damp != 0.0f) {
+        const float hgt = __fmul_rn(fp.damp, fbm3(__double2float_rn(__dmul_rn(p[0], y)),
+                                                 __double2float_rn(__dmul_rn(p[1], y)),
+                                                 __double2float_rn(__dmul_rn(p[2], y)), fp.dfreq, fp.doct,
+                                                 fp.dseed));
+        rad = __dadd_rn(rad, (double)hgt);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pf[c] = p[c];
+    pf[3] = __dmul_rn(rad, y);
+}
+
+// The per-frame part: the point relative to the eye, rounded to FP32.
+__device__ __forceinline__ void sphere_rel(double px, double py, double pz, double f, const FrameP& fp,
+                                           float r[3]) {
+    r[0] = __double2float_rn(__fma_rn(px, f, -fp.eye[0]));
+    r[1] = __double2float_rn(__fma_rn(py, f, -fp.eye[1]));
+    r[2] = __double2float_rn(__fma_rn(pz, f, -fp.eye[2]));
+}
+
 template <typename T>
 __device__ __forceinline__ void eval_vertex(const T W[9], int v, int d, const FrameP& fp, const void* rel,
                                             uint32_t h, float r[3]) {
     const uint32_t precision = fp.precision;
     if (precision == 3) {
-        const double* V = static_cast<const double*>(rel) + 9u * h;
-        const double sc = pow2d(-d);
-        const double w0 = __dmul_rn(__ull2double_rn(W[3 * v + 0]), sc);
-        const double w1 = __dmul_rn(__ull2double_rn(W[3 * v + 1]), sc);
-        const double w2 = __dmul_rn(__ull2double_rn(W[3 * v + 2]), sc);
-        double p[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) p[c] = __fma_rn(w2, V[6 + c], __fma_rn(w1, V[3 + c], __dmul_rn(w0, V[c])));
-        const double n2 = __fma_rn(p[2], p[2], __fma_rn(p[1], p[1], __dmul_rn(p[0], p[0])));
-        double y = (double)__frcp_rn(__fsqrt_rn(__double2float_rn(n2)));
-#pragma unroll
-        for (int it = 0; it < 2; ++it) y = __fma_rn(__dmul_rn(y, 0.5), __fma_rn(-n2, __dmul_rn(y, y), 1.0), y);
-        double rad = fp.radius;
-        if (fp.damp != 0.0f) {
-            const float hgt = __fmul_rn(fp.damp, fbm3(__double2float_rn(__dmul_rn(p[0], y)),
-                                                     __double2float_rn(__dmul_rn(p[1], y)),
-                                                     __double2float_rn(__dmul_rn(p[2], y)), fp.dfreq, fp.doct,
-                                                     fp.dseed));
-            rad = __dadd_rn(rad, (double)hgt);
-        }
-        const double f = __dmul_rn(rad, y);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r[c] = __double2float_rn(__fma_rn(p[c], f, -fp.eye[c]));
+        double pf[4];
+        sphere_point<T>(W, v, d, fp, static_cast<const double*>(rel) + 9u * h, pf);
+        sphere_rel(pf[0], pf[1], pf[2], pf[3], fp, r);
     } else if (precision == 1) {
         const long long* X = static_cast<const long long*>(rel) + 9u * h;
 #pragma unroll

@@ -205,6 +205,7 @@ __device__ void phase_prep(const BatchDev& bt, Pair* s_warp, uint32_t* s_tmp) {
                 g->stats[kStLiveBefore] = N;
                 g->stats[kStFreeBefore] = I.cap - N;
                 g->stats[kStFrame] = frame_of(bt, b).frame;
+                pc_generation(g, frame_of(bt, b));
                 if (bt.nout) bt.nout[b] = N;
             }
             Pair tot;

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
                     g->stats[kStLiveBefore] = N;
                     g->stats[kStFreeBefore] = I.cap - N;
                     g->stats[kStFrame] = frame_of(bt, b).frame;
+                    pc_generation(g, frame_of(bt, b));
                     if (bt.nout) bt.nout[b] = N;
                     atomicAdd(&s_live, N);
                 }

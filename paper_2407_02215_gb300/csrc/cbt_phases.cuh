@@ -349,6 +349,102 @@ __device__ __forceinline__ void lod_wishes(const Inst& I, const FrameP& fp, uint
     }
 }
 
+// The sphere form (R13) with the per-slot point cache. A vertex's FP64 point
+// p and scale f depend on the heap ID, the mesh and the shape (radius and
+// displacement) only, so classify keeps the four vertices the LOD test reads
+// (the bisector's three, then the parent's new one) per slot, tagged with the
+// heap ID and the cache generation (a new generation whenever the shape
+// changes). A bisector whose slot still holds them evaluates only
+// r = float(fma(p, f, -eye)) per coordinate: 24 FP64 operations in place of
+// the decode, four projections with their Newton steps and the displacement.
+// The floats are those of a fresh evaluation (the same operations).
+template <typename T>
+__device__ __forceinline__ void sphere_points(const Inst& I, const FrameP& fp, uint64_t j, int d, uint32_t h,
+                                           const uint32_t* tab, uint32_t s) {
+    T W[9], Wp[9];
+    decode_weights<T>(j, d, W, Wp, tab);
+    const double* V = static_cast<const double*>(I.rel) + 9u * h;
+    const size_t cap = I.cap;
+    double* pc = I.pc + s;
+#pragma unroll 1
+    for (int v = 0; v < 3; ++v) {
+        double pf[4];
+        sphere_point<T>(W, v, d, fp, V, pf);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pc[(size_t)(4 * v + k) * cap] = pf[k];
+    }
+    double pf[4] = {0.0, 0.0, 0.0, 0.0};  // a root has no parent (never read)
+    if (d >= 1) {
+        // the parent's new vertex: its v0 (odd heap ID) or v1 (even), as in
+        // lod_wishes
+        const bool odd = (j & 1ull) != 0ull;
+        T row[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) row[k] = odd ? Wp[k] : Wp[3 + k];
+        sphere_point<T>(row, 0, d - 1, fp, V, pf);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pc[(size_t)(12 + k) * cap] = pf[k];
+}
+
+__device__ __forceinline__ void sphere_wishes(const Inst& I, const FrameP& fp, uint32_t s, uint64_t j, int d,
+                                              uint32_t h, const uint32_t* tab, bool& split, bool& merge,
+                                              float* keep) {
+    const unsigned long long gen = I.g->pc_gen;
+    const ulonglong2 tag = I.pct[s];
+    if (tag.x != j || tag.y != gen) {
+        if (d <= 31)
+            sphere_points<uint32_t>(I, fp, j, d, h, tab, s);
+        else
+            sphere_points<unsigned long long>(I, fp, j, d, h, tab, s);
+        I.pct[s] = make_ulonglong2(j, gen);
+    }
+    const size_t cap = I.cap;
+    const double* pc = I.pc + s;
+    float r[9];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+        sphere_rel(pc[(size_t)(4 * v) * cap], pc[(size_t)(4 * v + 1) * cap], pc[(size_t)(4 * v + 2) * cap],
+                   pc[(size_t)(4 * v + 3) * cap], fp, r + 3 * v);
+    if (keep)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) keep[k] = r[k];
+    split = lod_test(r, fp) == 3u && d < (int)I.max_depth;
+    merge = false;
+    if (!split && d >= 1) {
+        const bool odd = (j & 1ull) != 0ull;
+        float nv[3];
+        sphere_rel(pc[12 * cap], pc[13 * cap], pc[14 * cap], pc[15 * cap], fp, nv);
+        float q[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q[c] = odd ? nv[c] : r[c];
+            q[3 + c] = odd ? r[3 + c] : nv[c];
+            q[6 + c] = odd ? r[c] : r[3 + c];
+        }
+        merge = lod_test(q, fp) != 3u;
+    }
+}
+
+// A new generation of the sphere-point cache when a LOD frame of the sphere
+// form has a shape (radius, displacement) other than the one the current
+// generation was made with. Called for each instance by one thread, at the
+// frame's start, before any classify.
+__device__ __forceinline__ void pc_generation(Globals* g, const FrameP& fp) {
+    if (fp.precision != 3u || fp.mode != 0u) return;
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(fp.radius);
+    const uint32_t a = __float_as_uint(fp.damp), f = __float_as_uint(fp.dfreq);
+    if (g->pc_gen == 0ull || g->pc_radius != rb || g->pc_damp != a || g->pc_dfreq != f || g->pc_doct != fp.doct ||
+        g->pc_dseed != fp.dseed) {
+        g->pc_gen += 1ull;
+        g->pc_radius = rb;
+        g->pc_damp = a;
+        g->pc_dfreq = f;
+        g->pc_doct = fp.doct;
+        g->pc_dseed = fp.dseed;
+    }
+}
+
 // Compatibility chain of bisector b on the frame-start state (command form
 // of Alg. 3): returns its allocation count; with `scatter` it ORs R (and N or
 // P on coarser members) into the command words. With `rec` (cost mode) it
@@ -424,7 +520,7 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
 //
 // keep (optional): where the LOD test's vertices of j are stored (only the
 // LOD mode evaluates them; `kept` says whether it did).
-__device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uint64_t key, uint64_t j,
+__device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uint64_t key, uint32_t s, uint64_t j,
                                             const uint32_t* tab, bool& split, bool& merge, float* keep = nullptr,
                                             bool* kept = nullptr) {
     const int d = depth_of(j, I.ch);
@@ -434,7 +530,9 @@ __device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uin
     if (d < 0 || h >= I.H) return false;
     switch (fp.mode) {
         case 0:
-            if (d <= 31)
+            if (fp.precision == 3u)
+                sphere_wishes(I, fp, s, j, d, h, tab, split, merge, keep);
+            else if (d <= 31)
                 lod_wishes<uint32_t>(I, fp, j, d, h, tab, split, merge, keep);
             else
                 lod_wishes<unsigned long long>(I, fp, j, d, h, tab, split, merge, keep);
@@ -465,7 +563,7 @@ __device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& f
                                                   uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt,
                                                   bool cache = false) {
     bool split, merge, kept;
-    if (!item_wishes(I, fp, key, j, tab, split, merge, cache ? I.vc + 9ull * s : nullptr, &kept)) {
+    if (!item_wishes(I, fp, key, s, j, tab, split, merge, cache ? I.vc + 9ull * s : nullptr, &kept)) {
         set_err(I.g, kErrLink);
         *cmd_ptr(I, s) = 0u;
         I.scan[i] = 0u;
