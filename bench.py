@@ -68,9 +68,9 @@ STEP_KERNELS = ("prep", "classify", "walk", "gate", "scatter", "alloc", "free", 
 # + dram__bytes_write, L2 flushed before each pass), per live bisector at
 # frame start, valid only for the kernel sources it was taken on
 # (profiles/grid_flythrough_k_frame.md has the capture and its command).
-FRAME_TRAFFIC = {"sources_sha256_16": "382a0c6386655379", "bytes_per_live": 75.3,
-                 "capture": "frames 7 and 8 of the flythrough: 50.4 MB at 659,164 live, "
-                            "52.9 MB at 712,190 live"}
+FRAME_TRAFFIC = {"sources_sha256_16": "292d55da21e88d61", "bytes_per_live": 76.7,
+                 "capture": "frames 7 and 8 of the flythrough: 51.6 MB at 659,164 live, "
+                            "53.6 MB at 712,190 live"}
 FRAME_SOURCES = ("cbt_fused.cu", "cbt_phases.cuh", "cbt_device.cuh")
 
 
@@ -620,20 +620,21 @@ def bench_reduce(args):
                        "reps": reps}}
 
 
-def _frames_timed(args, spec, vertices=True, busy_min=1000):
+def _frames_timed(args, spec, vertices=True, busy_min=1000, point_cache=False):
     """One instance over its frames as a CUDA graph, L2 flushed before every
-    frame, vertices exported every frame: per-frame event times, live
-    counts, and a device-timer phase breakdown (second run) of the frames
-    with more than busy_min live bisectors."""
+    frame, vertices exported every frame (with ``point_cache``, the sphere
+    form's point cache attached): per-frame event times, live counts, and a
+    device-timer phase breakdown (second run) of the frames with more than
+    busy_min live bisectors."""
     import torch
 
     from paper_2407_02215_gb300 import CBT
     vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device="cuda") if vertices else None
-    g0 = CBT(spec.mesh, spec.D, spec.max_depth)
+    g0 = CBT(spec.mesh, spec.D, spec.max_depth, point_cache=point_cache)
     for fp in spec.frames[:max(args.warmup, 3)]:
         g0.update(fp, vertices_out=vbuf)
     del g0
-    g = CBT(spec.mesh, spec.D, spec.max_depth)
+    g = CBT(spec.mesh, spec.D, spec.max_depth, point_cache=point_cache)
     g.set_graph(True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in spec.frames]
@@ -648,7 +649,7 @@ def _frames_timed(args, spec, vertices=True, busy_min=1000):
     ms = np.array([a.elapsed_time(b) for a, b in ev])
     live = np.array(live)
     busy = live > busy_min
-    gk = CBT(spec.mesh, spec.D, spec.max_depth)
+    gk = CBT(spec.mesh, spec.D, spec.max_depth, point_cache=point_cache)
     gk.set_timing(True)
     pt, nb = {}, 0
     for k, fp in enumerate(spec.frames):
@@ -673,12 +674,13 @@ def bench_dodeca(args):
     300-frame descent from 2e7 m to 2 m; one instance, CUDA graph, vertices
     exported every frame, L2 flushed before every frame."""
     spec = W.configs.config_dodeca()
-    out = {"metric": METRIC + " [paper's planet shape]", **_frames_timed(args, spec)}
+    out = {"metric": METRIC + " [paper's planet shape]", **_frames_timed(args, spec, point_cache=True)}
     out.update({"paper": {"ms_per_update": 0.1,
                           "what": "Table 3, water planet (H 60, D 17), AMD 6800 XT, FP64 vertex decode"},
                 "config": {"workload": "dodeca planet: dodecahedron (60 halfedges), R 6.371e6 m, pool 2^17, "
                                        "max depth 50, 300-frame descent 2e7 m -> 2 m, sphere projection in FP64, "
-                                       "14 px edges, L2 flushed before every frame", "frames": len(spec.frames)}})
+                                       "14 px edges, point cache attached, L2 flushed before every frame",
+                           "frames": len(spec.frames)}})
     return out
 
 
@@ -688,12 +690,12 @@ def bench_waves(args):
     4-octave value noise (2 m, cells of 1 km to 125 m) standing in for its
     four FFT wave layers; the same descent, timing and export."""
     spec = W.configs.config_waves()
-    out = {"metric": METRIC + " [water planet, displaced]", **_frames_timed(args, spec)}
+    out = {"metric": METRIC + " [water planet, displaced]", **_frames_timed(args, spec, point_cache=True)}
     out.update({"paper": {"ms_per_update": 0.1,
                           "what": "Table 3, water planet (H 60, D 17), AMD 6800 XT, FP64 vertex decode"},
                 "config": {"workload": "wave planet: dodeca planet + radial displacement 2 m x fbm(4 octaves, "
-                                       "1 km .. 125 m cells), pool 2^17, 300-frame descent, L2 flushed before "
-                                       "every frame", "frames": len(spec.frames)}})
+                                       "1 km .. 125 m cells), pool 2^17, 300-frame descent, point cache attached, "
+                                       "L2 flushed before every frame", "frames": len(spec.frames)}})
     return out
 
 

@@ -178,6 +178,28 @@ int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_
                int32_t D, int32_t max_depth, void* workspace, size_t bytes,
                cbt_stream_t stream, cbt_state** out);
 
+/* Optional per-slot cache of the sphere form's camera-independent FP64
+ * points (precision CBT_PREC_SPHERE with the LOD mode; Sec. 4 decodes planet
+ * vertices in FP64 every frame). Classify keeps, per slot, the FP64 point
+ * and radial scale of the four vertices its LOD tests read, tagged with the
+ * heap ID and a generation that changes with the radius or the displacement.
+ * A bisector whose tag matches then costs one FP64 fused multiply-add and one
+ * conversion per coordinate; the results are the same floats as without the
+ * cache. 144 bytes per pool slot: cbt_point_cache_bytes(D) returns
+ * 144 * 2^D, or 0 for D outside 1..30. */
+size_t cbt_point_cache_bytes(int32_t D);
+
+/* Attaches a point cache to a state:
+ *   memory/bytes: caller-owned device memory, 16-byte aligned, at least
+ *                 cbt_point_cache_bytes(D) long; it must stay allocated and
+ *                 unmoved until cbt_destroy (no detach).
+ * The tags are cleared on `stream`, and the call synchronises it. Batches
+ * and servers built afterwards include the cache; ones built before run the
+ * state without it (still correct).
+ * Errors: CBT_EINVAL (NULL state or memory, memory not 16-byte aligned, a
+ * cache already attached), CBT_ENOMEM (bytes too small), CBT_ECUDA. */
+int cbt_attach_point_cache(cbt_state* st, void* memory, size_t bytes, cbt_stream_t stream);
+
 /* One frame of the update (Sec. 3.3, the update pipeline; Alg. 9):
  *   1. the live slots in ascending order (Alg. 7, CachePointers);
  *   2. classification on the frame-start state (GenerateCommands): split

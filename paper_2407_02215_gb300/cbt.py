@@ -40,6 +40,9 @@ def load(path: str | None = None):
     lib.cbt_halfedges_from_faces.argtypes = [I32, P, P, I32, P, P, P, P, P]
     lib.cbt_workspace_bytes.argtypes = [I32, I32]
     lib.cbt_workspace_bytes.restype = C.c_size_t
+    lib.cbt_point_cache_bytes.argtypes = [I32]
+    lib.cbt_point_cache_bytes.restype = C.c_size_t
+    lib.cbt_attach_point_cache.argtypes = [P, P, C.c_size_t, P]
     lib.cbt_create.argtypes = [I32, P, P, P, P, P, I32, P, I32, I32, P, C.c_size_t, P,
                                C.POINTER(C.c_void_p)]
     lib.cbt_update.argtypes = [P, P, P]
@@ -240,7 +243,11 @@ class CBT:
     """One instance: a halfedge mesh and a pool of 2^D bisectors on a GPU."""
 
     def __init__(self, mesh=None, D: int = 16, max_depth: int = 14, halfedges=None, pos=None,
-                 device="cuda", stream=None, workspace=None):
+                 device="cuda", stream=None, workspace=None, point_cache=False):
+        """``workspace``: optional caller memory (a contiguous uint8 CUDA tensor of
+        at least cbt_workspace_bytes); ``point_cache``: True to attach a newly
+        allocated sphere-form point cache (cbt_attach_point_cache), or a uint8
+        CUDA tensor of at least cbt_point_cache_bytes to attach as it is."""
         lib = load()
         if halfedges is None:
             halfedges = halfedges_from_faces(mesh)
@@ -273,6 +280,15 @@ class CBT:
             raise CBTError(rc, "cbt_create")
         self._h = h
         self._keep = []
+        self.point_cache = None
+        if point_cache is not False and point_cache is not None:
+            pbytes = lib.cbt_point_cache_bytes(D)
+            if point_cache is True:
+                point_cache = torch.empty(pbytes, dtype=torch.uint8, device=self.device)
+            rc = lib.cbt_attach_point_cache(h, _t_ptr(point_cache), point_cache.numel(), _stream_ptr(stream))
+            if rc:
+                raise CBTError(rc, "cbt_attach_point_cache")
+            self.point_cache = point_cache
 
     def __del__(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

@@ -46,7 +46,7 @@ uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems;
 
 // Per-instance arrays.
 struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, pc, pct, root64, rel, corner, batch,
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, root64, rel, corner, batch,
         total;
     uint32_t cap, W, ch;
 };
@@ -110,8 +110,6 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.chg = take(4u * cap);
     L.chgr = take(16u * cap);
     L.vc = take(36u * cap);
-    L.pc = take(128u * cap);
-    L.pct = take(16u * cap);
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
     L.corner = take(12u * h);
@@ -510,6 +508,29 @@ extern "C" size_t cbt_workspace_bytes(int32_t H, int32_t D) {
     return make_layout(H, D, L) ? L.total : 0u;
 }
 
+extern "C" size_t cbt_point_cache_bytes(int32_t D) {
+    if (D < 1 || D > 30) return 0;
+    return 144u * (static_cast<size_t>(1) << D);
+}
+
+extern "C" int cbt_attach_point_cache(cbt_state* st, void* memory, size_t bytes, cbt_stream_t stream) {
+    if (!st || !memory || (reinterpret_cast<uintptr_t>(memory) & 15u) || st->inst.pc) return CBT_EINVAL;
+    const size_t cap = st->inst.cap;
+    if (bytes < 144u * cap) return CBT_ENOMEM;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char* b = static_cast<char*>(memory);
+    Inst I = st->inst;
+    I.pc = reinterpret_cast<double*>(b);                // [16][cap]
+    I.pct = reinterpret_cast<ulonglong2*>(b + 128u * cap);  // [cap], cleared: heap ID 0 is never live
+    if (cudaMemsetAsync(I.pct, 0, 16u * cap, s) != cudaSuccess ||
+        cudaMemcpyAsync(const_cast<Inst*>(st->self->dev.inst), &I, sizeof(Inst), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CBT_ECUDA;
+    st->inst = I;
+    return CBT_OK;
+}
+
 extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, const int32_t* prev,
                           const int32_t* vert, const int32_t* face, int32_t V, const double* pos,
                           int32_t D, int32_t max_depth, void* workspace, size_t bytes,
@@ -550,8 +571,8 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     I.chg = reinterpret_cast<uint32_t*>(b + L.chg);
     I.chgr = reinterpret_cast<uint4*>(b + L.chgr);
     I.vc = reinterpret_cast<float*>(b + L.vc);
-    I.pc = reinterpret_cast<double*>(b + L.pc);
-    I.pct = reinterpret_cast<ulonglong2*>(b + L.pct);
+    I.pc = nullptr;  // no point cache until cbt_attach_point_cache
+    I.pct = nullptr;
     I.root64 = reinterpret_cast<double*>(b + L.root64);
     I.rel = b + L.rel;
     I.cap = L.cap;
@@ -582,7 +603,6 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     double* d_hpos = reinterpret_cast<double*>(b + L.rel + align256(12u * h));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaMemsetAsync(I.g, 0, sizeof(Globals), s);
-    cudaMemsetAsync(I.pct, 0, 16u * static_cast<size_t>(L.cap), s);  // no tag matches (heap ID 0)
     cudaMemcpyAsync(d_ints, ints.data(), 12u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_hpos, hpos.data(), 24u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(st->corner, corner.data(), 12u * h, cudaMemcpyHostToDevice, s);

@@ -20,6 +20,7 @@
 //   vc[cap]    9 x f32 in the sphere and displaced forms, the vertices the LOD test
 //                    evaluated this frame (valid while the slot's cmd has
 //                    kVcValid), copied by the vertex export
+// and, when a point cache is attached (caller memory of its own):
 //   pc[16][cap] f64  sphere form: per slot the frame-independent part of the
 //                    LOD test's four vertices (its three and the parent's new
 //                    one), {p_x, p_y, p_z, f} each (component-major: entry k
@@ -106,8 +107,8 @@ struct Inst {
     uint32_t* chg;  // live indices of the changed bisectors, in ascending slot order
     uint4* chgr;    // one-launch frame: per changed bisector {live index, slot, cmd, dest}
     float* vc;      // per slot, the frame's FP32 vertices [3][3] (sphere form, one-launch frame)
-    double* pc;     // sphere form: per slot {p, f} of the LOD test's four vertices, [16][cap]
-    ulonglong2* pct;  // tag of pc[.][s]: {heap ID, generation}
+    double* pc;     // optional point cache (sphere form): per slot {p, f} of the LOD test's four vertices, [16][cap]
+    ulonglong2* pct;  // tag of pc[.][s]: {heap ID, generation}; both null without a cache
     double* root64;
     void* rel;
     Globals* g;

@@ -349,7 +349,7 @@ __device__ __forceinline__ void lod_wishes(const Inst& I, const FrameP& fp, uint
     }
 }
 
-// The sphere form (R13) with the per-slot point cache. A vertex's FP64 point
+// The sphere form (R13) with a point cache attached. A vertex's FP64 point
 // p and scale f depend on the heap ID, the mesh and the shape (radius and
 // displacement) only, so classify keeps the four vertices the LOD test reads
 // (the bisector's three, then the parent's new one) per slot, tagged with the
@@ -530,7 +530,7 @@ __device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uin
     if (d < 0 || h >= I.H) return false;
     switch (fp.mode) {
         case 0:
-            if (fp.precision == 3u)
+            if (fp.precision == 3u && I.pc)
                 sphere_wishes(I, fp, s, j, d, h, tab, split, merge, keep);
             else if (d <= 31)
                 lod_wishes<uint32_t>(I, fp, j, d, h, tab, split, merge, keep);

@@ -1,10 +1,11 @@
-"""The sphere form's per-slot point cache (classify keeps each bisector's
-FP64 points and scales, tagged with its heap ID and a cache generation, and
-evaluates only the eye-relative rounding while the tag matches). The cache
-must never change a result: a new generation is made whenever the radius or
-the displacement changes, frames of another form or mode leave it as it is,
-and a workspace that held another instance's cache starts with no tag
-matching. Every case is compared with the oracle frame by frame."""
+"""The sphere form's optional per-slot point cache (cbt_attach_point_cache:
+classify keeps each bisector's FP64 points and scales, tagged with its heap
+ID and a cache generation, and evaluates only the eye-relative rounding while
+the tag matches). The cache must never change a result: a new generation is
+made whenever the radius or the displacement changes, frames of another form
+or mode leave it as it is, and cache memory that held another instance's
+points starts with no tag matching. Every case is compared with the oracle
+frame by frame; the same frames without a cache take the uncached path."""
 import dataclasses
 
 import numpy as np
@@ -16,6 +17,7 @@ from workloads.cameras import PREC_FP32, forced_params
 from tests.gpu_helpers import assert_same_state, run_pair
 
 FORMS = pytest.mark.parametrize("fused", [True, False], ids=["fused", "per_step"])
+EINVAL, ENOMEM = 1, 4  # CBT_EINVAL, CBT_ENOMEM
 
 
 @pytest.fixture(scope="module")
@@ -25,9 +27,9 @@ def P():
     return P
 
 
-def _maker(P, fused):
+def _maker(P, fused, cache=True):
     def make(mesh, D, max_depth):
-        g = P.CBT(mesh, D, max_depth)
+        g = P.CBT(mesh, D, max_depth, point_cache=cache)
         g.set_fused(fused)
         return g
     return make
@@ -66,14 +68,15 @@ def _export_check(g, o, fp, D):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("cache", [True, False], ids=["cache", "no_cache"])
 @FORMS
-def test_shape_changes_make_new_generations(P, fused):
+def test_shape_changes_make_new_generations(P, fused, cache):
     """States equal the oracle's after every frame of the shape-changing
     sequence (a stale cached point would change an LOD decision); then two
     more frames with the exported vertices compared bit for bit, the first
     with a new shape, the second with the same one (cached points)."""
     spec, frames = _shape_frames()
-    g, o = run_pair(spec.mesh, 15, spec.max_depth, frames, _maker(P, fused), Oracle, check_every=1)
+    g, o = run_pair(spec.mesh, 15, spec.max_depth, frames, _maker(P, fused, cache), Oracle, check_every=1)
     last = frames[-1]
     _export_check(g, o, dataclasses.replace(last, disp_amplitude=2.0e4), 15)
     _export_check(g, o, dataclasses.replace(last, disp_amplitude=2.0e4), 15)
@@ -98,22 +101,23 @@ def test_the_shape_changes_decide_something():
 
 @pytest.mark.gpu
 @FORMS
-def test_reused_workspace_starts_without_tags(P, fused):
-    """An instance created in the workspace of another one (same mesh and
-    pool, the same heap IDs early in the descent, another radius) equals
-    the oracle: none of the old instance's cached points is taken."""
+def test_reused_cache_memory_starts_without_tags(P, fused):
+    """An instance (in the workspace of another one) attached to the other
+    one's point-cache memory, with the same mesh and pool, the same heap IDs
+    early in the descent and another radius, equals the oracle: none of the
+    old instance's cached points is taken."""
     import torch
     spec = W.configs.config_dodeca(n_frames=300, D=15)
     frames = spec.frames[::10][:20]
     R = frames[0].sphere_radius
-    g1 = P.CBT(spec.mesh, 15, spec.max_depth)
+    g1 = P.CBT(spec.mesh, 15, spec.max_depth, point_cache=True)
     g1.set_fused(fused)
     for fp in frames:
         g1.update(fp)
     torch.cuda.synchronize()
-    ws = g1.workspace
+    ws, pcm = g1.workspace, g1.point_cache
     del g1
-    g2 = P.CBT(spec.mesh, 15, spec.max_depth, workspace=ws)
+    g2 = P.CBT(spec.mesh, 15, spec.max_depth, workspace=ws, point_cache=pcm)
     g2.set_fused(fused)
     o = Oracle(spec.mesh, 15, spec.max_depth)
     for k, fp in enumerate(frames[:-1]):
@@ -124,3 +128,40 @@ def test_reused_workspace_starts_without_tags(P, fused):
         assert g2.stats()["error"] == 0
         assert_same_state(g2, o, f"frame {k}")
     _export_check(g2, o, dataclasses.replace(frames[-1], sphere_radius=R * 1.002), 15)
+
+
+@pytest.mark.gpu
+def test_attach_errors(P):
+    """cbt_attach_point_cache refuses memory that is not 16-byte aligned or
+    too short, and a second cache; the state still updates afterwards."""
+    import ctypes as C
+    import torch
+    lib = P.load()
+    spec = W.configs.config_dodeca(n_frames=300, D=14)
+    g = P.CBT(spec.mesh, 14, spec.max_depth)
+    need = lib.cbt_point_cache_bytes(14)
+    buf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.cbt_attach_point_cache(g.handle, C.c_void_p(buf.data_ptr() + 8), need, s) == EINVAL
+    assert lib.cbt_attach_point_cache(g.handle, C.c_void_p(buf.data_ptr()), need - 16, s) == ENOMEM
+    assert lib.cbt_attach_point_cache(g.handle, None, need, s) == EINVAL
+    assert lib.cbt_attach_point_cache(g.handle, C.c_void_p(buf.data_ptr()), need, s) == 0
+    assert lib.cbt_attach_point_cache(g.handle, C.c_void_p(buf.data_ptr()), need, s) == EINVAL
+    o = Oracle(spec.mesh, 14, spec.max_depth)
+    for fp in spec.frames[::30]:
+        g.update(fp)
+        o.update(fp)
+    torch.cuda.synchronize()
+    assert g.stats()["error"] == 0
+    assert_same_state(g, o, "after the attach calls")
+
+
+def test_point_cache_bytes():
+    """144 bytes per pool slot (16 FP64 values and a 16-byte tag), 0 for a
+    pool exponent outside 1..30; a host call, no GPU needed."""
+    import paper_2407_02215_gb300 as P
+    P.build_library()
+    lib = P.load()
+    assert lib.cbt_point_cache_bytes(17) == 144 << 17
+    assert lib.cbt_point_cache_bytes(1) == 288
+    assert lib.cbt_point_cache_bytes(0) == 0 and lib.cbt_point_cache_bytes(31) == 0
