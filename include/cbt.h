@@ -193,8 +193,9 @@ size_t cbt_point_cache_bytes(int32_t D);
  *   memory/bytes: caller-owned device memory, 16-byte aligned, at least
  *                 cbt_point_cache_bytes(D) long; it must stay allocated and
  *                 unmoved until cbt_destroy (no detach).
- * The tags are cleared on `stream`, and the call synchronises it. Batches
- * and servers built afterwards include the cache; ones built before run the
+ * The tags are cleared on `stream`, and the call synchronises it. Call it
+ * while no frame of the state is in flight on another stream. Batches and
+ * servers built afterwards include the cache; ones built before run the
  * state without it (still correct).
  * Errors: CBT_EINVAL (NULL state or memory, memory not 16-byte aligned, a
  * cache already attached), CBT_ENOMEM (bytes too small), CBT_ECUDA. */
