@@ -262,6 +262,13 @@ class CBT:
         nbytes = lib.cbt_workspace_bytes(H, D)
         if nbytes == 0:
             raise CBTError(1, "cbt_workspace_bytes")
+        pbytes = lib.cbt_point_cache_bytes(D)
+        if isinstance(point_cache, torch.Tensor):
+            if (point_cache.dtype != torch.uint8 or not point_cache.is_cuda or not point_cache.is_contiguous()
+                    or point_cache.numel() < pbytes):
+                raise ValueError(f"point_cache: a contiguous uint8 CUDA tensor of at least {pbytes} bytes")
+        elif not (point_cache is True or point_cache is False or point_cache is None):
+            raise ValueError("point_cache: True, False or a uint8 CUDA tensor")
         if workspace is None:
             workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         elif (workspace.dtype != torch.uint8 or not workspace.is_cuda or not workspace.is_contiguous()
@@ -282,7 +289,6 @@ class CBT:
         self._keep = []
         self.point_cache = None
         if point_cache is not False and point_cache is not None:
-            pbytes = lib.cbt_point_cache_bytes(D)
             if point_cache is True:
                 point_cache = torch.empty(pbytes, dtype=torch.uint8, device=self.device)
             rc = lib.cbt_attach_point_cache(h, _t_ptr(point_cache), point_cache.numel(), _stream_ptr(stream))

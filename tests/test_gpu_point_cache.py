@@ -165,3 +165,19 @@ def test_point_cache_bytes():
     assert lib.cbt_point_cache_bytes(17) == 144 << 17
     assert lib.cbt_point_cache_bytes(1) == 288
     assert lib.cbt_point_cache_bytes(0) == 0 and lib.cbt_point_cache_bytes(31) == 0
+
+
+def test_python_arguments_are_checked_before_any_device_work():
+    """The binding refuses a host tensor (or a wrong type) as workspace or
+    point-cache memory before it allocates or launches anything."""
+    import torch
+    import paper_2407_02215_gb300 as P
+    P.build_library()
+    mesh = W.meshes.cube_mesh()
+    with pytest.raises(ValueError, match="point_cache"):
+        P.CBT(mesh, 12, 8, point_cache=torch.empty(144 << 12, dtype=torch.uint8))
+    for bad in ("yes", 1):
+        with pytest.raises(ValueError, match="point_cache"):
+            P.CBT(mesh, 12, 8, point_cache=bad)
+    with pytest.raises(ValueError, match="workspace"):
+        P.CBT(mesh, 12, 8, workspace=torch.empty(1 << 24, dtype=torch.uint8))
