@@ -165,6 +165,7 @@ def test_point_cache_bytes():
     assert lib.cbt_point_cache_bytes(17) == 144 << 17
     assert lib.cbt_point_cache_bytes(1) == 288
     assert lib.cbt_point_cache_bytes(0) == 0 and lib.cbt_point_cache_bytes(31) == 0
+    assert lib.cbt_attach_point_cache(None, None, 0, None) == EINVAL  # NULL state: refused before any CUDA call
 
 
 def test_python_arguments_are_checked_before_any_device_work():
