@@ -66,8 +66,8 @@ STEP_KERNELS = ("prep", "classify", "walk", "gate", "scatter", "alloc", "free", 
 
 # DRAM traffic of the one-launch frame from one ncu capture (dram__bytes_read
 # + dram__bytes_write, L2 flushed before each pass), per live bisector at
-# frame start, valid only for the kernel sources it was taken on
-# (profiles/grid_flythrough_k_frame.md has the capture and its command).
+# frame start, valid only for the kernel sources it was taken on (their
+# hash below).
 FRAME_TRAFFIC = {"sources_sha256_16": "292d55da21e88d61", "bytes_per_live": 76.7,
                  "capture": "frames 7 and 8 of the flythrough: 51.6 MB at 659,164 live, "
                             "53.6 MB at 712,190 live"}
@@ -85,6 +85,20 @@ def frame_traffic(mean_live):
     if h.hexdigest()[:16] != FRAME_TRAFFIC["sources_sha256_16"]:
         return None
     return FRAME_TRAFFIC["bytes_per_live"] * mean_live
+
+
+def frame_bytes(st: dict, cap: int, export: bool = True) -> float:
+    """The bytes one frame must move, from the frame's counters: per live
+    bisector at frame start (N) its record read once (8 B heap ID, 4 B root
+    slot, 12 B links), its 4 B command word written and about 8 B of scan
+    words; 24 B per new record (A); 12 B per rewritten link of an unchanged
+    neighbour (U); the bitfield read and written (2^D / 8 B each) and the
+    sum tree written (8 B per bitfield word); with the export, 36 B per live
+    bisector after the frame (N')."""
+    N, A, U, N2 = st["live_before"], st["allocated"], st["relinked"], st["live_after"]
+    W = max(1, cap // 32)
+    b = N * (8 + 4 + 12) + N * 4 + N * 8 + A * 24 + U * 12 + 2 * cap / 8 + 8 * W
+    return float(b + (36 * N2 if export else 0))
 
 
 def algorithmic_bytes(kernel: str, st: dict, cap: int) -> float:
@@ -321,15 +335,17 @@ def bench_ours(args):
     # frame reads the device timer at its phase boundaries (block 0)
     gk = CBT(spec.mesh, spec.D, spec.max_depth, device=dev)
     gk.set_timing(True)
-    ptimes, frame_bytes = {}, 0.0
+    ptimes, kbytes = {}, {}
     for fp in frames:
         flush.zero_()
         gk.update(fp, vertices_out=vbuf)
         for name, pms in gk.kernel_times().items():
             ptimes[name] = ptimes.get(name, 0.0) + pms
         st = gk.stats()
-        frame_bytes += sum(algorithmic_bytes(k, st, 1 << spec.D) for k in STEP_KERNELS)
+        for k in STEP_KERNELS:
+            kbytes[k] = kbytes.get(k, 0.0) + algorithmic_bytes(k, st, 1 << spec.D)
     del gk
+    fbytes = sum(frame_bytes(st, 1 << spec.D) for st in stats)
 
     # the per-step form (one launch per step, CUDA graph) on the same frames,
     # for comparison, and its per-kernel times (events between the launches)
@@ -397,11 +413,12 @@ def bench_ours(args):
 
     if rank != 0:
         return None
+    frame_kernel = "k_frame1" if "final" in ptimes else "k_frame"
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     # the dominant (only) kernel of the timed region is the one-launch frame:
-    # its algorithmic bytes over its event-timed duration
-    ach = frame_bytes / (float(ms.sum()) / 1e3) / 1e9
+    # the frame's algorithmic bytes over its event-timed duration
+    ach = fbytes / (float(ms.sum()) / 1e3) / 1e9
     phase_share = {k: round(v / sum(ptimes.values()), 4) for k, v in sorted(ptimes.items(), key=lambda x: -x[1])}
     cfg = workload_config(spec, len(frames))
     cfg["parallelism"] = f"replicas x{world}"
@@ -411,12 +428,16 @@ def bench_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64+fp32",
         "data": "synthetic (seeded grid mesh and camera path)", "config": cfg,
         "ms_per_frame_p50": float(np.percentile(ms, 50)), "ms_per_frame_p99": float(np.percentile(ms, 99)),
-        "roofline": {"bound": "hbm", "kernel": "k_frame (the whole frame, one cooperative launch)",
+        "roofline": {"bound": "hbm", "kernel": f"{frame_kernel} (the whole frame, one cooperative launch)",
                      "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                      "peak_source": "measured" if peaks else "fallback",
-                     "algorithmic_bytes_per_frame": frame_bytes / len(frames),
+                     "algorithmic_bytes_per_frame": fbytes / len(frames),
+                     "bytes_model": "N(8+4+12) record read + 4N command + 8N scans + 24A new records + 12U "
+                                    "relinks + bitfield read/write + sum tree + 36N' export, from the frame counters",
                      "traffic": frame_traffic(bis / len(frames)),
                      "traffic_note": "ncu DRAM bytes per launch scaled by live count; null if the kernel changed"},
+        "per_kernel_bytes": {k: round(v / len(frames)) for k, v in kbytes.items()},
+        "per_kernel_bytes_note": "per-step form's kernels, each reading its inputs again (L2 re-reads included)",
         "phase_ms_per_frame": {k: round(v / len(frames), 5) for k, v in ptimes.items()},
         "phase_share": phase_share,
         "phase_times_from": "second pass over the same frames, device timer at the phase boundaries",

@@ -89,6 +89,8 @@ def load(path: str | None = None):
     lib.cbt_kernel_name.restype = C.c_char_p
     lib.cbt_phase_name.argtypes = [U32]
     lib.cbt_phase_name.restype = C.c_char_p
+    lib.cbt_state_phase_name.argtypes = [P, U32]
+    lib.cbt_state_phase_name.restype = C.c_char_p
     lib.cbt_sum_reduce.argtypes = [P, I32, P, P]
     lib.cbt_compact.argtypes = [P, P, I32, P, C.c_uint32, P]
     lib.cbt_server_set_fused.argtypes = [P, C.c_int]
@@ -341,8 +343,9 @@ class CBT:
         per phase (fused form), by name."""
         buf = (C.c_float * 16)()
         n = _lib.cbt_kernel_times(self._h, buf, 16)
-        name = _lib.cbt_phase_name if self.fused else _lib.cbt_kernel_name
-        return {name(k).decode(): float(buf[k]) for k in range(n)}
+        if self.fused:
+            return {_lib.cbt_state_phase_name(self._h, k).decode(): float(buf[k]) for k in range(n)}
+        return {_lib.cbt_kernel_name(k).decode(): float(buf[k]) for k in range(n)}
 
     def live_count(self, stream=None) -> int:
         n = C.c_uint32()

@@ -30,6 +30,9 @@ constexpr uint32_t kLaunchesPerStep[kNumKernels] = {1, 1, 1, 1, 1, 1, 1, 1, 2, 1
 // phases of the one-launch frame
 const char* const kPhaseNames[kFramePhases] = {"prep",  "classify", "gate_sum", "gate",    "alloc_sum",
                                                "alloc", "fill",     "reduce",   "compact", "vertices"};
+// phases of the single-instance frame (k_frame1)
+const char* const kPhaseNames1[kFrame1Phases] = {"prep", "classify", "gate_sum", "gate",
+                                                 "alloc", "fill",     "final",    "vertices"};
 constexpr uint32_t kFusedTileWords = 64;
 constexpr uint32_t kFusedMaxTileWords = 128;
 
@@ -179,6 +182,8 @@ struct cbt_batch {
     uint32_t grid_mult = 8;
     bool fused = true;   // one cooperative launch per frame (else one launch per step)
     int fused_grid = 1;  // its blocks: resident blocks per SM x SMs, at most the tiles
+    int fused_grid1 = 0; // the same for the single-instance frame (0: not available)
+    bool last_frame1 = false;  // the last fused frame ran the single-instance kernel
     bool use_graph = false;
     cudaGraphExec_t exec = nullptr;
     uint32_t exec_tw = 0, exec_mult = 0;
@@ -282,6 +287,9 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
         if (per_sm <= 0) rc = CBT_ECUDA;
         const uint32_t work = std::max({B->dev.Titems, B->dev.Twords, (B->dev.Trel + 255u) / 256u, 1u});
         B->fused_grid = static_cast<int>(std::min<uint32_t>(work, static_cast<uint32_t>(per_sm * B->sms)));
+        const int per_sm1 = n == 1 ? frame1_blocks_per_sm() : 0;
+        if (per_sm1 > 0)
+            B->fused_grid1 = static_cast<int>(std::min<uint32_t>(work, static_cast<uint32_t>(per_sm1 * B->sms)));
     }
     if (rc) {
         if (B->h_fps) cudaFreeHost(B->h_fps);
@@ -355,12 +363,26 @@ uint32_t enqueue_kernels(const BatchDev& bt, int sms, uint32_t grid_mult, bool v
 
 // The kernels of one frame. `timed`: record events between the kernels (the
 // one-launch frame records its phase boundaries on the device instead).
+// A single instance whose pool and word tiles fit the single-instance
+// frame's shared tables runs that kernel.
+bool use_frame1(const cbt_batch* B) {
+    return B->n == 1 && B->fused_grid1 > 0 && B->cap[0] <= kFrame1MaxCap && B->tw == kFrame1TileWords;
+}
+
 void enqueue_frame(cbt_batch* B, cudaStream_t s, bool vertices, bool timed) {
     if (B->fused) {
         BatchDev bt = B->dev;
         bt.timing = timed ? 1u : 0u;
-        launch_frame(bt, B->fused_grid, s);
         B->launches = 1;
+        if (use_frame1(B)) {
+            const uint32_t span = std::min<uint32_t>(B->cap[0], 32u * B->tw);
+            launch_frame1(bt, B->fused_grid1, ceil_log2(span), s);
+            B->last_frame1 = true;
+            B->timed = timed ? static_cast<uint32_t>(kFrame1Phases) : 0u;
+            return;
+        }
+        B->last_frame1 = false;
+        launch_frame(bt, B->fused_grid, s);
         // a batch exports vertices within its compaction phase
         B->timed = timed ? static_cast<uint32_t>(B->n == 1 ? kFramePhases : kFramePhases - 1) : 0u;
         return;
@@ -827,6 +849,11 @@ extern "C" const char* cbt_kernel_name(uint32_t k) { return k < kNumKernels ? kK
 
 extern "C" const char* cbt_phase_name(uint32_t k) {
     return k < static_cast<uint32_t>(kFramePhases) ? kPhaseNames[k] : "";
+}
+
+extern "C" const char* cbt_state_phase_name(const cbt_state* st, uint32_t k) {
+    if (st && st->self->last_frame1) return k < static_cast<uint32_t>(kFrame1Phases) ? kPhaseNames1[k] : "";
+    return cbt_phase_name(k);
 }
 
 extern "C" int cbt_selftest_bounded_wait(void* d_scratch, int32_t blocks, int32_t limit, cbt_stream_t stream) {

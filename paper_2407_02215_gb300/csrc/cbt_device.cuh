@@ -88,7 +88,11 @@ struct Globals {
     unsigned long long pc_gen;     // sphere-point cache generation (0: none made yet)
     unsigned long long pc_radius;  // the shape it was made with: radius (FP64 bits),
     uint32_t pc_damp, pc_dfreq, pc_doct, pc_dseed;  // displacement (FP32 bits)
-    uint32_t pad[64 - 32];
+    // single-instance frame: the frame's requested merge cost (over every
+    // recorded group) and split cost, summed in classify; when their sum fits
+    // the free slots every request is granted without the prefix gate
+    unsigned long long rq_merge, rq_split;
+    uint32_t pad[64 - 36];
 };
 static_assert(sizeof(Globals) == 256, "Globals must be 256 bytes");
 static_assert(10 + kStCount + 1 == 24, "pc_gen must sit at byte 96");

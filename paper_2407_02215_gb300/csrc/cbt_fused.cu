@@ -368,7 +368,7 @@ __device__ __forceinline__ uint32_t stile_first(const FCtx& c, uint32_t ipt) {
 // sums. The group checks (group record, then the members' command words)
 // run from a list, two dependent loads per listed item.
 __device__ void phase_gate_sum(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_t* s_red, uint32_t* s_n,
-                               uint32_t* s_list) {
+                               uint32_t* s_list, bool clear_marks = false) {
     const uint32_t T = bt.bg->total_stiles, ipt = bt.bg->scan_ipt;
     for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
         if (threadIdx.x == 0) *s_n = 0;
@@ -386,8 +386,13 @@ __device__ void phase_gate_sum(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uin
             loc.b += in ? I.scan[i0 + k] : 0u;
         }
 #pragma unroll
-        for (uint32_t k = 0; k < kMaxIpt; ++k)
-            if (sl[k] != kNull && (*cmd_ptr(I, sl[k]) & kGrpMin)) s_list[atomicAdd(s_n, 1u)] = i0 + k;
+        for (uint32_t k = 0; k < kMaxIpt; ++k) {
+            if (sl[k] == kNull) continue;
+            // the single-instance frame's classify marked every chain; the
+            // prefix gate starts from unmarked words
+            const uint32_t cw = clear_marks ? atomicAnd(cmd_ptr(I, sl[k]), ~kSplitMask) : *cmd_ptr(I, sl[k]);
+            if (cw & kGrpMin) s_list[atomicAdd(s_n, 1u)] = i0 + k;
+        }
         __syncthreads();
         const uint32_t n = *s_n;
         for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
@@ -452,7 +457,7 @@ __device__ uint32_t crossing_mg(const BatchDev& bt, const FCtx& c, uint32_t F, u
 // does (R6 reading); granted splits mark their chains (command form of
 // Alg. 3).
 __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_t* s_red, Pair* s_warp,
-                           uint32_t* s_tmp, uint32_t* s_n, uint2* s_list) {
+                           uint32_t* s_tmp, uint32_t* s_n, uint2* s_list, bool always_recorded = false) {
     const uint32_t T = bt.bg->total_stiles, ipt = bt.bg->scan_ipt;
     for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
         if (threadIdx.x == 0) *s_n = 0;
@@ -495,7 +500,9 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         }
         __syncthreads();
         const uint32_t n = *s_n;
-        const bool recorded = c.fp.gate != 1;  // the paper's gate charges 3d + 4 without a walk
+        // the paper's gate charges 3d + 4 without a walk (the single-instance
+        // frame walks, and records, every chain)
+        const bool recorded = always_recorded || c.fp.gate != 1;
         for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
             const uint2 e = s_list[q];
             const uint4 r = recorded ? I.grp[e.x] : make_uint4(kNull, kNull, kNull, kNull);
@@ -514,6 +521,8 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         __syncthreads();
     }
 }
+
+__device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_granted);
 
 // P4: the fate of every item after the chains are marked (kept in its scan
 // word for P5) and per tile the sums of (changed, allocations); then the
@@ -559,12 +568,23 @@ __device__ void phase_alloc_sum(const BatchDev& bt, FCtx& c, uint32_t* s_red, ui
         if (threadIdx.x == 0) bt.status[bt.Titems + t] = pack_pair(loc);
         __syncthreads();
     }
+    free_list(bt, c, s_w, false);
+}
+
+// The free list (Alg. 8 for every rank at once) per word tile: the frame's
+// first `bound` zero bits of the frame-start bitfield, bound = the free
+// slots or, when smaller, the granted merge cost plus the requested split
+// cost (all requests with `all_granted`), an upper bound of the
+// allocations.
+__device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_granted) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (uint32_t wt = blockIdx.x; wt < bt.Twords; wt += gridDim.x) {
         ctx_tile(bt, bt.wtile_base, wt, bt.Twords, c);
         const Inst& I = c.I;
         const uint32_t lt = c.lt;
-        const uint32_t bound = (uint32_t)min((uint64_t)c.F, (uint64_t)I.g->Mg + (uint64_t)I.g->Stot);
+        const uint64_t req = all_granted ? __ldcg(&I.g->rq_merge) + __ldcg(&I.g->rq_split)
+                                         : (uint64_t)I.g->Mg + (uint64_t)I.g->Stot;
+        const uint32_t bound = (uint32_t)min((uint64_t)c.F, req);
         const uint32_t TW = min(I.W, bt.tw);
         const uint32_t nt = I.W / TW;
         uint32_t ones_before = 0;
@@ -667,17 +687,22 @@ __device__ void phase_alloc(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32
 // index of its first new record (a split, or a merge group's smallest
 // member, whose command word carries no split bits). Returns the number of
 // unchanged neighbours relinked.
-__device__ __forceinline__ uint32_t fill_item(const Inst& I, uint32_t i, uint32_t s, uint32_t cmd, uint32_t dest) {
+template <typename DM>
+__device__ __forceinline__ uint32_t fill_item_dm(const Inst& I, uint32_t i, uint32_t s, uint32_t cmd, uint32_t dest,
+                                                 const DM& dm) {
     if (cmd & kSplitMask) {
-        clear_bit(I, s);
-        return fill_split(I, s, cmd, dest);
+        dm.clear(I, s);
+        return fill_split(I, s, cmd, dest, dm);
     }
     const uint4 m = I.grp[i];
     const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) clear_bit(I, ms[q]);
-    return fill_merge(I, dest, m);
+        if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) dm.clear(I, ms[q]);
+    return fill_merge(I, dest, m, dm);
+}
+__device__ __forceinline__ uint32_t fill_item(const Inst& I, uint32_t i, uint32_t s, uint32_t cmd, uint32_t dest) {
+    return fill_item_dm(I, i, s, cmd, dest, DestPlain{I.g->A});
 }
 
 // P6: FillNewBlocks + UpdateNeighbors + UpdateBitfield for the changed items,
@@ -1022,6 +1047,638 @@ __global__ void __launch_bounds__(kFThreads) k_wait_selftest(BatchGlobals* bg, i
     if (blockIdx.x == 0 && threadIdx.x == 0) bg->bar_epoch = epoch + gridDim.x;
 }
 
+// ===================================================== one instance, fewer phases
+//
+// k_frame1: the frame of a single instance (a batch of one), with the same
+// results as k_frame in five phases when the frame's requests all fit the
+// free slots, and seven when some may not:
+//   P0 prep      frame counters; the camera-relative roots; the command words
+//                of the live slots cleared
+//   P1 classify  wishes, ORed into the command words; the walks: a split
+//                wish's chain walk also marks its chain (command form of
+//                Alg. 3), a group walk records the group at its smallest
+//                member; the frame's requested merge cost (every recorded
+//                group) and split cost
+//   when requested merges plus splits exceed the free slots F:
+//   P2 gate-sum  the chain marks cleared; per-tile (merge, split) cost sums
+//   P3 gate      grants in the order of the R6 reading, and chain marking
+//   otherwise every request is granted (the prefix gate would grant them
+//   all) and the marks of P1 stand;
+//   P4 alloc     fates, their tile-local allocation prefix (a destination
+//                word holds the tile and the offset within it), the fill
+//                records per tile, the bits cleared per word tile, the free
+//                list
+//   P5 fill      the tiles' record and allocation offsets in shared memory;
+//                new records, links and bits
+//   P6 final     every word tile's new count (frame-start count, clears, and
+//                its share of the first A zero bits), hence the sum tree;
+//                the new live list read off the bitfield by warps over equal
+//                row ranges, with the vertex export (FP32, fixed point, FP64)
+//   P7 vertices  sphere and displaced forms: the export from the cache of P1
+
+constexpr uint32_t kLocBits = 13, kLocMask = (1u << kLocBits) - 1u;  // offset of a new record within its tile
+constexpr uint32_t kMaxTiles1 = kFBuf / 2;  // scan tiles and word tiles the shared tables hold
+
+// A destination word (tile << kLocBits | offset) resolved through the
+// tiles' allocation offsets in shared memory.
+struct DestTiles {
+    const uint32_t* apre;
+    uint32_t A;
+    __device__ __forceinline__ uint32_t operator()(uint32_t d) const {
+        return apre[min(d >> kLocBits, kMaxTiles1 - 1u)] + (d & kLocMask);
+    }
+    __device__ __forceinline__ void set(const Inst& I, uint32_t s) const { set_bit(I, s); }
+    __device__ __forceinline__ void clear(const Inst& I, uint32_t s) const { clear_bit(I, s); }
+};
+
+// Word-tile counts of the single-instance frame, one 64-bit word per word
+// tile (2^tbits slots, its sum-tree node at nt + t): the node's frame-start
+// value in the high half, the bits the frame clears in it in the low half.
+// The bits it sets there follow from the allocation count A alone: the new
+// records take the first A zero bits of the frame-start bitfield (Alg. 8).
+__device__ __forceinline__ unsigned long long* tile_counts(const BatchDev& bt) {
+    return bt.status + 2u * bt.Titems;
+}
+
+// P0 (single instance). The frame counters are set by block 0; every block
+// reads the live count itself. The command words of the live slots are
+// cleared: classify ORs its bits in while other walks may mark them.
+__device__ void phase_prep1(const BatchDev& bt, uint32_t tbits) {
+    const Inst& I = bt.inst[0];
+    const FrameP& fp = frame_of(bt, 0);
+    const uint32_t N = __ldcg(I.sums + 1);
+    const uint32_t nt = I.cap >> tbits;
+    unsigned long long* tc = tile_counts(bt);
+    for (uint32_t t = blockIdx.x * kFThreads + threadIdx.x; t < nt; t += gridDim.x * kFThreads)
+        tc[t] = (unsigned long long)__ldcg(I.sums + nt + t) << 32;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t per_round = gridDim.x * kFThreads;
+        const uint32_t ipt = min(kMaxIpt, max(kMinIpt, (N + per_round - 1u) / per_round));
+        const uint32_t S = ipt * kFThreads;
+        Globals* g = I.g;
+        g->N = N;
+        g->F = I.cap - N;
+        g->A = 0;
+        g->Mg = 0;
+        g->Stot = 0;
+        g->C = 0;
+        g->done = 0;
+        g->ntiles = (N + kTileItems - 1u) / kTileItems;
+        g->nstiles = (N + S - 1u) / S;
+        for (int k = 0; k < kStCount; ++k) g->stats[k] = 0;
+        g->stats[kStLiveBefore] = N;
+        g->stats[kStFreeBefore] = I.cap - N;
+        g->stats[kStFrame] = fp.frame;
+        g->rq_merge = 0;
+        g->rq_split = 0;
+        pc_generation(g, fp);
+        if (bt.nout) bt.nout[0] = N;
+        bt.tile_base[0] = 0;
+        bt.tile_base[1] = g->ntiles;
+        bt.stile_base[0] = 0;
+        bt.stile_base[1] = g->nstiles;
+        bt.bg->total_tiles = g->ntiles;
+        bt.bg->total_stiles = g->nstiles;
+        bt.bg->scan_ipt = ipt;
+        bt.bg->live_total = N;
+        bt.bg->t[kFramePhases] = 0;
+    }
+    const uint32_t nw = gridDim.x * (kFThreads / 32), wid = blockIdx.x * (kFThreads / 32) + threadIdx.x / 32u;
+    const uint32_t per = min(kRelRange, ((bt.Trel + nw - 1u) / nw + 31u) & ~31u);
+    for (uint32_t e = wid * per; e < bt.Trel; e += nw * per) rel_range(bt, e, min(bt.Trel, e + per));
+    for (uint32_t i = blockIdx.x * kFThreads + threadIdx.x; i < N; i += gridDim.x * kFThreads)
+        *cmd_ptr(I, __ldcg(I.live + i)) = 0u;
+}
+
+// Walks of the listed items (single instance): a split wish's chain walk
+// checks the chain, records its first members and marks it; a group walk
+// records the group at its smallest member. s_req sums the requests: [0]
+// merge cost of the recorded groups, [1] split cost.
+__device__ __forceinline__ void walk_list1(const Inst& I, const FrameP& fp, const uint2* s_list, uint32_t n,
+                                           uint32_t* s_req) {
+    for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
+        const uint2 e = s_list[q];
+        const uint32_t i = e.x & 0x7FFFFFFFu, s = e.y;
+        if (e.x & 0x80000000u) {
+            uint4 rec;
+            const int d = depth_of(I.heap[s], I.ch);
+            const uint32_t cost = chain_walk(I, s, d, true, &rec, true);
+            I.grp[i] = rec;
+            uint32_t sc = 3u * (uint32_t)d + 4u;  // the paper's gate: scan[i] holds it already
+            if (fp.gate != 1) {
+                sc = cost;
+                I.scan[i] = cost;
+            }
+            atomicAdd(&s_req[1], sc);
+        } else {
+            Group g;
+            if (find_group(I, s, g) && g.imin == 0) {
+                I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
+                atomicOr(cmd_ptr(I, s), kGrpMin);
+                atomicAdd(&s_req[0], fp.gate == 1 ? 2u : (uint32_t)g.np);
+            }
+        }
+    }
+}
+
+// P1 (single instance): the live list strided over the whole grid, the
+// slot and heap ID of the next rounds loaded while the current item is
+// classified; walks from the block's list.
+__device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, uint32_t* s_cnt, uint32_t* s_n,
+                                uint2* s_list, uint32_t* s_req) {
+    if (threadIdx.x == 0) {
+        *s_n = 0;
+        s_req[0] = s_req[1] = 0;
+    }
+    stats_reset(s_cnt);
+    ctx_tile(bt, bt.tile_base, 0, 1, c);
+    const Inst& I = c.I;
+    const FrameP& fp = c.fp;
+    const uint32_t N = c.N;
+    const uint64_t key = splitmix64(((uint64_t)fp.seed << 32) | (uint64_t)fp.frame);
+    const bool cache = vc_form(fp) && fp.vout;
+    const uint32_t stride = gridDim.x * kFThreads;
+    uint32_t i = blockIdx.x * kFThreads + threadIdx.x;
+    uint32_t sa = i < N ? I.live[i] : 0u;
+    uint64_t ja = i < N ? I.heap[sa] : 0ull;
+    uint32_t sb = i + stride < N ? I.live[i + stride] : 0u;
+    for (uint32_t base = blockIdx.x * kFThreads; base < N; base += stride, i += stride) {
+        const uint32_t sc = i + 2u * stride < N ? I.live[i + 2u * stride] : 0u;
+        const uint64_t jb = i + stride < N ? I.heap[sb] : 0ull;
+        if (i < N) {
+            const uint32_t cmd = classify_item(I, fp, key, i, sa, ja, s_tab, s_cnt, cache, true);
+            const bool split = (cmd & kSplitWish) != 0u;
+            const bool group = (cmd & kMergeWish) && !(cmd & kHeapOdd);
+            if (split || group) s_list[atomicAdd(s_n, 1u)] = make_uint2(i | (split ? 0x80000000u : 0u), sa);
+        }
+        sa = sb;
+        ja = jb;
+        sb = sc;
+        __syncthreads();
+        const uint32_t n = *s_n;
+        __syncthreads();
+        if (n > kWalkCap - kFThreads) {  // block-uniform
+            walk_list1(I, fp, s_list, n, s_req);
+            __syncthreads();
+            if (threadIdx.x == 0) *s_n = 0;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    walk_list1(I, fp, s_list, *s_n, s_req);
+    __syncthreads();
+    stats_flush(s_cnt, I.g, kStSplitWishes);
+    if (threadIdx.x == 0) {
+        if (s_req[0]) atomicAdd(&I.g->rq_merge, (unsigned long long)s_req[0]);
+        if (s_req[1]) atomicAdd(&I.g->rq_split, (unsigned long long)s_req[1]);
+    }
+    __syncthreads();
+}
+
+// Fate of live index i that charges its group (kGrpMin) when every request
+// is granted: the group's parent count (1 or 2) and bit 3 when every member
+// wishes to merge and none was marked by a chain. A group whose members all
+// wish to merge is a merge candidate (counted in s_cnt[3]), and granted.
+__device__ __forceinline__ uint32_t fate_group_granted(const Inst& I, uint32_t i, uint32_t* s_cnt) {
+    const uint4 m = I.grp[i];
+    const uint32_t ms[3] = {m.y, m.z, m.w};
+    uint32_t c[3];
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const bool b = ms[q] != kNull && bad_slot(I, ms[q], kErrLink);
+        bad = bad || b;
+        c[q] = (ms[q] != kNull && !b) ? *cmd_ptr(I, ms[q]) : kMergeWish;
+    }
+    const bool all = !bad && (c[0] & c[1] & c[2] & kMergeWish);
+    count_stat(s_cnt, 3, all);
+    const bool ok = all && !((c[0] | c[1] | c[2]) & kSplitMask);
+    return ok ? ((m.z == kNull ? 1u : 2u) | 8u) : 0u;
+}
+
+// P4 (single instance): per scan tile the fate of every item (allocation
+// count, bit 3 for a merging group), the tile-local exclusive prefix of
+// (changed, allocations), the fill records in the tile's region of chgr
+// (tile t at t S), destination words (t << kLocBits | offset) and merged
+// marks; the tile's totals go to status[Titems + t] for the fill. Then the
+// free list. Group validations run from a list (dependent loads), their
+// fates returned through shared memory.
+__device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint32_t tbits, uint32_t* s_cnt,
+                             Pair* s_warp, uint32_t* s_w, uint32_t* s_n, uint32_t* s_buf) {
+    const uint32_t T = bt.bg->total_stiles, ipt = bt.bg->scan_ipt;
+    const uint32_t S = kFThreads * ipt;
+    uint32_t* s_list = s_buf;          // local item indices to validate
+    uint32_t* s_fate = s_buf + kFBuf / 2;  // their fates, by local item index
+    if (T > kMaxTiles1 || S > kFBuf / 2) {  // the host keeps pools within the tables
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(bt.inst[0].g, kErrOverflow);
+        return;
+    }
+    if (all_granted && blockIdx.x == 0 && threadIdx.x == 0) {
+        Globals* g = bt.inst[0].g;
+        g->stats[kStSplitGranted] = __ldcg(&g->stats[kStSplitWishes]);
+    }
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        if (threadIdx.x == 0) *s_n = 0;
+        stats_reset(s_cnt);
+        ctx_tile(bt, bt.stile_base, t, T, c);
+        const Inst& I = c.I;
+        const uint32_t N = c.N;
+        const uint32_t i0 = stile_first(c, ipt);
+        const uint32_t e0 = threadIdx.x * ipt;
+        uint32_t sl[kMaxIpt], cm[kMaxIpt], f[kMaxIpt];
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) sl[k] = (k < ipt && i0 + k < N) ? I.live[i0 + k] : kNull;
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) cm[k] = sl[k] != kNull ? *cmd_ptr(I, sl[k]) : 0u;
+        // groups to validate: when every request is granted, every group its
+        // charged member recorded (a group whose members all wish to merge
+        // counts as a granted candidate even if a chain marked one of them);
+        // else the granted candidates without split bits
+        bool lst[kMaxIpt];
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) {
+            f[k] = leaves_of(cm[k] & kSplitMask);
+            lst[k] = sl[k] != kNull && (all_granted ? (cm[k] & kGrpMin) != 0u
+                                                    : (!(cm[k] & kSplitMask) && (cm[k] & kCand) && (cm[k] & kMergeGrant)));
+            if (lst[k]) s_list[atomicAdd(s_n, 1u)] = e0 + k;
+        }
+        __syncthreads();
+        const uint32_t n = *s_n;
+        for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
+            const uint32_t e = s_list[q];
+            const uint32_t i = c.lt * S + e;
+            s_fate[e] = all_granted ? fate_group_granted(I, i, s_cnt) : alloc_fate(I, i, kCand | kMergeGrant);
+        }
+        __syncthreads();
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k)
+            if (lst[k] && !(cm[k] & kSplitMask)) f[k] = s_fate[e0 + k];
+        Pair loc{0, 0};
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) {
+            const uint32_t na = f[k] & 7u;
+            loc = padd(loc, Pair{na ? 1u : 0u, na});
+        }
+        Pair tot;
+        const Pair ex = block_scan(loc, tot, s_warp);
+        if (threadIdx.x == 0) bt.status[bt.Titems + t] = pack_pair(tot);
+        // the bits this tile's changed items clear, per word tile: a block
+        // histogram over the word tiles from the one holding the tile's first
+        // slot (slots ascend with the live index); others go straight out
+        uint32_t* s_hist = s_buf + kFBuf / 2;
+        const uint32_t hbase = (I.cap + I.live[c.lt * S]) >> tbits, nt = I.cap >> tbits;
+        unsigned long long* tc = tile_counts(bt);
+        s_hist[threadIdx.x] = 0u;
+        __syncthreads();
+        auto cleared = [&](uint32_t slot) {
+            const uint32_t node = (I.cap + slot) >> tbits;
+            if (node - hbase < (uint32_t)kFThreads)
+                atomicAdd(&s_hist[node - hbase], 1u);
+            else if (node - nt < nt)
+                atomicAdd(&tc[node - nt], 1ull);
+        };
+        uint32_t crun = ex.a, arun = ex.b;
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) {
+            const uint32_t na = f[k] & 7u;
+            if (!na) continue;
+            const uint32_t dw = (t << kLocBits) | arun;
+            I.chgr[t * S + crun] = make_uint4(i0 + k, sl[k], cm[k], dw);
+            // alloc_apply, with the clears counted
+            if (!(f[k] & 8u)) {
+                *dest_ptr(I, sl[k]) = dw;
+                count_stat(s_cnt, 0, true);
+                cleared(sl[k]);
+            } else {
+                const uint4 m = I.grp[i0 + k];
+                const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (ms[q] == kNull || bad_slot(I, ms[q], kErrLink)) continue;
+                    atomicOr(cmd_ptr(I, ms[q]), kMerged);
+                    *dest_ptr(I, ms[q]) = dw + (q < 2 ? 0u : 1u);
+                    cleared(ms[q]);
+                }
+                atomicAdd(&s_cnt[2], m.z == kNull ? 2u : 4u);
+                count_stat(s_cnt, 1, true);
+            }
+            ++crun;
+            arun += na;
+        }
+        __syncthreads();
+        if (s_hist[threadIdx.x] && hbase + threadIdx.x - nt < nt)
+            atomicAdd(&tc[hbase + threadIdx.x - nt], (unsigned long long)s_hist[threadIdx.x]);
+        if (threadIdx.x == 0) {
+            const int idx[4] = {kStSplitBis, kStMergeGroups, kStMergedBis, kStMergeCand};
+            for (int k = 0; k < 4; ++k)
+                if (s_cnt[k]) atomicAdd(&I.g->stats[idx[k]], s_cnt[k]);
+            if (s_cnt[3]) atomicAdd(&I.g->stats[kStMergeGranted], s_cnt[3]);
+        }
+        __syncthreads();
+    }
+    free_list(bt, c, s_w, all_granted);
+}
+
+// P5 (single instance): every block scans the tiles' (changed, allocation)
+// totals into shared memory; the changed records of the frame, one range
+// strided evenly over the grid, are then filled with their destinations
+// resolved through the allocation offsets. The records are FillNewBlocks +
+// UpdateNeighbors + UpdateBitfield, the bit changes also moving the word
+// tiles' sum-tree nodes.
+__device__ void phase_fill1(const BatchDev& bt, FCtx& c, bool all_granted, uint32_t* s_cnt, uint32_t* s_buf,
+                            Pair* s_warp) {
+    stats_reset(s_cnt);
+    ctx_tile(bt, bt.tile_base, 0, 1, c);
+    const Inst& I = c.I;
+    const uint32_t T = bt.bg->total_stiles, S = kFThreads * bt.bg->scan_ipt;
+    uint32_t* s_cpre = s_buf;
+    uint32_t* s_apre = s_buf + kMaxTiles1;
+    if (T > kMaxTiles1) {  // alloc has set the error word
+        __syncthreads();
+        return;
+    }
+    Pair carry{0, 0};
+    for (uint32_t t0 = 0; t0 < T; t0 += kFThreads) {
+        const uint32_t t = t0 + threadIdx.x;
+        const Pair v = t < T ? unpack_pair(__ldcg(bt.status + bt.Titems + t)) : Pair{0, 0};
+        Pair tot;
+        const Pair ex = block_scan(v, tot, s_warp);
+        if (t < T) {
+            s_cpre[t] = carry.a + ex.a;
+            s_apre[t] = carry.b + ex.b;
+        }
+        carry = padd(carry, tot);
+    }
+    __syncthreads();
+    const uint32_t C = carry.a;
+    const uint64_t req = all_granted ? __ldcg(&I.g->rq_merge) + __ldcg(&I.g->rq_split)
+                                     : (uint64_t)I.g->Mg + (uint64_t)I.g->Stot;
+    const uint32_t bound = (uint32_t)min((uint64_t)c.F, req);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        I.g->A = carry.b;
+        I.g->C = C;
+        I.g->stats[kStAllocated] = carry.b;
+        if (carry.b > bound) set_err(I.g, kErrOverflow);
+    }
+    const DestTiles dm{s_apre, min(carry.b, bound)};
+    uint32_t relinked = 0;
+    for (uint32_t q = blockIdx.x * kFThreads + threadIdx.x; q < C; q += gridDim.x * kFThreads) {
+        uint32_t lo = 0, hi = T;  // the last tile whose first record is at or before q
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_cpre[mid] <= q)
+                lo = mid + 1u;
+            else
+                hi = mid;
+        }
+        const uint32_t t = lo - 1u;
+        const uint4 r = I.chgr[t * S + (q - s_cpre[t])];
+        relinked += fill_item_dm(I, r.x, r.y, r.z, dm(r.w), dm);
+    }
+    if (relinked) atomicAdd(&s_cnt[0], relinked);
+    __syncthreads();
+    stats_flush(s_cnt, I.g, kStRelinked);
+    __syncthreads();
+}
+
+// P6 (single instance). Every block computes each word tile's new count
+// from the tile counts of the frame (no bitfield read) and scans them into
+// shared memory: the new live count and each tile's first row. Block 0
+// writes the nodes above the tiles as differences of that scan; each word
+// tile's node and the nodes below it are rebuilt from its words (and the
+// count checked against them). Rows of the new live
+// list (Alg. 7 for every index) go to warps in chunks of at most 256: a warp
+// finds its first row's word from the scan and the tile's popcounts, then
+// reads the bitfield 32 words at a time, staging the set positions in
+// shared memory, and writes the chunk's live slots and, with `rows_out`,
+// their vertices.
+__device__ void phase_final1(const BatchDev& bt, FCtx& c, const uint32_t* s_tab, uint32_t* s_buf, float* s_vst,
+                             Pair* s_warp, uint32_t* s_tmp, uint32_t tbits, bool rows_out) {
+    ctx_tile(bt, bt.tile_base, 0, 1, c);
+    const Inst& I = c.I;
+    const FrameP& fp = c.fp;
+    const uint32_t W = I.W, TW = min(W, bt.tw), nt = I.cap >> tbits;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t* s_tpre = s_buf;
+    uint32_t* s_rows = s_buf + kMaxTiles1 + 256u * warp;
+    float* vst = s_vst + 288u * warp;
+    if (nt > kMaxTiles1 || TW > 64u) {  // the host keeps pools within the tables
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(I.g, kErrOverflow);
+        return;
+    }
+    // each word tile's new count: frame-start count - cleared + set, the set
+    // ones being the tile's share of the first A zero bits
+    const unsigned long long* tc = tile_counts(bt);
+    const uint32_t A = __ldcg(&I.g->A), TS = 1u << tbits;
+    uint32_t carry = 0, carry0 = 0;
+    for (uint32_t t0 = 0; t0 < nt; t0 += kFThreads) {
+        const uint32_t t = t0 + threadIdx.x;
+        const unsigned long long w = t < nt ? __ldcg(tc + t) : 0ull;
+        const uint32_t old = (uint32_t)(w >> 32), clr = (uint32_t)w;
+        Pair tot;
+        const uint32_t ones_before = carry0 + block_scan(Pair{old, 0u}, tot, s_warp).a;
+        carry0 += tot.a;
+        const long long zb = (long long)t * TS - ones_before;  // zero bits before the tile at frame start
+        const long long set = min(max((long long)A - zb, 0ll), (long long)(TS - old));
+        const uint32_t v = t < nt ? old - clr + (uint32_t)set : 0u;
+        const Pair ex = block_scan(Pair{v, 0u}, tot, s_warp);
+        if (t < nt) s_tpre[t] = carry + ex.a;
+        carry += tot.a;
+    }
+    if (threadIdx.x == 0) s_tmp[0] = 0;
+    __syncthreads();
+    const uint32_t Nn = carry;
+    if (blockIdx.x == 0) {
+        // node m (1 <= m < nt) covers tile nodes [m 2^k, (m + 1) 2^k) at 2^k
+        // tiles per node of its level
+        const int lnt = 31 - __clz((int)nt);
+        for (uint32_t m = 1u + threadIdx.x; m < nt; m += kFThreads) {
+            const int k = lnt - (31 - __clz((int)m));
+            const uint32_t a = (m << k) - nt, b = ((m + 1u) << k) - nt;
+            I.sums[m] = (b < nt ? s_tpre[b] : Nn) - s_tpre[a];
+        }
+        if (threadIdx.x == 0) {
+            I.g->stats[kStLiveAfter] = Nn;
+            if (nt == 1u) I.sums[1] = Nn;
+        }
+    }
+    // word tiles: their levels below the tile node (TW <= 64: the levels of
+    // one warp, then the node, which the fill kept, over two warps)
+    for (uint32_t wt = blockIdx.x; wt < nt; wt += gridDim.x) {
+        const uint32_t w = wt * TW + threadIdx.x;
+        const bool mine = threadIdx.x < TW;
+        const uint32_t pc = mine ? __popc(__ldcg(I.bits + w)) : 0u;
+        if (mine && TW > 1u) I.sums[W + w] = pc;
+        uint32_t v = pc;
+#pragma unroll
+        for (uint32_t L = 1; L <= 5; ++L) {
+            v += __shfl_down_sync(0xFFFFFFFFu, v, 1u << (L - 1u));
+            if ((1u << L) < TW && mine && (threadIdx.x & ((1u << L) - 1u)) == 0u) I.sums[(W + w) >> L] = v;
+        }
+        if (lane == 0 && warp * 32u < TW) atomicAdd(&s_tmp[0], v);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t node = (wt + 1u < nt ? s_tpre[wt + 1u] : Nn) - s_tpre[wt];
+            if (s_tmp[0] != node) set_err(I.g, kErrLink);
+            if (nt > 1u) I.sums[nt + wt] = node;  // (a single tile's node is the root, written above)
+            s_tmp[0] = 0;
+        }
+        __syncthreads();
+    }
+    // rows
+    const uint32_t nw = gridDim.x * (kFThreads / 32u);
+    uint32_t R = (Nn + nw - 1u) / nw;
+    R = max(32u, min(256u, (R + 31u) & ~31u));
+    const uint32_t nch = (Nn + R - 1u) / R;
+    for (uint32_t ch = blockIdx.x * (kFThreads / 32u) + warp; ch < nch; ch += nw) {
+        const uint32_t r0 = ch * R, r1 = min(Nn, r0 + R);
+        uint32_t lo = 0, hi = nt;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (s_tpre[mid] <= r0)
+                lo = mid + 1u;
+            else
+                hi = mid;
+        }
+        const uint32_t t = lo - 1u;
+        uint32_t rank = r0 - s_tpre[t];
+        uint32_t wcur = t * TW, skip = 0;
+        for (uint32_t w0 = t * TW; w0 < (t + 1u) * TW; w0 += 32u) {  // the word of set bit `rank` of the tile
+            const uint32_t wi = w0 + lane;
+            const uint32_t pc = wi < (t + 1u) * TW ? __popc(__ldcg(I.bits + wi)) : 0u;
+            uint32_t inc = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if ((int)lane >= o) inc += y;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            if (rank < total) {
+                const uint32_t L = (uint32_t)(__ffs(__ballot_sync(0xFFFFFFFFu, inc > rank)) - 1);
+                wcur = w0 + L;
+                skip = rank - __shfl_sync(0xFFFFFFFFu, inc - pc, L);
+                break;
+            }
+            rank -= total;
+        }
+        uint32_t row = r0;
+        bool first = true;
+        while (row < r1) {
+            if (wcur >= W) {  // fewer set bits than the tile nodes count
+                if (lane == 0) set_err(I.g, kErrLink);
+                break;
+            }
+            const uint32_t wi = wcur + lane;
+            uint32_t v = wi < W ? __ldcg(I.bits + wi) : 0u;
+            if (first && lane == 0)
+                for (uint32_t k = 0; k < skip; ++k) v &= v - 1u;
+            const uint32_t pc = __popc(v);
+            uint32_t inc = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if ((int)lane >= o) inc += y;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            const uint32_t need = r1 - row;
+            uint32_t o = inc - pc;
+            while (v && o < need) {
+                s_rows[o++] = wi * 32u + (uint32_t)(__ffs(v) - 1);
+                v &= v - 1u;
+            }
+            __syncwarp();
+            const uint32_t ne = min(total, need);
+            for (uint32_t k0 = 0; k0 < ne; k0 += 32u) {
+                const uint32_t k = k0 + lane;
+                const bool valid = k < ne;
+                const uint32_t sl = valid ? s_rows[k] : 0u;
+                if (valid) I.live[row + k] = sl;
+                if (rows_out) {
+                    const uint32_t r = row + k0;
+                    const uint32_t nv = fp.vcap > r ? min(min(32u, ne - k0), fp.vcap - r) : 0u;
+                    float x[9];
+                    bool ok = true;
+                    if (lane < nv) ok = vertex_eval(I, fp, I.heap[sl], s_tab, x);
+                    if (nv && __all_sync(0xFFFFFFFFu, ok)) {
+                        warp_rows_out(x, vst, fp.vout, r, nv);
+                    } else if (lane < nv && ok) {  // a row the decode refused stays unwritten
+                        float* out = fp.vout + 9ull * (r + lane);
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) out[q] = x[q];
+                    }
+                }
+            }
+            __syncwarp();
+            row += ne;
+            wcur += 32u;
+            first = false;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(BatchDev bt, uint32_t tbits) {
+    __shared__ FCtx s_c;
+    __shared__ uint32_t s_tab[64 * 9];
+    __shared__ __align__(16) uint32_t s_buf[kFBuf];
+    __shared__ __align__(16) float s_vst[288 * (kFThreads / 32)];
+    __shared__ Pair s_warp[kFThreads / 32 + 1];
+    __shared__ uint32_t s_red[4 * (kFThreads / 32)];
+    __shared__ uint32_t s_cnt[kBlockStats];
+    __shared__ uint32_t s_w[kFThreads / 32 + 1];
+    __shared__ uint32_t s_tmp[4];
+    __shared__ uint32_t s_n;
+    const uint32_t epoch = ld_volatile(&bt.bg->bar_epoch);
+    uint32_t nbar = 0;
+    auto sync = [&]() {
+        ++nbar;
+        grid_sync(bt.bg, epoch, nbar);
+    };
+    stamp(bt, 0);
+    load_dec6(s_tab);
+    if (threadIdx.x == 0) s_c.b = kNull;
+    phase_prep1(bt, tbits);
+    sync();
+    stamp(bt, 1);
+    phase_classify1(bt, s_c, s_tab, s_cnt, &s_n, reinterpret_cast<uint2*>(s_buf), s_tmp);
+    sync();
+    stamp(bt, 2);
+    const Globals* g = s_c.I.g;
+    const bool all_granted = __ldcg(&g->rq_merge) + __ldcg(&g->rq_split) <= (unsigned long long)s_c.F;
+    if (!all_granted) {
+        phase_gate_sum(bt, s_c, s_cnt, s_red, &s_n, s_buf, true);
+        sync();
+        stamp(bt, 3);
+        phase_gate(bt, s_c, s_cnt, s_red, s_warp, s_tmp, &s_n, reinterpret_cast<uint2*>(s_buf), true);
+        sync();
+    } else {
+        stamp(bt, 3);
+    }
+    stamp(bt, 4);
+    phase_alloc1(bt, s_c, all_granted, tbits, s_cnt, s_warp, s_w, &s_n, s_buf);
+    sync();
+    stamp(bt, 5);
+    phase_fill1(bt, s_c, all_granted, s_cnt, s_buf, s_warp);
+    sync();
+    stamp(bt, 6);
+    const bool cached = vc_form(s_c.fp) && s_c.fp.vout;
+    phase_final1(bt, s_c, s_tab, s_buf, s_vst, s_warp, s_tmp, tbits, s_c.fp.vout && !cached);
+    if (cached) {
+        sync();
+        stamp(bt, 7);
+        phase_vertices(bt, s_c, s_tab, s_buf, &s_n);
+    } else {
+        stamp(bt, 7);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (bt.timing) atomicMax(&bt.bg->t[kFramePhases], global_ns());
+        if (blockIdx.x == 0) {
+            bt.bg->bar_epoch = epoch + nbar * gridDim.x;
+            if (ld_volatile(&bt.bg->abort)) set_err(bt.inst[0].g, kErrTimeout);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_wait_selftest(BatchGlobals* bg, int blocks, int limit, cudaStream_t s) {
@@ -1041,6 +1698,26 @@ int frame_blocks_per_sm() {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame, kFThreads, 0) != cudaSuccess) return 0;
     return n;
+}
+
+int frame1_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame1, kFThreads, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+cudaError_t launch_frame1(const BatchDev& bt, int grid, uint32_t tbits, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(kFThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_frame1, bt, tbits);
 }
 
 cudaError_t launch_frame(const BatchDev& bt, int grid, cudaStream_t s) {

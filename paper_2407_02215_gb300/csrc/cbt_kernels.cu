@@ -442,14 +442,14 @@ __global__ void __launch_bounds__(kThreads) k_fill(BatchDev bt) {
             uint32_t relinked;
             if (c.x & kSplitMask) {
                 clear_bit(I, s);
-                relinked = fill_split(I, s, c.x, c.y);
+                relinked = fill_split(I, s, c.x, c.y, DestPlain{I.g->A});
             } else {
                 const uint4 m = I.grp[i];
                 const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (ms[q] != kNull && !bad_slot(I, ms[q], kErrLink)) clear_bit(I, ms[q]);
-                relinked = fill_merge(I, c.y, m);
+                relinked = fill_merge(I, c.y, m, DestPlain{I.g->A});
             }
             if (relinked) atomicAdd(&s_cnt[0], relinked);
         }

@@ -31,6 +31,15 @@ int launch_index(const Inst& I, const uint32_t* corner, uint32_t cap, void* work
 // cooperative launch over `grid` blocks.
 int frame_blocks_per_sm();
 cudaError_t launch_frame(const BatchDev& bt, int grid, cudaStream_t s);
+// The single-instance frame in fewer phases (cbt_fused.cu); tbits = log2 of
+// the slots under one word tile's sum-tree node, min(2^D, 32 tile words).
+// It holds its scan-tile and word-tile tables in shared memory, so it takes
+// pools of at most kFrame1MaxCap slots with 64-word tiles.
+constexpr uint32_t kFrame1MaxCap = 1u << 22;
+constexpr uint32_t kFrame1TileWords = 64;
+constexpr int kFrame1Phases = 8;
+int frame1_blocks_per_sm();
+cudaError_t launch_frame1(const BatchDev& bt, int grid, uint32_t tbits, cudaStream_t s);
 cudaError_t launch_wait_selftest(BatchGlobals* bg, int blocks, int limit, cudaStream_t s);
 void launch_init(const Inst& I, const int32_t* twin, const int32_t* next, const int32_t* prev,
                  const double* hpos, int grid, cudaStream_t s);

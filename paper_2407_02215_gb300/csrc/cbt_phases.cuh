@@ -455,7 +455,8 @@ __device__ __forceinline__ uint32_t chain_code_bits(uint32_t code) {
     return code == 1u ? kR : (code == 2u ? (kR | kN) : (kR | kP));
 }
 
-static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool scatter, uint4* rec = nullptr) {
+static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool scatter, uint4* rec = nullptr,
+                                      bool check = false) {
     uint32_t cur = b, cost = 2;
     uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, n = 0;
     bool over = false;
@@ -498,9 +499,8 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
             set_err(I.g, kErrChain);
             return done(cost, false);
         }
-        if (scatter) {
-            atomicOr(cmd_ptr(I, t), bits);
-        } else if (depth_of(I.heap[t], I.ch) + 1 != dcur) {
+        if (scatter) atomicOr(cmd_ptr(I, t), bits);
+        if ((!scatter || check) && depth_of(I.heap[t], I.ch) + 1 != dcur) {
             set_err(I.g, kErrChain);
             return done(cost, false);
         }
@@ -559,20 +559,25 @@ __device__ __forceinline__ bool item_wishes(const Inst& I, const FrameP& fp, uin
 // With `cache` (the one-launch frame exporting sphere-form or displaced
 // vertices) the LOD test's vertices go to vc[s] and the command word says so
 // (kVcValid): the export then copies them instead of evaluating them again.
+// With `merge_in` the word is ORed in: it was cleared before the phase and
+// other bisectors' chain walks may mark it while this one classifies.
 __device__ __forceinline__ uint32_t classify_item(const Inst& I, const FrameP& fp, uint64_t key, uint32_t i,
                                                   uint32_t s, uint64_t j, const uint32_t* tab, uint32_t* s_cnt,
-                                                  bool cache = false) {
+                                                  bool cache = false, bool merge_in = false) {
     bool split, merge, kept;
     if (!item_wishes(I, fp, key, s, j, tab, split, merge, cache ? I.vc + 9ull * s : nullptr, &kept)) {
         set_err(I.g, kErrLink);
-        *cmd_ptr(I, s) = 0u;
+        if (!merge_in) *cmd_ptr(I, s) = 0u;
         I.scan[i] = 0u;
         return 0u;
     }
     const int d = depth_of(j, I.ch);
     const uint32_t cmd = (split ? kSplitWish : 0u) | (merge ? kMergeWish : 0u) |
                          ((d & 1) ? kDepthOdd : 0u) | ((j & 1ull) ? kHeapOdd : 0u) | (kept ? kVcValid : 0u);
-    *cmd_ptr(I, s) = cmd;
+    if (merge_in)
+        atomicOr(cmd_ptr(I, s), cmd);
+    else
+        *cmd_ptr(I, s) = cmd;
     // the paper's gate charges 3d + 4 without walking the chain (k_walk
     // computes the exact chain cost otherwise)
     I.scan[i] = (split && fp.gate == 1) ? 3u * (uint32_t)d + 4u : 0u;
@@ -777,10 +782,28 @@ __device__ __forceinline__ void across_load(const Inst& I, const uint4& rx, Acro
     }
 }
 
+__device__ __forceinline__ void set_bit(const Inst& I, uint32_t s) {
+    atomicOr(I.bits + (s >> 5), 1u << (s & 31u));
+}
+__device__ __forceinline__ void clear_bit(const Inst& I, uint32_t s) {
+    atomicAnd(I.bits + (s >> 5), ~(1u << (s & 31u)));
+}
+
+// How the fill reads a destination word and updates the bitfield: here the
+// word is the free-list index itself and A the frame's allocation count
+// (the single-instance frame has a form that resolves tile-local words).
+struct DestPlain {
+    uint32_t A;
+    __device__ __forceinline__ uint32_t operator()(uint32_t d) const { return d; }
+    __device__ __forceinline__ void set(const Inst& I, uint32_t s) const { set_bit(I, s); }
+    __device__ __forceinline__ void clear(const Inst& I, uint32_t s) const { clear_bit(I, s); }
+};
+
 // Resolves old edge E of x (depth parity xodd), whole (hv = false) or by
 // halves: a split neighbour gives the leaf of its family on the same
 // portion, a merged one its parent, an unchanged one itself (R11 reading).
-static __device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, bool xodd) {
+template <typename DM>
+static __device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, bool xodd, const DM& dm) {
     const uint32_t y = a.y[E];
     a.slot[E][0] = a.slot[E][1] = kNull;
     a.rev[E][0] = a.rev[E][1] = 3u;
@@ -788,12 +811,13 @@ static __device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, 
     const int Ep = (int)a.ep[E];
     const uint2 yc = a.yc[E];
     const uint32_t ysb = yc.x & kSplitMask;
-    const uint32_t A = I.g->A;
+    const uint32_t A = dm.A;
     if (Ep > 2) {
         set_err(I.g, kErrLink);
         return;
     }
     if (ysb) {
+        const uint32_t yd = dm(yc.y);
         const bool same = ((yc.x & kDepthOdd) != 0u) == xodd;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // unrolled: a.slot and a.rev stay in registers
@@ -801,19 +825,20 @@ static __device__ void across_resolve(const Inst& I, Across& a, int E, bool hv, 
             int p = hv ? (h == 0 ? kFirst : kSecond) : kWhole;
             if (p != kWhole && same) p = p == kFirst ? kSecond : kFirst;
             uint32_t leaf, edge;
-            if (!family_leaf(ysb, Ep, p, leaf, edge) || yc.y + leaf >= A) {
+            if (!family_leaf(ysb, Ep, p, leaf, edge) || yd + leaf >= A) {
                 set_err(I.g, kErrLink);
                 continue;
             }
-            a.slot[E][h] = I.freel[yc.y + leaf];
+            a.slot[E][h] = I.freel[yd + leaf];
             a.rev[E][h] = edge;
         }
     } else if (yc.x & kMerged) {
-        if (hv || Ep != kT || yc.y >= A) {
+        const uint32_t yd = dm(yc.y);
+        if (hv || Ep != kT || yd >= A) {
             set_err(I.g, kErrLink);
             return;
         }
-        a.slot[E][0] = I.freel[yc.y];
+        a.slot[E][0] = I.freel[yd];
         a.rev[E][0] = (yc.x & kHeapOdd) ? (uint32_t)kNe : (uint32_t)kPe;
     } else {
         if (hv) {
@@ -845,21 +870,17 @@ __device__ __forceinline__ uint32_t push_keep(const Inst& I, const Across& a, in
     return 1u;
 }
 
-__device__ __forceinline__ void set_bit(const Inst& I, uint32_t s) {
-    atomicOr(I.bits + (s >> 5), 1u << (s & 31u));
-}
-__device__ __forceinline__ void clear_bit(const Inst& I, uint32_t s) {
-    atomicAnd(I.bits + (s >> 5), ~(1u << (s & 31u)));
-}
 
-// Both fills return the number of unchanged neighbours relinked.
-static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t dest) {
+// Both fills return the number of unchanged neighbours relinked; dest is
+// the free-list index of the first new record.
+template <typename DM = DestPlain>
+static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, uint32_t dest, const DM& dm) {
     const uint32_t sb = cmd & kSplitMask;
     const int fc = fam_case(sb);
     const uint64_t edges = pick_case(fc, kFamE0, kFamE1, kFamE2, kFamE3);
     const uint32_t misc = pick_case(fc, kFamM0, kFamM1, kFamM2, kFamM3);
     const uint32_t n = misc & 7u;
-    if (dest + n > I.g->A) {
+    if (dest + n > dm.A) {
         set_err(I.g, kErrOverflow);
         return 0u;
     }
@@ -872,7 +893,7 @@ static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, u
     across_load(I, rx, a);
     const bool xodd = (cmd & kDepthOdd) != 0u;
 #pragma unroll
-    for (int E = 0; E < 3; ++E) across_resolve(I, a, E, halves(sb, E), xodd);
+    for (int E = 0; E < 3; ++E) across_resolve(I, a, E, halves(sb, E), xodd, dm);
 #pragma unroll
     for (int l = 0; l < 4; ++l)
         if ((uint32_t)l < n && bad_slot(I, slots[l], kErrOverflow)) return 0u;
@@ -903,7 +924,7 @@ static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, u
         I.nb[slots[l]] = make_uint4(lk[0], lk[1], lk[2], rv);
         I.heap[slots[l]] = (j << sh) + off;
         *cmd_ptr(I, slots[l]) = 0u;  // a new record: no cached vertices
-        set_bit(I, slots[l]);
+        dm.set(I, slots[l]);
     }
     return relinked;
 }
@@ -912,10 +933,11 @@ static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, u
 // Next = across child 2p+1's Twin edge, Prev = across child 2p's Twin edge,
 // Twin = the other parent (Table 1 read backwards, Alg. 6). Members m0, m1
 // are the children of the smaller parent, m2, m3 of the other one.
-static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 m) {
+template <typename DM = DestPlain>
+static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 m, const DM& dm) {
     const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
     const int np = m.z == kNull ? 1 : 2;
-    if (dest + (uint32_t)np > I.g->A) {
+    if (dest + (uint32_t)np > dm.A) {
         set_err(I.g, kErrOverflow);
         return 0u;
     }
@@ -940,8 +962,8 @@ static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 
         const uint4 ra = I.nb[a], rb = I.nb[c1];
         across_load(I, rb, xb);
         across_load(I, ra, xa);
-        across_resolve(I, xb, kT, false, modd);
-        across_resolve(I, xa, kT, false, modd);
+        across_resolve(I, xb, kT, false, modd, dm);
+        across_resolve(I, xa, kT, false, modd, dm);
         relinked += push_keep(I, xb, kT, ps[pk], (uint32_t)kNe);
         relinked += push_keep(I, xa, kT, ps[pk], (uint32_t)kPe);
         const uint32_t tw = np == 2 ? ps[1 - pk] : kNull;
@@ -950,7 +972,7 @@ static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 
                                   rvT | (xb.rev[kT][0] << 2) | (xa.rev[kT][0] << 4));
         I.heap[ps[pk]] = ju >> 1;
         *cmd_ptr(I, ps[pk]) = 0u;  // a new record: no cached vertices
-        set_bit(I, ps[pk]);
+        dm.set(I, ps[pk]);
     }
     return relinked;
 }
