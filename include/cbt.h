@@ -345,10 +345,10 @@ const char* cbt_kernel_name(uint32_t k);
 const char* cbt_phase_name(uint32_t k);
 /* Name of phase k of the state's last timed fused frame. A single instance
  * whose pool has at most 2^22 slots runs a frame of fewer phases (prep,
- * classify, gate_sum, gate, alloc, fill, final, vertices; the two gate
- * phases last 0 when every request of the frame fits the free slots and is
- * granted without a prefix, vertices when the export is computed in final);
- * other fused frames have the phases of cbt_phase_name. */
+ * classify, walks, gate, alloc, fill, final, vertices; gate lasts 0 when
+ * every request of the frame fits the free slots and is granted without a
+ * prefix, vertices when the export is computed in final); other fused
+ * frames have the phases of cbt_phase_name. */
 const char* cbt_state_phase_name(const cbt_state* st, uint32_t k);
 
 /* Update through a CUDA graph (on: the frame's launches are captured once

@@ -31,8 +31,8 @@ constexpr uint32_t kLaunchesPerStep[kNumKernels] = {1, 1, 1, 1, 1, 1, 1, 1, 2, 1
 const char* const kPhaseNames[kFramePhases] = {"prep",  "classify", "gate_sum", "gate",    "alloc_sum",
                                                "alloc", "fill",     "reduce",   "compact", "vertices"};
 // phases of the single-instance frame (k_frame1)
-const char* const kPhaseNames1[kFrame1Phases] = {"prep", "classify", "gate_sum", "gate",
-                                                 "alloc", "fill",     "final",    "vertices"};
+const char* const kPhaseNames1[kFrame1Phases] = {"prep",  "classify", "walks", "gate",
+                                                 "alloc", "fill",     "final", "vertices"};
 constexpr uint32_t kFusedTileWords = 64;
 constexpr uint32_t kFusedMaxTileWords = 128;
 

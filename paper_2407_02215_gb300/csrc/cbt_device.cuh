@@ -53,6 +53,11 @@ constexpr uint32_t kHeapOdd = 1u << 8;
 constexpr uint32_t kCand = 1u << 9;    // smallest member of a mergeable group (members in grp[i])
 constexpr uint32_t kGrpMin = 1u << 10; // smallest member of a merge group whose members are in grp[i]
 constexpr uint32_t kVcValid = 1u << 11; // vc[slot] holds this frame's vertices (sphere or displaced form, one-launch frame)
+// scan word of a live index: split cost in bits 0-23, merge cost in bits
+// 24-30, and (single-instance frame) bit 31 when the split's chain has more
+// members than its record keeps
+constexpr uint32_t kScanMore = 1u << 31;
+constexpr uint32_t kMergeCostMask = 0x7Fu;
 
 // Edge indices of a bisector: Twin (v0,v1), Next (v1,v2), Prev (v2,v0).
 constexpr int kT = 0, kNe = 1, kPe = 2;
@@ -88,11 +93,14 @@ struct Globals {
     unsigned long long pc_gen;     // sphere-point cache generation (0: none made yet)
     unsigned long long pc_radius;  // the shape it was made with: radius (FP64 bits),
     uint32_t pc_damp, pc_dfreq, pc_doct, pc_dseed;  // displacement (FP32 bits)
-    // single-instance frame: the frame's requested merge cost (over every
-    // recorded group) and split cost, summed in classify; when their sum fits
-    // the free slots every request is granted without the prefix gate
+    // single-instance frame: the frame's merge cost (groups whose members all
+    // wish to merge) and requested split cost, summed by the walks; when their
+    // sum fits the free slots every request is granted without the prefix gate
     unsigned long long rq_merge, rq_split;
-    uint32_t pad[64 - 36];
+    uint32_t nwalk;  // single-instance frame: entries of the frame's walk list
+    uint32_t marks_clean;  // 1 when the chain-mark words (chg) of the live slots are 0 (the
+                           // single-instance frame leaves them so; the other frames clear this)
+    uint32_t pad[64 - 38];
 };
 static_assert(sizeof(Globals) == 256, "Globals must be 256 bytes");
 static_assert(10 + kStCount + 1 == 24, "pc_gen must sit at byte 96");
@@ -222,20 +230,22 @@ __device__ __forceinline__ void set_err(Globals* g, uint32_t e) { atomicOr(&g->e
 // Integer form of Alg. 2 evaluated from the first split down: with W the
 // weights over 2^k after k levels, a 0 bit maps the rows (r0, r1, r2) to
 // (2 r0, 2 r2, r0 + r1) and a 1 bit to (2 r2, 2 r1, r0 + r1) (Eq. 1 times 2),
-// i.e. W <- T_b W with T_0 = 2 M_0 and T_1 = 2 M_1. Six levels at once are
-// W <- P_c W with P_c = T_{c0} T_{c1} ... T_{c5} for the six path bits c
-// (most significant applied first), precomputed below for all 64 c; every
-// entry of P_c is at most 64. W = 2^d M exactly while entries fit T (T = u32
-// for d <= 31).
+// i.e. W <- T_b W with T_0 = 2 M_0 and T_1 = 2 M_1. Eight levels at once are
+// W <- P_c W with P_c = T_{c7} T_{c6} ... T_{c0} for the eight path bits c
+// (most significant applied first), precomputed below for all 256 c; every
+// entry of P_c is at most 2^8 (16 bits). Every row of W sums to 2^k (the
+// rows of M are barycentric), so only the first two columns are carried
+// and the third is 2^k minus them. W = 2^d M exactly while entries fit T
+// (T = u32 for d <= 31).
 struct DecTable {
-    uint32_t p[64][9];
+    uint16_t p[256][9];
 };
 
-constexpr DecTable make_dec6() {
+constexpr DecTable make_dec8() {
     DecTable t{};
-    for (int c = 0; c < 64; ++c) {
+    for (int c = 0; c < 256; ++c) {
         uint32_t m[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-        for (int k = 5; k >= 0; --k) {
+        for (int k = 7; k >= 0; --k) {
             const int b = (c >> k) & 1;
             uint32_t n[9] = {};
             for (int col = 0; col < 3; ++col) {
@@ -245,68 +255,86 @@ constexpr DecTable make_dec6() {
             }
             for (int e = 0; e < 9; ++e) m[e] = n[e];
         }
-        for (int e = 0; e < 9; ++e) t.p[c][e] = m[e];
+        for (int e = 0; e < 9; ++e) t.p[c][e] = static_cast<uint16_t>(m[e]);
     }
     return t;
 }
 
-__constant__ DecTable c_dec6 = make_dec6();
+__constant__ DecTable c_dec8 = make_dec8();
+constexpr uint32_t kDecTabWords = 256u * 9u / 2u;  // the table in 32-bit words
 
-// Copies the six-level table into shared memory (call with the whole block,
-// then __syncthreads()).
+// Copies the eight-level table into shared memory (kDecTabWords words; call
+// with the whole block, then __syncthreads()).
 __device__ __forceinline__ void load_dec6(uint32_t* s_tab) {
-    const uint32_t* src = &c_dec6.p[0][0];
-    for (uint32_t k = threadIdx.x; k < 64u * 9u; k += blockDim.x) s_tab[k] = src[k];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&c_dec8.p[0][0]);
+    for (uint32_t k = threadIdx.x; k < kDecTabWords; k += blockDim.x) s_tab[k] = src[k];
 }
 
+// One level on the first two columns, a[2 r + c] (c = 0, 1).
 template <typename T>
-__device__ __forceinline__ void dec_step(T a[9], bool b) {
-    T n[9];
+__device__ __forceinline__ void dec_step(T a[6], bool b) {
+    T n[6];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        n[6 + c] = a[c] + a[3 + c];
-        n[c] = (b ? a[6 + c] : a[c]) << 1;
-        n[3 + c] = (b ? a[3 + c] : a[6 + c]) << 1;
+    for (int c = 0; c < 2; ++c) {
+        n[4 + c] = a[c] + a[2 + c];
+        n[c] = (b ? a[4 + c] : a[c]) << 1;
+        n[2 + c] = (b ? a[2 + c] : a[4 + c]) << 1;
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) a[k] = n[k];
+    for (int k = 0; k < 6; ++k) a[k] = n[k];
 }
 
 template <typename T>
-__device__ __forceinline__ void dec_chunk(T a[9], const uint32_t* P) {
-    T n[9];
+__device__ __forceinline__ void dec_chunk(T a[6], const uint16_t* P) {
+    T n[6];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const T p0 = P[3 * r], p1 = P[3 * r + 1], p2 = P[3 * r + 2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) n[3 * r + c] = p0 * a[c] + p1 * a[3 + c] + p2 * a[6 + c];
+        for (int c = 0; c < 2; ++c) n[2 * r + c] = p0 * a[c] + p1 * a[2 + c] + p2 * a[4 + c];
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) a[k] = n[k];
+    for (int k = 0; k < 6; ++k) a[k] = n[k];
+}
+
+// The 3 x 3 weights from the first two columns at 2^k.
+template <typename T>
+__device__ __forceinline__ void dec_expand(const T a[6], T pw, T W[9]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        W[3 * r] = a[2 * r];
+        W[3 * r + 1] = a[2 * r + 1];
+        W[3 * r + 2] = pw - a[2 * r] - a[2 * r + 1];
+    }
 }
 
 // W = weights of bisector j at depth d, Wp = those of its parent (d >= 1);
-// tab = the six-level table in shared memory.
+// tab = the eight-level table in shared memory.
 template <typename T>
 __device__ __forceinline__ void decode_weights(uint64_t j, int d, T W[9], T Wp[9], const uint32_t* tab) {
-    T a[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const uint16_t* tab16 = reinterpret_cast<const uint16_t*>(tab);
+    T a[6] = {1, 0, 0, 1, 0, 0};
     if (d >= 1) {
         int lvl = d - 1;  // path bit applied next; the parent covers bits d-1 .. 1
-        const int rem = (d - 1) % 6;
+        const int rem = (d - 1) & 7;
 #pragma unroll 1
         for (int k = 0; k < rem; ++k, --lvl) dec_step<T>(a, (j >> lvl) & 1ull);
 #pragma unroll 1
-        for (; lvl >= 6; lvl -= 6) dec_chunk<T>(a, tab + 9u * (uint32_t)((j >> (lvl - 5)) & 63ull));
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Wp[k] = a[k];
+        for (; lvl >= 8; lvl -= 8) dec_chunk<T>(a, tab16 + 9u * (uint32_t)((j >> (lvl - 7)) & 255ull));
+        dec_expand<T>(a, (T)1 << (d - 1), Wp);
         dec_step<T>(a, j & 1ull);
     } else {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Wp[k] = a[k];
+        dec_expand<T>(a, (T)1, Wp);
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) W[k] = a[k];
+    dec_expand<T>(a, (T)1 << d, W);
 }
+
+// Round-to-nearest conversion of a weight to FP32 / FP64 (exact below 2^24 /
+// 2^53; the 32-bit forms for 32-bit weights).
+__device__ __forceinline__ float wfloat(uint32_t w) { return __uint2float_rn(w); }
+__device__ __forceinline__ float wfloat(unsigned long long w) { return __ull2float_rn(w); }
+__device__ __forceinline__ double wdouble(uint32_t w) { return __uint2double_rn(w); }
+__device__ __forceinline__ double wdouble(unsigned long long w) { return __ull2double_rn(w); }
 
 // Correctly rounded signed 128-bit integer -> float: shift down to 63
 // significant bits with a sticky bit (round to odd), then one RN conversion.
@@ -438,9 +466,9 @@ template <typename T>
 __device__ __forceinline__ void sphere_point(const T W[9], int v, int d, const FrameP& fp, const double* V,
                                              double pf[4]) {
     const double sc = pow2d(-d);
-    const double w0 = __dmul_rn(__ull2double_rn(W[3 * v + 0]), sc);
-    const double w1 = __dmul_rn(__ull2double_rn(W[3 * v + 1]), sc);
-    const double w2 = __dmul_rn(__ull2double_rn(W[3 * v + 2]), sc);
+    const double w0 = __dmul_rn(wdouble(W[3 * v + 0]), sc);
+    const double w1 = __dmul_rn(wdouble(W[3 * v + 1]), sc);
+    const double w2 = __dmul_rn(wdouble(W[3 * v + 2]), sc);
     double p[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) p[c] = __fma_rn(w2, V[6 + c], __fma_rn(w1, V[3 + c], __dmul_rn(w0, V[c])));
@@ -489,9 +517,9 @@ __device__ __forceinline__ void eval_vertex(const T W[9], int v, int d, const Fr
     } else if (precision == 2) {
         const double* Dp = static_cast<const double*>(rel) + 9u * h;
         const double sc = pow2d(-d);
-        const double w0 = __dmul_rn(__ull2double_rn(W[3 * v + 0]), sc);
-        const double w1 = __dmul_rn(__ull2double_rn(W[3 * v + 1]), sc);
-        const double w2 = __dmul_rn(__ull2double_rn(W[3 * v + 2]), sc);
+        const double w0 = __dmul_rn(wdouble(W[3 * v + 0]), sc);
+        const double w1 = __dmul_rn(wdouble(W[3 * v + 1]), sc);
+        const double w2 = __dmul_rn(wdouble(W[3 * v + 2]), sc);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double t = __dadd_rn(__dadd_rn(__dmul_rn(w0, Dp[c]), __dmul_rn(w1, Dp[3 + c])),
@@ -501,9 +529,9 @@ __device__ __forceinline__ void eval_vertex(const T W[9], int v, int d, const Fr
     } else {
         const float* R = static_cast<const float*>(rel) + 9u * h;
         const float sc = pow2f(-d);
-        const float w0 = __fmul_rn(__ull2float_rn(W[3 * v + 0]), sc);
-        const float w1 = __fmul_rn(__ull2float_rn(W[3 * v + 1]), sc);
-        const float w2 = __fmul_rn(__ull2float_rn(W[3 * v + 2]), sc);
+        const float w0 = __fmul_rn(wfloat(W[3 * v + 0]), sc);
+        const float w1 = __fmul_rn(wfloat(W[3 * v + 1]), sc);
+        const float w2 = __fmul_rn(wfloat(W[3 * v + 2]), sc);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             r[c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])), __fmul_rn(w2, R[6 + c]));
@@ -536,9 +564,9 @@ __device__ __forceinline__ void eval_vertices(const T W[9], int d, const FrameP&
         const double sc = pow2d(-d);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const double w0 = __dmul_rn(__ull2double_rn(W[3 * i + 0]), sc);
-            const double w1 = __dmul_rn(__ull2double_rn(W[3 * i + 1]), sc);
-            const double w2 = __dmul_rn(__ull2double_rn(W[3 * i + 2]), sc);
+            const double w0 = __dmul_rn(wdouble(W[3 * i + 0]), sc);
+            const double w1 = __dmul_rn(wdouble(W[3 * i + 1]), sc);
+            const double w2 = __dmul_rn(wdouble(W[3 * i + 2]), sc);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const double t = __dadd_rn(__dadd_rn(__dmul_rn(w0, Dp[c]), __dmul_rn(w1, Dp[3 + c])),
@@ -551,9 +579,9 @@ __device__ __forceinline__ void eval_vertices(const T W[9], int d, const FrameP&
         const float sc = pow2f(-d);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const float w0 = __fmul_rn(__ull2float_rn(W[3 * i + 0]), sc);
-            const float w1 = __fmul_rn(__ull2float_rn(W[3 * i + 1]), sc);
-            const float w2 = __fmul_rn(__ull2float_rn(W[3 * i + 2]), sc);
+            const float w0 = __fmul_rn(wfloat(W[3 * i + 0]), sc);
+            const float w1 = __fmul_rn(wfloat(W[3 * i + 1]), sc);
+            const float w2 = __fmul_rn(wfloat(W[3 * i + 2]), sc);
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 r[3 * i + c] = __fadd_rn(__fadd_rn(__fmul_rn(w0, R[c]), __fmul_rn(w1, R[3 + c])), __fmul_rn(w2, R[6 + c]));
@@ -564,29 +592,36 @@ __device__ __forceinline__ void eval_vertices(const T W[9], int d, const FrameP&
     }
 }
 
-// LOD reading: bit0 visible (no plane has all three vertices strictly on its
-// negative side), bit1 big (|v1 - v0|^2 q > |(v0 + v1)/2|^2).
-__device__ __forceinline__ uint32_t lod_test(const float r[9], const FrameP& fp) {
-    uint32_t vis = 1u;
-    for (uint32_t p = 0; p < fp.nplanes; ++p) {
-        bool all_out = true;
+// LOD reading: a triangle is visible unless one plane has all three
+// vertices strictly on its negative side, where a vertex r is on the
+// negative side of plane n when (n.x r.x + n.y r.y) + n.z r.z < 0; it is
+// big when |v1 - v0|^2 q > |(v0 + v1)/2|^2.
+// The planes on whose negative side vertex r lies, as a bit mask.
+__device__ __forceinline__ uint32_t plane_mask(const float* r, const FrameP& fp) {
+    uint32_t m = 0u;
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            const float s = __fadd_rn(__fadd_rn(__fmul_rn(fp.planes[3 * p], r[3 * v]),
-                                                __fmul_rn(fp.planes[3 * p + 1], r[3 * v + 1])),
-                                      __fmul_rn(fp.planes[3 * p + 2], r[3 * v + 2]));
-            all_out = all_out && (s < 0.0f);
-        }
-        if (all_out) vis = 0u;
+    for (uint32_t p = 0; p < 5u; ++p) {
+        if (p >= fp.nplanes) break;
+        const float s = __fadd_rn(__fadd_rn(__fmul_rn(fp.planes[3 * p], r[0]), __fmul_rn(fp.planes[3 * p + 1], r[1])),
+                                  __fmul_rn(fp.planes[3 * p + 2], r[2]));
+        m |= (s < 0.0f ? 1u : 0u) << p;
     }
-    const float ex = __fsub_rn(r[3], r[0]), ey = __fsub_rn(r[4], r[1]), ez = __fsub_rn(r[5], r[2]);
-    const float mx = __fmul_rn(0.5f, __fadd_rn(r[0], r[3]));
-    const float my = __fmul_rn(0.5f, __fadd_rn(r[1], r[4]));
-    const float mz = __fmul_rn(0.5f, __fadd_rn(r[2], r[5]));
+    return m;
+}
+// |a - b|^2 q > |(a + b)/2|^2 for the refinement edge (a, b).
+__device__ __forceinline__ bool edge_big(const float* a, const float* b, float q) {
+    const float ex = __fsub_rn(b[0], a[0]), ey = __fsub_rn(b[1], a[1]), ez = __fsub_rn(b[2], a[2]);
+    const float mx = __fmul_rn(0.5f, __fadd_rn(a[0], b[0]));
+    const float my = __fmul_rn(0.5f, __fadd_rn(a[1], b[1]));
+    const float mz = __fmul_rn(0.5f, __fadd_rn(a[2], b[2]));
     const float L2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
     const float R2 = __fadd_rn(__fadd_rn(__fmul_rn(mx, mx), __fmul_rn(my, my)), __fmul_rn(mz, mz));
-    const uint32_t big = __fmul_rn(L2, fp.q) > R2 ? 1u : 0u;
-    return vis | (big << 1);
+    return __fmul_rn(L2, q) > R2;
+}
+// bit0 visible, bit1 big.
+__device__ __forceinline__ uint32_t lod_test(const float r[9], const FrameP& fp) {
+    const uint32_t out = plane_mask(r, fp) & plane_mask(r + 3, fp) & plane_mask(r + 6, fp);
+    return (out == 0u ? 1u : 0u) | (edge_big(r, r + 3, fp.q) ? 2u : 0u);
 }
 
 __device__ __forceinline__ bool in_sorted(const uint64_t* a, uint32_t n, uint64_t x) {

@@ -197,6 +197,7 @@ __device__ void phase_prep(const BatchDev& bt, Pair* s_warp, uint32_t* s_tmp) {
                 g->Stot = 0;
                 g->C = 0;
                 g->done = 0;
+                g->marks_clean = 0;
                 tiles = (N + kTileItems - 1u) / kTileItems;
                 stiles = (N + S - 1u) / S;
                 g->ntiles = tiles;
@@ -434,7 +435,7 @@ __device__ uint32_t crossing_mg(const BatchDev& bt, const FCtx& c, uint32_t F, u
     uint32_t loc = 0;
 #pragma unroll
     for (uint32_t k = 0; k < kMaxIpt; ++k) {
-        mc[k] = (k < ipt && i0 + k < c.N) ? (__ldcg(I.scan + i0 + k) >> 24) : 0u;
+        mc[k] = (k < ipt && i0 + k < c.N) ? ((__ldcg(I.scan + i0 + k) >> 24) & kMergeCostMask) : 0u;
         loc += mc[k];
     }
     Pair tot;
@@ -465,6 +466,14 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         ctx_tile(bt, bt.stile_base, t, T, c);
         const Inst& I = c.I;
         const uint32_t N = c.N, F = c.F;
+        const uint32_t i0 = stile_first(c, ipt);
+        uint32_t sl[kMaxIpt], w[kMaxIpt];
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k) {  // loaded before the tile sums, which do not need them
+            const bool in = k < ipt && i0 + k < N;
+            sl[k] = in ? I.live[i0 + k] : kNull;
+            w[k] = in ? I.scan[i0 + k] : 0u;
+        }
         Pair before, all;
         tile_sums(bt.status, c, before, all, s_red);
         const uint32_t Mg = all.a <= F ? all.a : crossing_mg(bt, c, F, ipt, s_warp, s_tmp);
@@ -472,49 +481,58 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
             I.g->Mg = Mg;
             I.g->Stot = all.b;
         }
-        const uint32_t i0 = stile_first(c, ipt);
-        uint32_t sl[kMaxIpt], w[kMaxIpt];
         Pair loc{0, 0};
 #pragma unroll
-        for (uint32_t k = 0; k < kMaxIpt; ++k) {
-            const bool in = k < ipt && i0 + k < N;
-            sl[k] = in ? I.live[i0 + k] : kNull;
-            w[k] = in ? I.scan[i0 + k] : 0u;
-            loc = padd(loc, Pair{w[k] >> 24, w[k] & 0xFFFFFFu});
-        }
+        for (uint32_t k = 0; k < kMaxIpt; ++k) loc = padd(loc, Pair{(w[k] >> 24) & kMergeCostMask, w[k] & 0xFFFFFFu});
         Pair tot;
         const Pair tex = block_scan(loc, tot, s_warp);
         Pair run = padd(before, tex);
 #pragma unroll
         for (uint32_t k = 0; k < kMaxIpt; ++k) {
-            const uint32_t mc = w[k] >> 24, sc = w[k] & 0xFFFFFFu;
+            const uint32_t mc = (w[k] >> 24) & kMergeCostMask, sc = w[k] & 0xFFFFFFu;
             run = padd(run, Pair{mc, sc});
             if (sl[k] == kNull) continue;
             const bool mgrant = mc > 0u && run.a <= F;
             if (mc) atomicOr(cmd_ptr(I, sl[k]), mgrant ? (kCand | kMergeGrant) : kCand);
             count_stat(s_cnt, 0, mgrant);
-            // a split wish, and only a split wish, has a nonzero split cost
+            // a split wish, and only a split wish, has a nonzero split cost;
+            // bit 31 of the list's live index: its chain continues past the
+            // recorded members
             const bool sgrant = sc > 0u && (uint64_t)Mg + (uint64_t)run.b <= F;
-            if (sgrant) s_list[atomicAdd(s_n, 1u)] = make_uint2(i0 + k, sl[k]);
+            if (sgrant) s_list[atomicAdd(s_n, 1u)] = make_uint2((i0 + k) | (w[k] & kScanMore), sl[k]);
             count_stat(s_cnt, 1, sgrant);
         }
         __syncthreads();
         const uint32_t n = *s_n;
         // the paper's gate charges 3d + 4 without a walk (the single-instance
-        // frame walks, and records, every chain)
+        // frame walks, and records, every chain that can be granted); the
+        // records of four grants are loaded before their marks go out
         const bool recorded = always_recorded || c.fp.gate != 1;
-        for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
-            const uint2 e = s_list[q];
-            const uint4 r = recorded ? I.grp[e.x] : make_uint4(kNull, kNull, kNull, kNull);
-            if (r.x == kNull && r.w == kNull) {
-                chain_walk(I, e.y, 0, true);
-                continue;
-            }
-            atomicOr(cmd_ptr(I, e.y), kR);
-            const uint32_t m[4] = {r.x, r.y, r.z, r.w};
+        for (uint32_t q0 = threadIdx.x; q0 < n; q0 += 4u * kFThreads) {
+            uint2 e[4];
+            uint4 r[4];
 #pragma unroll
-            for (uint32_t q2 = 0; q2 < 4; ++q2)
-                if (m[q2] >> 30) atomicOr(cmd_ptr(I, m[q2] & 0x3FFFFFFFu), chain_code_bits(m[q2] >> 30));
+            for (uint32_t k = 0; k < 4; ++k) {
+                const uint32_t q = q0 + k * kFThreads;
+                e[k] = q < n ? s_list[q] : make_uint2(0u, kNull);
+                r[k] = (q < n && recorded) ? I.grp[e[k].x & ~kScanMore] : make_uint4(kNull, kNull, kNull, kNull);
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k) {
+                if (e[k].y == kNull) continue;
+                if (r[k].x == kNull && r[k].w == kNull) {
+                    chain_walk(I, e[k].y, 0, true);
+                    continue;
+                }
+                atomicOr(cmd_ptr(I, e[k].y), kR);
+                const uint32_t m[4] = {r[k].x, r[k].y, r[k].z, r[k].w};
+#pragma unroll
+                for (uint32_t q2 = 0; q2 < 4; ++q2)
+                    if (m[q2] >> 30) atomicOr(cmd_ptr(I, m[q2] & 0x3FFFFFFFu), chain_code_bits(m[q2] >> 30));
+                // a longer chain goes on from its fourth member (the walk
+                // from there is the rest of the chain)
+                if ((e[k].x & kScanMore) && (m[3] >> 30)) chain_walk(I, m[3] & 0x3FFFFFFFu, 0, true);
+            }
         }
         __syncthreads();
         stats_flush(s_cnt, I.g, kStMergeGranted, kStSplitGranted);
@@ -522,7 +540,8 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
     }
 }
 
-__device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_granted);
+__device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_granted,
+                          const unsigned long long* tcounts = nullptr);
 
 // P4: the fate of every item after the chains are marked (kept in its scan
 // word for P5) and per tile the sums of (changed, allocations); then the
@@ -576,7 +595,11 @@ __device__ void phase_alloc_sum(const BatchDev& bt, FCtx& c, uint32_t* s_red, ui
 // slots or, when smaller, the granted merge cost plus the requested split
 // cost (all requests with `all_granted`), an upper bound of the
 // allocations.
-__device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_granted) {
+// With `tcounts` (single instance, word tiles of the frame's tile counts)
+// the ones before a word tile are summed over the block from those counts
+// instead of read down the sum tree one level at a time.
+__device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_granted,
+                          const unsigned long long* tcounts) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (uint32_t wt = blockIdx.x; wt < bt.Twords; wt += gridDim.x) {
         ctx_tile(bt, bt.wtile_base, wt, bt.Twords, c);
@@ -588,8 +611,19 @@ __device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_g
         const uint32_t TW = min(I.W, bt.tw);
         const uint32_t nt = I.W / TW;
         uint32_t ones_before = 0;
-        for (uint32_t n = nt + lt; n > 1; n >>= 1)
-            if (n & 1u) ones_before += I.sums[n - 1];
+        if (tcounts) {
+            uint32_t part = 0;
+            for (uint32_t t = threadIdx.x; t < lt; t += blockDim.x) part += (uint32_t)(__ldcg(tcounts + t) >> 32);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+            if (lane == 0) s_w[warp] = part;
+            __syncthreads();
+            for (int q = 0; q < nw; ++q) ones_before += s_w[q];
+            __syncthreads();
+        } else {
+            for (uint32_t n = nt + lt; n > 1; n >>= 1)
+                if (n & 1u) ones_before += I.sums[n - 1];
+        }
         const uint64_t zeros_before = (uint64_t)lt * TW * 32u - ones_before;
         if (zeros_before < bound) {  // block-uniform
             const uint32_t w = lt * TW + threadIdx.x;
@@ -982,7 +1016,7 @@ __device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_ta
 
 __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame(BatchDev bt) {
     __shared__ FCtx s_c;
-    __shared__ uint32_t s_tab[64 * 9];
+    __shared__ uint32_t s_tab[kDecTabWords];
     __shared__ __align__(16) uint32_t s_buf[kFBuf];
     __shared__ Pair s_warp[kFThreads / 32 + 1];
     __shared__ uint32_t s_red[4 * (kFThreads / 32)];
@@ -1050,20 +1084,26 @@ __global__ void __launch_bounds__(kFThreads) k_wait_selftest(BatchGlobals* bg, i
 // ===================================================== one instance, fewer phases
 //
 // k_frame1: the frame of a single instance (a batch of one), with the same
-// results as k_frame in five phases when the frame's requests all fit the
-// free slots, and seven when some may not:
-//   P0 prep      frame counters; the camera-relative roots; the command words
-//                of the live slots cleared
-//   P1 classify  wishes, ORed into the command words; the walks: a split
-//                wish's chain walk also marks its chain (command form of
-//                Alg. 3), a group walk records the group at its smallest
-//                member; the frame's requested merge cost (every recorded
-//                group) and split cost
-//   when requested merges plus splits exceed the free slots F:
-//   P2 gate-sum  the chain marks cleared; per-tile (merge, split) cost sums
-//   P3 gate      grants in the order of the R6 reading, and chain marking
-//   otherwise every request is granted (the prefix gate would grant them
-//   all) and the marks of P1 stand;
+// results as k_frame in six phases, or five when the frame's requests all
+// fit the free slots:
+//   P0 prep      frame counters; the camera-relative roots; the chain-mark
+//                words of the live slots and the tile counters cleared
+//   P1 classify  wishes (Sec. 3.3 GenerateCommands), balanced over the grid;
+//                the items that need a walk appended to the frame's walk
+//                list; split wishes counted per scan tile
+//   P2 walks     the walk list spread evenly over the grid. A split wish's
+//                chain (command form of Alg. 3) is walked, recorded and
+//                marked (into the chain-mark words) unless the split wishes
+//                before its scan tile already cost more than the free slots
+//                at 2 each, so that the gate denies it whatever its cost. A
+//                merge wish with an even heap ID walks its Alg. 4 group while
+//                it can be a merge candidate with this wish its smallest
+//                member, which then records it with its merge cost. Per scan
+//                tile the (merge, split) cost sums, per frame their totals.
+//   P3 gate      (when the totals exceed the free slots F) grants in the
+//                order of the R6 reading and chain marking into the command
+//                words; otherwise every request is granted and the chain-mark
+//                words hold the marks
 //   P4 alloc     fates, their tile-local allocation prefix (a destination
 //                word holds the tile and the offset within it), the fill
 //                records per tile, the bits cleared per word tile, the free
@@ -1099,22 +1139,85 @@ struct DestTiles {
 __device__ __forceinline__ unsigned long long* tile_counts(const BatchDev& bt) {
     return bt.status + 2u * bt.Titems;
 }
+// Per scan tile: the split wishes (P1), then the allocation sums (P4).
+__device__ __forceinline__ unsigned long long* wish_counts(const BatchDev& bt) { return bt.status + bt.Titems; }
+// The chain marks of P2 (one word per slot; the per-step frame's list of
+// changed items uses the same array).
+__device__ __forceinline__ uint32_t* chain_marks(const Inst& I) { return I.chg; }
+// The frame's walk list, in the fill records' array (written only in P4):
+// per entry {live index | split flag << 31, slot, heap ID low, high}.
+__device__ __forceinline__ uint4* walk_list_of(const Inst& I) { return I.chgr; }
+constexpr uint32_t kWalkCap1 = kFBuf / 4;  // uint4 entries of the block's list
+
+// Alg. 4 group of s1 (heap ID j1, a merge wish) on the frame-start state,
+// walked only while s1 can be its smallest member and every member wishes
+// to merge: true when both hold, with the members (m[0] = s1, m[1] its
+// sibling, m[2] the bisector across the outer half of the refinement edge,
+// m[3] its sibling) and the parents' count.
+static __device__ bool group_if_mergeable(const Inst& I, uint32_t s1, uint64_t j1, Group& g) {
+    if (depth_of(j1, I.ch) < 1) return false;
+    const uint4 r1 = I.nb[s1];
+    const bool bit = j1 & 1ull;
+    const uint32_t s2 = bit ? r1.z : r1.y;
+    const uint32_t s3 = bit ? r1.y : r1.z;
+    if (s2 == kNull || bad_slot(I, s2, kErrLink)) return false;
+    if (s3 != kNull && bad_slot(I, s3, kErrLink)) return false;
+    const uint64_t j2 = I.heap[s2];
+    const uint32_t c2 = *cmd_ptr(I, s2);
+    uint64_t j3 = 0ull;
+    uint4 r3 = make_uint4(kNull, kNull, kNull, 0u);
+    uint32_t c3 = 0u;
+    if (s3 != kNull) {
+        j3 = I.heap[s3];
+        r3 = I.nb[s3];
+        c3 = *cmd_ptr(I, s3);
+    }
+    if ((j2 >> 1) != (j1 >> 1) || j2 < j1 || !(c2 & kMergeWish)) return false;
+    g.m[0] = s1;
+    g.m[1] = s2;
+    g.m[2] = g.m[3] = kNull;
+    g.n = 2;
+    g.np = 1;
+    g.imin = 0;
+    if (s3 != kNull) {
+        // the other pair's smaller member is its even one
+        if (bitlen64(j3) != bitlen64(j1) || (j3 >> 1) == (j1 >> 1) || (j3 & ~1ull) < j1 || !(c3 & kMergeWish))
+            return false;
+        const uint32_t s4 = bit ? r3.y : r3.z;
+        if (s4 == kNull || bad_slot(I, s4, kErrLink)) return false;
+        const uint64_t j4 = I.heap[s4];
+        const uint32_t c4 = *cmd_ptr(I, s4);
+        if ((j4 >> 1) != (j3 >> 1) || !(c4 & kMergeWish)) return false;
+        g.m[2] = s3;
+        g.m[3] = s4;
+        g.n = 4;
+        g.np = 2;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t scan_ipt1(uint32_t N) {
+    const uint32_t per_round = gridDim.x * kFThreads;
+    return min(kMaxIpt, max(kMinIpt, (N + per_round - 1u) / per_round));
+}
 
 // P0 (single instance). The frame counters are set by block 0; every block
-// reads the live count itself. The command words of the live slots are
-// cleared: classify ORs its bits in while other walks may mark them.
+// reads the live count itself. The chain-mark words of the live slots are
+// cleared unless the last frame (this kernel) left them 0.
 __device__ void phase_prep1(const BatchDev& bt, uint32_t tbits) {
     const Inst& I = bt.inst[0];
     const FrameP& fp = frame_of(bt, 0);
     const uint32_t N = __ldcg(I.sums + 1);
     const uint32_t nt = I.cap >> tbits;
+    const uint32_t ipt = scan_ipt1(N), S = ipt * kFThreads, T = (N + S - 1u) / S;
+    const uint32_t gt = blockIdx.x * kFThreads + threadIdx.x, stride = gridDim.x * kFThreads;
     unsigned long long* tc = tile_counts(bt);
-    for (uint32_t t = blockIdx.x * kFThreads + threadIdx.x; t < nt; t += gridDim.x * kFThreads)
-        tc[t] = (unsigned long long)__ldcg(I.sums + nt + t) << 32;
+    for (uint32_t t = gt; t < nt; t += stride) tc[t] = (unsigned long long)__ldcg(I.sums + nt + t) << 32;
+    for (uint32_t t = gt; t < T; t += stride) {
+        bt.status[t] = 0ull;
+        wish_counts(bt)[t] = 0ull;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const uint32_t per_round = gridDim.x * kFThreads;
-        const uint32_t ipt = min(kMaxIpt, max(kMinIpt, (N + per_round - 1u) / per_round));
-        const uint32_t S = ipt * kFThreads;
         Globals* g = I.g;
         g->N = N;
         g->F = I.cap - N;
@@ -1124,21 +1227,22 @@ __device__ void phase_prep1(const BatchDev& bt, uint32_t tbits) {
         g->C = 0;
         g->done = 0;
         g->ntiles = (N + kTileItems - 1u) / kTileItems;
-        g->nstiles = (N + S - 1u) / S;
+        g->nstiles = T;
         for (int k = 0; k < kStCount; ++k) g->stats[k] = 0;
         g->stats[kStLiveBefore] = N;
         g->stats[kStFreeBefore] = I.cap - N;
         g->stats[kStFrame] = fp.frame;
         g->rq_merge = 0;
         g->rq_split = 0;
+        g->nwalk = 0;
         pc_generation(g, fp);
         if (bt.nout) bt.nout[0] = N;
         bt.tile_base[0] = 0;
         bt.tile_base[1] = g->ntiles;
         bt.stile_base[0] = 0;
-        bt.stile_base[1] = g->nstiles;
+        bt.stile_base[1] = T;
         bt.bg->total_tiles = g->ntiles;
-        bt.bg->total_stiles = g->nstiles;
+        bt.bg->total_stiles = T;
         bt.bg->scan_ipt = ipt;
         bt.bg->live_total = N;
         bt.bg->t[kFramePhases] = 0;
@@ -1146,55 +1250,44 @@ __device__ void phase_prep1(const BatchDev& bt, uint32_t tbits) {
     const uint32_t nw = gridDim.x * (kFThreads / 32), wid = blockIdx.x * (kFThreads / 32) + threadIdx.x / 32u;
     const uint32_t per = min(kRelRange, ((bt.Trel + nw - 1u) / nw + 31u) & ~31u);
     for (uint32_t e = wid * per; e < bt.Trel; e += nw * per) rel_range(bt, e, min(bt.Trel, e + per));
-    for (uint32_t i = blockIdx.x * kFThreads + threadIdx.x; i < N; i += gridDim.x * kFThreads)
-        *cmd_ptr(I, __ldcg(I.live + i)) = 0u;
-}
-
-// Walks of the listed items (single instance): a split wish's chain walk
-// checks the chain, records its first members and marks it; a group walk
-// records the group at its smallest member. s_req sums the requests: [0]
-// merge cost of the recorded groups, [1] split cost.
-__device__ __forceinline__ void walk_list1(const Inst& I, const FrameP& fp, const uint2* s_list, uint32_t n,
-                                           uint32_t* s_req) {
-    for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
-        const uint2 e = s_list[q];
-        const uint32_t i = e.x & 0x7FFFFFFFu, s = e.y;
-        if (e.x & 0x80000000u) {
-            uint4 rec;
-            const int d = depth_of(I.heap[s], I.ch);
-            const uint32_t cost = chain_walk(I, s, d, true, &rec, true);
-            I.grp[i] = rec;
-            uint32_t sc = 3u * (uint32_t)d + 4u;  // the paper's gate: scan[i] holds it already
-            if (fp.gate != 1) {
-                sc = cost;
-                I.scan[i] = cost;
-            }
-            atomicAdd(&s_req[1], sc);
-        } else {
-            Group g;
-            if (find_group(I, s, g) && g.imin == 0) {
-                I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
-                atomicOr(cmd_ptr(I, s), kGrpMin);
-                atomicAdd(&s_req[0], fp.gate == 1 ? 2u : (uint32_t)g.np);
-            }
-        }
+    uint32_t* marks = chain_marks(I);
+    if (__ldcg(&I.g->marks_clean)) return;  // the last frame left them 0
+    for (uint32_t i0 = gt; i0 < N; i0 += 4u * stride) {
+        uint32_t sl[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) sl[k] = i0 + k * stride < N ? __ldcg(I.live + i0 + k * stride) : kNull;
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k)
+            if (sl[k] != kNull) marks[sl[k]] = 0u;
     }
 }
 
-// P1 (single instance): the live list strided over the whole grid, the
-// slot and heap ID of the next rounds loaded while the current item is
-// classified; walks from the block's list.
+// Appends the block's walk entries to the frame's walk list (one reservation
+// per block and flush, coalesced copy). Call with the whole block.
+__device__ __forceinline__ void walks_out(const Inst& I, const uint4* s_list, uint32_t n, uint32_t* s_tmp) {
+    if (threadIdx.x == 0) s_tmp[0] = n ? atomicAdd(&I.g->nwalk, n) : 0u;
+    __syncthreads();
+    const uint32_t base = s_tmp[0];
+    uint4* wl = walk_list_of(I);
+    for (uint32_t q = threadIdx.x; q < n; q += kFThreads) wl[base + q] = s_list[q];
+    __syncthreads();
+}
+
+// P1 (single instance): the live list strided over the whole grid, the slot
+// and heap ID of the next rounds loaded while the current item is classified.
+// Walk entries (live index | split flag << 31, slot) are listed per block
+// and flushed to the frame's walk list; split wishes are counted per scan
+// tile (warp-aggregated, consecutive live indices share a tile).
 __device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, uint32_t* s_cnt, uint32_t* s_n,
-                                uint2* s_list, uint32_t* s_req) {
-    if (threadIdx.x == 0) {
-        *s_n = 0;
-        s_req[0] = s_req[1] = 0;
-    }
+                                uint4* s_list, uint32_t* s_tmp) {
+    if (threadIdx.x == 0) *s_n = 0;
     stats_reset(s_cnt);
     ctx_tile(bt, bt.tile_base, 0, 1, c);
     const Inst& I = c.I;
     const FrameP& fp = c.fp;
     const uint32_t N = c.N;
+    const uint32_t S = kFThreads * bt.bg->scan_ipt;
+    unsigned long long* wc = wish_counts(bt);
     const uint64_t key = splitmix64(((uint64_t)fp.seed << 32) | (uint64_t)fp.frame);
     const bool cache = vc_form(fp) && fp.vout;
     const uint32_t stride = gridDim.x * kFThreads;
@@ -1205,11 +1298,20 @@ __device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, ui
     for (uint32_t base = blockIdx.x * kFThreads; base < N; base += stride, i += stride) {
         const uint32_t sc = i + 2u * stride < N ? I.live[i + 2u * stride] : 0u;
         const uint64_t jb = i + stride < N ? I.heap[sb] : 0ull;
+        bool split = false;
         if (i < N) {
-            const uint32_t cmd = classify_item(I, fp, key, i, sa, ja, s_tab, s_cnt, cache, true);
-            const bool split = (cmd & kSplitWish) != 0u;
+            const uint32_t cmd = classify_item(I, fp, key, i, sa, ja, s_tab, s_cnt, cache);
+            split = (cmd & kSplitWish) != 0u;
             const bool group = (cmd & kMergeWish) && !(cmd & kHeapOdd);
-            if (split || group) s_list[atomicAdd(s_n, 1u)] = make_uint2(i | (split ? 0x80000000u : 0u), sa);
+            if (split || group)
+                s_list[atomicAdd(s_n, 1u)] = make_uint4(i | (split ? 0x80000000u : 0u), sa, (uint32_t)ja,
+                                                        (uint32_t)(ja >> 32));
+        }
+        {  // split wishes per scan tile
+            const uint32_t t = i / S;
+            const unsigned m = __match_any_sync(0xFFFFFFFFu, i < N ? t : kNull);
+            const uint32_t n = __popc(__ballot_sync(0xFFFFFFFFu, split) & m);
+            if (n && (threadIdx.x & 31u) == (uint32_t)(__ffs(m) - 1)) atomicAdd(&wc[t], (unsigned long long)n);
         }
         sa = sb;
         ja = jb;
@@ -1217,29 +1319,164 @@ __device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, ui
         __syncthreads();
         const uint32_t n = *s_n;
         __syncthreads();
-        if (n > kWalkCap - kFThreads) {  // block-uniform
-            walk_list1(I, fp, s_list, n, s_req);
-            __syncthreads();
+        if (n > kWalkCap1 - kFThreads) {  // block-uniform
+            walks_out(I, s_list, n, s_tmp);
             if (threadIdx.x == 0) *s_n = 0;
             __syncthreads();
         }
     }
     __syncthreads();
-    walk_list1(I, fp, s_list, *s_n, s_req);
-    __syncthreads();
+    walks_out(I, s_list, *s_n, s_tmp);
     stats_flush(s_cnt, I.g, kStSplitWishes);
+    __syncthreads();
+}
+
+// P2 (single instance): the frame's walk list over the whole grid. s_wpre
+// (shared) gets the split wishes before each scan tile. A block first takes
+// its share of the entries and settles the splits past the bound below; the
+// walks left are queued and spread evenly over the block's threads. Per
+// entry:
+//   - a split wish: unless 2 (wishes before its scan tile + 1) > F, its
+//     chain is walked on the frame-start links, checked, its first members
+//     recorded in grp[i] and marked in the chain-mark words; its scan word
+//     the chain's allocation count (or 3d + 4 under the paper's gate, set by
+//     classify); past that bound the gate denies it whatever its cost (every
+//     cost is at least 2), and 2 stands in;
+//   - a merge wish with an even heap ID: its Alg. 4 group, walked while the
+//     wish can be its smallest member and every member wishes to merge (a
+//     merge candidate); then it records the members and kGrpMin, and the
+//     merge cost (parents, or 2 under the paper's gate) in the top byte of
+//     its scan word. A group that is no candidate can never merge.
+// The costs go to their scan tile's (merge, split) sums in status[t] and to
+// the frame's totals.
+__device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_t* s_buf, Pair* s_warp,
+                             uint32_t* s_tmp, uint32_t* s_n1) {
+    stats_reset(s_cnt);
+    ctx_tile(bt, bt.tile_base, 0, 1, c);
+    const Inst& I = c.I;
+    const FrameP& fp = c.fp;
+    const uint32_t T = bt.bg->total_stiles, S = kFThreads * bt.bg->scan_ipt;
+    if (threadIdx.x == 0) s_tmp[0] = s_tmp[1] = 0;
+    if (T > kMaxTiles1) {  // the host keeps pools within the tables
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(I.g, kErrOverflow);
+        __syncthreads();
+        return;
+    }
+    uint32_t* s_wpre = s_buf;
+    uint32_t carry = 0;
+    const unsigned long long* wc = wish_counts(bt);
+    for (uint32_t t0 = 0; t0 < T; t0 += kFThreads) {
+        const uint32_t t = t0 + threadIdx.x;
+        const uint32_t v = t < T ? (uint32_t)__ldcg(wc + t) : 0u;
+        Pair tot;
+        const Pair ex = block_scan(Pair{v, 0u}, tot, s_warp);
+        if (t < T) s_wpre[t] = carry + ex.a;
+        carry += tot.a;
+    }
+    __syncthreads();
+    const uint32_t n = __ldcg(&I.g->nwalk), F = c.F;
+    const uint4* wl = walk_list_of(I);
+    uint32_t* marks = chain_marks(I);
+    uint32_t* s_q = s_buf + kMaxTiles1;  // list indices of the block's walks to do
+    constexpr uint32_t kQCap = kFBuf - kMaxTiles1;
+    // a split's cost and a group's merge cost, added to their scan tile's
+    // sums (one atomic per tile present among the active lanes)
+    auto account = [&](uint32_t t, uint32_t mc, uint32_t sc) {
+        const unsigned act = __activemask();
+        const unsigned m = __match_any_sync(act, t);
+        const uint32_t smc = __reduce_add_sync(m, mc), ssc = __reduce_add_sync(m, sc);
+        if (t != kNull && (threadIdx.x & 31u) == (uint32_t)(__ffs(m) - 1) && (smc | ssc))
+            atomicAdd(&bt.status[min(t, T - 1u)], ((unsigned long long)smc << 32) | ssc);
+        if (mc) atomicAdd(&s_tmp[0], mc);
+        if (sc) atomicAdd(&s_tmp[1], sc);
+        count_stat(s_cnt, 0, mc != 0u);
+    };
+    // the queued walks, evenly over the block's threads
+    auto walk_queue = [&](uint32_t cnt) {
+        for (uint32_t k = threadIdx.x; k < cnt; k += kFThreads) {
+            const uint32_t q = s_q[k];
+            const uint4 e = wl[q];
+            const uint32_t i = e.x & 0x7FFFFFFFu, s = e.y;
+            const uint64_t j = (uint64_t)e.z | ((uint64_t)e.w << 32);
+            uint32_t mc = 0, sc = 0;
+            if (e.x & 0x80000000u) {
+                const int d = depth_of(j, I.ch);
+                uint4 rec;
+                bool more;
+                const uint32_t cost = chain_walk(I, s, d, true, &rec, true, marks, &more);
+                I.grp[i] = rec;
+                sc = fp.gate == 1 ? 3u * (uint32_t)d + 4u : cost;
+                I.scan[i] = sc | (more ? kScanMore : 0u);
+            } else {
+                Group g;
+                if (group_if_mergeable(I, s, j, g)) {
+                    I.grp[i] = make_uint4(g.m[0], g.m[1], g.m[2], g.m[3]);
+                    atomicOr(cmd_ptr(I, s), kGrpMin);
+                    mc = fp.gate == 1 ? 2u : (uint32_t)g.np;
+                    I.scan[i] = mc << 24;
+                }
+            }
+            account(i / S, mc, sc);
+        }
+    };
+    if (threadIdx.x == 0) *s_n1 = 0;
+    __syncthreads();
+    // a block takes 256 consecutive entries per round (neighbouring entries
+    // walk neighbouring records, which its L1 then holds); a thread loads
+    // the entries of four rounds together
+    const uint32_t stride = gridDim.x * kFThreads;
+    for (uint32_t c0 = blockIdx.x * kFThreads; c0 < n; c0 += 4u * stride) {  // block-uniform
+        uint32_t qq[4];
+        uint4 e[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t q = c0 + k * stride + threadIdx.x;
+            qq[k] = q < n ? q : kNull;
+            e[k] = qq[k] != kNull ? wl[qq[k]] : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            if (qq[k] == kNull) continue;
+            const uint32_t i = e[k].x & 0x7FFFFFFFu;
+            const uint32_t t = i / S;
+            // a split is denied whatever its cost when the wishes before its
+            // scan tile cost more than F at 2 each
+            const bool skip = (e[k].x & 0x80000000u) &&
+                              2ull * ((unsigned long long)s_wpre[min(t, T - 1u)] + 1ull) > (unsigned long long)F;
+            if (skip) {
+                const uint64_t j = (uint64_t)e[k].z | ((uint64_t)e[k].w << 32);
+                const uint32_t sc = fp.gate == 1 ? 3u * (uint32_t)depth_of(j, I.ch) + 4u : 2u;
+                if (fp.gate != 1) I.scan[i] = sc;
+                account(t, 0u, sc);
+            } else {
+                s_q[atomicAdd(s_n1, 1u)] = qq[k];
+            }
+        }
+        __syncthreads();
+        const uint32_t cnt = *s_n1;
+        __syncthreads();
+        if (cnt > kQCap - 4u * kFThreads) {  // block-uniform
+            walk_queue(cnt);
+            __syncthreads();
+            if (threadIdx.x == 0) *s_n1 = 0;
+            __syncthreads();
+        }
+    }
+    walk_queue(*s_n1);
+    __syncthreads();
+    stats_flush(s_cnt, I.g, kStMergeCand);
     if (threadIdx.x == 0) {
-        if (s_req[0]) atomicAdd(&I.g->rq_merge, (unsigned long long)s_req[0]);
-        if (s_req[1]) atomicAdd(&I.g->rq_split, (unsigned long long)s_req[1]);
+        if (s_tmp[0]) atomicAdd(&I.g->rq_merge, (unsigned long long)s_tmp[0]);
+        if (s_tmp[1]) atomicAdd(&I.g->rq_split, (unsigned long long)s_tmp[1]);
     }
     __syncthreads();
 }
 
 // Fate of live index i that charges its group (kGrpMin) when every request
 // is granted: the group's parent count (1 or 2) and bit 3 when every member
-// wishes to merge and none was marked by a chain. A group whose members all
-// wish to merge is a merge candidate (counted in s_cnt[3]), and granted.
-__device__ __forceinline__ uint32_t fate_group_granted(const Inst& I, uint32_t i, uint32_t* s_cnt) {
+// wishes to merge and none is marked by a chain (marks in the command words
+// or, with `marks`, in those words).
+__device__ __forceinline__ uint32_t fate_group_granted(const Inst& I, uint32_t i, const uint32_t* marks) {
     const uint4 m = I.grp[i];
     const uint32_t ms[3] = {m.y, m.z, m.w};
     uint32_t c[3];
@@ -1248,10 +1485,9 @@ __device__ __forceinline__ uint32_t fate_group_granted(const Inst& I, uint32_t i
     for (int q = 0; q < 3; ++q) {
         const bool b = ms[q] != kNull && bad_slot(I, ms[q], kErrLink);
         bad = bad || b;
-        c[q] = (ms[q] != kNull && !b) ? *cmd_ptr(I, ms[q]) : kMergeWish;
+        c[q] = (ms[q] != kNull && !b) ? (*cmd_ptr(I, ms[q]) | marks[ms[q]]) : kMergeWish;
     }
     const bool all = !bad && (c[0] & c[1] & c[2] & kMergeWish);
-    count_stat(s_cnt, 3, all);
     const bool ok = all && !((c[0] | c[1] | c[2]) & kSplitMask);
     return ok ? ((m.z == kNull ? 1u : 2u) | 8u) : 0u;
 }
@@ -1260,9 +1496,10 @@ __device__ __forceinline__ uint32_t fate_group_granted(const Inst& I, uint32_t i
 // count, bit 3 for a merging group), the tile-local exclusive prefix of
 // (changed, allocations), the fill records in the tile's region of chgr
 // (tile t at t S), destination words (t << kLocBits | offset) and merged
-// marks; the tile's totals go to status[Titems + t] for the fill. Then the
-// free list. Group validations run from a list (dependent loads), their
-// fates returned through shared memory.
+// marks; the tile's totals go to status[Titems + t] for the fill. When every
+// request was granted, the chain marks are ORed into the command words (the
+// fill reads them there). Then the free list. Group validations run from a
+// list (dependent loads), their fates returned through shared memory.
 __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint32_t tbits, uint32_t* s_cnt,
                              Pair* s_warp, uint32_t* s_w, uint32_t* s_n, uint32_t* s_buf) {
     const uint32_t T = bt.bg->total_stiles, ipt = bt.bg->scan_ipt;
@@ -1276,6 +1513,7 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
     if (all_granted && blockIdx.x == 0 && threadIdx.x == 0) {
         Globals* g = bt.inst[0].g;
         g->stats[kStSplitGranted] = __ldcg(&g->stats[kStSplitWishes]);
+        g->stats[kStMergeGranted] = __ldcg(&g->stats[kStMergeCand]);
     }
     for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
         if (threadIdx.x == 0) *s_n = 0;
@@ -1283,23 +1521,32 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
         ctx_tile(bt, bt.stile_base, t, T, c);
         const Inst& I = c.I;
         const uint32_t N = c.N;
+        const uint32_t* marks = chain_marks(I);
         const uint32_t i0 = stile_first(c, ipt);
         const uint32_t e0 = threadIdx.x * ipt;
         uint32_t sl[kMaxIpt], cm[kMaxIpt], f[kMaxIpt];
 #pragma unroll
         for (uint32_t k = 0; k < kMaxIpt; ++k) sl[k] = (k < ipt && i0 + k < N) ? I.live[i0 + k] : kNull;
 #pragma unroll
-        for (uint32_t k = 0; k < kMaxIpt; ++k) cm[k] = sl[k] != kNull ? *cmd_ptr(I, sl[k]) : 0u;
-        // groups to validate: when every request is granted, every group its
-        // charged member recorded (a group whose members all wish to merge
-        // counts as a granted candidate even if a chain marked one of them);
-        // else the granted candidates without split bits
+        for (uint32_t k = 0; k < kMaxIpt; ++k) {
+            cm[k] = sl[k] != kNull ? *cmd_ptr(I, sl[k]) : 0u;
+            if (all_granted && sl[k] != kNull) {
+                const uint32_t mk = marks[sl[k]];
+                if (mk) {
+                    cm[k] |= mk;
+                    atomicOr(cmd_ptr(I, sl[k]), mk);
+                }
+            }
+        }
+        // groups to validate: when every request is granted, every recorded
+        // group without split bits at its charged member; else the granted
+        // candidates without split bits
         bool lst[kMaxIpt];
 #pragma unroll
         for (uint32_t k = 0; k < kMaxIpt; ++k) {
             f[k] = leaves_of(cm[k] & kSplitMask);
-            lst[k] = sl[k] != kNull && (all_granted ? (cm[k] & kGrpMin) != 0u
-                                                    : (!(cm[k] & kSplitMask) && (cm[k] & kCand) && (cm[k] & kMergeGrant)));
+            lst[k] = sl[k] != kNull && !(cm[k] & kSplitMask) &&
+                     (all_granted ? (cm[k] & kGrpMin) != 0u : ((cm[k] & kCand) && (cm[k] & kMergeGrant)));
             if (lst[k]) s_list[atomicAdd(s_n, 1u)] = e0 + k;
         }
         __syncthreads();
@@ -1307,12 +1554,12 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
         for (uint32_t q = threadIdx.x; q < n; q += kFThreads) {
             const uint32_t e = s_list[q];
             const uint32_t i = c.lt * S + e;
-            s_fate[e] = all_granted ? fate_group_granted(I, i, s_cnt) : alloc_fate(I, i, kCand | kMergeGrant);
+            s_fate[e] = all_granted ? fate_group_granted(I, i, marks) : alloc_fate(I, i, kCand | kMergeGrant);
         }
         __syncthreads();
 #pragma unroll
         for (uint32_t k = 0; k < kMaxIpt; ++k)
-            if (lst[k] && !(cm[k] & kSplitMask)) f[k] = s_fate[e0 + k];
+            if (lst[k]) f[k] = s_fate[e0 + k];
         Pair loc{0, 0};
 #pragma unroll
         for (uint32_t k = 0; k < kMaxIpt; ++k) {
@@ -1368,15 +1615,10 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
         __syncthreads();
         if (s_hist[threadIdx.x] && hbase + threadIdx.x - nt < nt)
             atomicAdd(&tc[hbase + threadIdx.x - nt], (unsigned long long)s_hist[threadIdx.x]);
-        if (threadIdx.x == 0) {
-            const int idx[4] = {kStSplitBis, kStMergeGroups, kStMergedBis, kStMergeCand};
-            for (int k = 0; k < 4; ++k)
-                if (s_cnt[k]) atomicAdd(&I.g->stats[idx[k]], s_cnt[k]);
-            if (s_cnt[3]) atomicAdd(&I.g->stats[kStMergeGranted], s_cnt[3]);
-        }
+        stats_flush(s_cnt, I.g, kStSplitBis, kStMergeGroups, kStMergedBis);
         __syncthreads();
     }
-    free_list(bt, c, s_w, all_granted);
+    free_list(bt, c, s_w, all_granted, tile_counts(bt));
 }
 
 // P5 (single instance): every block scans the tiles' (changed, allocation)
@@ -1526,6 +1768,8 @@ __device__ void phase_final1(const BatchDev& bt, FCtx& c, const uint32_t* s_tab,
         __syncthreads();
     }
     // rows
+    uint32_t* marks = chain_marks(I);
+    if (blockIdx.x == 0 && threadIdx.x == 0) I.g->marks_clean = 1u;  // read by the next frame
     const uint32_t nw = gridDim.x * (kFThreads / 32u);
     uint32_t R = (Nn + nw - 1u) / nw;
     R = max(32u, min(256u, (R + 31u) & ~31u));
@@ -1588,17 +1832,23 @@ __device__ void phase_final1(const BatchDev& bt, FCtx& c, const uint32_t* s_tab,
             }
             __syncwarp();
             const uint32_t ne = min(total, need);
+            uint64_t jn = rows_out && lane < ne ? I.heap[s_rows[lane]] : 0ull;
             for (uint32_t k0 = 0; k0 < ne; k0 += 32u) {
                 const uint32_t k = k0 + lane;
                 const bool valid = k < ne;
                 const uint32_t sl = valid ? s_rows[k] : 0u;
-                if (valid) I.live[row + k] = sl;
+                if (valid) {
+                    I.live[row + k] = sl;
+                    marks[sl] = 0u;  // for the next frame's chain marks
+                }
                 if (rows_out) {
+                    const uint64_t j = jn;
+                    jn = k + 32u < ne ? I.heap[s_rows[k + 32u]] : 0ull;
                     const uint32_t r = row + k0;
                     const uint32_t nv = fp.vcap > r ? min(min(32u, ne - k0), fp.vcap - r) : 0u;
                     float x[9];
                     bool ok = true;
-                    if (lane < nv) ok = vertex_eval(I, fp, I.heap[sl], s_tab, x);
+                    if (lane < nv) ok = vertex_eval(I, fp, j, s_tab, x);
                     if (nv && __all_sync(0xFFFFFFFFu, ok)) {
                         warp_rows_out(x, vst, fp.vout, r, nv);
                     } else if (lane < nv && ok) {  // a row the decode refused stays unwritten
@@ -1618,7 +1868,7 @@ __device__ void phase_final1(const BatchDev& bt, FCtx& c, const uint32_t* s_tab,
 
 __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(BatchDev bt, uint32_t tbits) {
     __shared__ FCtx s_c;
-    __shared__ uint32_t s_tab[64 * 9];
+    __shared__ uint32_t s_tab[kDecTabWords];
     __shared__ __align__(16) uint32_t s_buf[kFBuf];
     __shared__ __align__(16) float s_vst[288 * (kFThreads / 32)];
     __shared__ Pair s_warp[kFThreads / 32 + 1];
@@ -1639,19 +1889,17 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
     phase_prep1(bt, tbits);
     sync();
     stamp(bt, 1);
-    phase_classify1(bt, s_c, s_tab, s_cnt, &s_n, reinterpret_cast<uint2*>(s_buf), s_tmp);
+    phase_classify1(bt, s_c, s_tab, s_cnt, &s_n, reinterpret_cast<uint4*>(s_buf), s_tmp);
     sync();
     stamp(bt, 2);
+    phase_walks1(bt, s_c, s_cnt, s_buf, s_warp, s_tmp, &s_n);
+    sync();
+    stamp(bt, 3);
     const Globals* g = s_c.I.g;
     const bool all_granted = __ldcg(&g->rq_merge) + __ldcg(&g->rq_split) <= (unsigned long long)s_c.F;
     if (!all_granted) {
-        phase_gate_sum(bt, s_c, s_cnt, s_red, &s_n, s_buf, true);
-        sync();
-        stamp(bt, 3);
         phase_gate(bt, s_c, s_cnt, s_red, s_warp, s_tmp, &s_n, reinterpret_cast<uint2*>(s_buf), true);
         sync();
-    } else {
-        stamp(bt, 3);
     }
     stamp(bt, 4);
     phase_alloc1(bt, s_c, all_granted, tbits, s_cnt, s_warp, s_w, &s_n, s_buf);

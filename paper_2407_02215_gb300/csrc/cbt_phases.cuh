@@ -312,6 +312,33 @@ static __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
 
 // -------------------------------------------------------------- classify
 
+// The wishes from the bisector's camera-relative vertices r (R8 reading):
+// split = visible, big and below the maximum depth; merge = no split, depth
+// >= 1 and the parent not (visible and big). The parent's vertices are
+// {nv, r0, r1} (nv its new vertex, from new_vertex() only when needed), its
+// refinement edge (nv, r1) for an odd heap ID and (r0, nv) for an even one;
+// its plane masks for r0 and r1 are the child's.
+template <typename NV>
+__device__ __forceinline__ void wishes_from(const float r[9], bool odd, int d, uint32_t max_depth, const FrameP& fp,
+                                            NV new_vertex, bool& split, bool& merge) {
+    const uint32_t m0 = plane_mask(r, fp), m1 = plane_mask(r + 3, fp), m2 = plane_mask(r + 6, fp);
+    const bool big = edge_big(r, r + 3, fp.q);
+    split = (m0 & m1 & m2) == 0u && big && d < (int)max_depth;
+    merge = false;
+    if (!split && d >= 1) {
+        float nv[3];
+        new_vertex(nv);
+        const bool pvis = (plane_mask(nv, fp) & m0 & m1) == 0u;
+        float a[3], b[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[c] = odd ? nv[c] : r[c];
+            b[c] = odd ? r[3 + c] : nv[c];
+        }
+        merge = !(pvis && edge_big(a, b, fp.q));
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void lod_wishes(const Inst& I, const FrameP& fp, uint64_t j, int d,
                                            uint32_t h, const uint32_t* tab, bool& split, bool& merge,
@@ -323,30 +350,21 @@ __device__ __forceinline__ void lod_wishes(const Inst& I, const FrameP& fp, uint
     if (keep)
 #pragma unroll
         for (int k = 0; k < 9; ++k) keep[k] = r[k];
-    split = lod_test(r, fp) == 3u && d < (int)I.max_depth;
-    merge = false;
-    if (!split && d >= 1) {
-        // Two vertices of the parent are the child's: a 0 bit makes the
-        // child's rows (2 r0, 2 r2, r0 + r1) of the parent's, a 1 bit
-        // (2 r2, 2 r1, r0 + r1) (Eq. 1), and a row doubled over a doubled
-        // denominator evaluates to the same value in every precision form.
-        // The new vertex is the parent's v0 (1 bit) or v1 (0 bit); the row
-        // is picked by selects so that every lane takes the same path.
-        const bool odd = (j & 1ull) != 0ull;
-        T row[9];
+    // Two vertices of the parent are the child's: a 0 bit makes the child's
+    // rows (2 r0, 2 r2, r0 + r1) of the parent's, a 1 bit (2 r2, 2 r1,
+    // r0 + r1) (Eq. 1), and a row doubled over a doubled denominator
+    // evaluates to the same value in every precision form. The new vertex is
+    // the parent's v0 (1 bit) or v1 (0 bit); the row is picked by selects so
+    // that every lane takes the same path.
+    const bool odd = (j & 1ull) != 0ull;
+    wishes_from(r, odd, d, I.max_depth, fp,
+                [&](float nv[3]) {
+                    T row[9];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) row[k] = odd ? Wp[k] : Wp[3 + k];
-        float nv[3];
-        eval_vertex<T>(row, 0, d - 1, fp, I.rel, h, nv);
-        float q[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            q[c] = odd ? nv[c] : r[c];
-            q[3 + c] = odd ? r[3 + c] : nv[c];
-            q[6 + c] = odd ? r[c] : r[3 + c];
-        }
-        merge = lod_test(q, fp) != 3u;
-    }
+                    for (int k = 0; k < 3; ++k) row[k] = odd ? Wp[k] : Wp[3 + k];
+                    eval_vertex<T>(row, 0, d - 1, fp, I.rel, h, nv);
+                },
+                split, merge);
 }
 
 // The sphere form (R13) with a point cache attached. A vertex's FP64 point
@@ -409,21 +427,9 @@ __device__ __forceinline__ void sphere_wishes(const Inst& I, const FrameP& fp, u
     if (keep)
 #pragma unroll
         for (int k = 0; k < 9; ++k) keep[k] = r[k];
-    split = lod_test(r, fp) == 3u && d < (int)I.max_depth;
-    merge = false;
-    if (!split && d >= 1) {
-        const bool odd = (j & 1ull) != 0ull;
-        float nv[3];
-        sphere_rel(pc[12 * cap], pc[13 * cap], pc[14 * cap], pc[15 * cap], fp, nv);
-        float q[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            q[c] = odd ? nv[c] : r[c];
-            q[3 + c] = odd ? r[3 + c] : nv[c];
-            q[6 + c] = odd ? r[c] : r[3 + c];
-        }
-        merge = lod_test(q, fp) != 3u;
-    }
+    wishes_from(r, (j & 1ull) != 0ull, d, I.max_depth, fp,
+                [&](float nv[3]) { sphere_rel(pc[12 * cap], pc[13 * cap], pc[14 * cap], pc[15 * cap], fp, nv); },
+                split, merge);
 }
 
 // A new generation of the sphere-point cache when a LOD frame of the sphere
@@ -455,8 +461,11 @@ __device__ __forceinline__ uint32_t chain_code_bits(uint32_t code) {
     return code == 1u ? kR : (code == 2u ? (kR | kN) : (kR | kP));
 }
 
+// With `more`, a chain of more than four members after b keeps its first
+// four in rec and sets *more (else the record is all kNull).
 static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool scatter, uint4* rec = nullptr,
-                                      bool check = false) {
+                                      bool check = false, uint32_t* marks = nullptr, bool* more = nullptr) {
+    auto mark = [&](uint32_t x, uint32_t bits) { atomicOr(marks ? marks + x : cmd_ptr(I, x), bits); };
     uint32_t cur = b, cost = 2;
     uint32_t m0 = 0, m1 = 0, m2 = 0, m3 = 0, n = 0;
     bool over = false;
@@ -475,10 +484,12 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
         ++n;
     };
     auto done = [&](uint32_t c, bool ok) {
-        if (rec) *rec = (ok && !over) ? make_uint4(m0, m1, m2, m3) : make_uint4(kNull, kNull, kNull, kNull);
+        if (rec)
+            *rec = (ok && (!over || more)) ? make_uint4(m0, m1, m2, m3) : make_uint4(kNull, kNull, kNull, kNull);
+        if (more) *more = ok && over;
         return c;
     };
-    if (scatter) atomicOr(cmd_ptr(I, b), kR);
+    if (scatter) mark(b, kR);
     int dcur = d;
     for (int guard = 0; guard < 64; ++guard) {
         const uint32_t t = I.nb[cur].x;
@@ -486,7 +497,7 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
         if (bad_slot(I, t, kErrChain)) return done(cost, false);
         const uint4 tn = I.nb[t];
         if (tn.x == cur) {
-            if (scatter) atomicOr(cmd_ptr(I, t), kR);
+            if (scatter) mark(t, kR);
             note(t, 1u);
             return done(cost + 2, true);
         }
@@ -499,7 +510,7 @@ static __device__ uint32_t chain_walk(const Inst& I, uint32_t b, int d, bool sca
             set_err(I.g, kErrChain);
             return done(cost, false);
         }
-        if (scatter) atomicOr(cmd_ptr(I, t), bits);
+        if (scatter) mark(t, bits);
         if ((!scatter || check) && depth_of(I.heap[t], I.ch) + 1 != dcur) {
             set_err(I.g, kErrChain);
             return done(cost, false);
