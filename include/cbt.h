@@ -127,6 +127,38 @@ typedef struct {
     uint32_t disp_seed;
 } cbt_frame;
 
+/* A pinhole camera, FP64 world units: the eye, the point looked at, an up
+ * direction (need not be unit length), the vertical field of view in
+ * radians, width / height, and the viewport in pixels. */
+typedef struct {
+    double eye[3];
+    double target[3];
+    double up[3];
+    double fovy_rad;
+    double aspect;
+    int32_t width_px;
+    int32_t height_px;
+} cbt_camera;
+
+/* The LOD inputs of a frame from a camera and a threshold of tau_px pixels
+ * (the paper leaves the criterion to the application, Sec. 3.3 kernel 4;
+ * this library's reading is described at cbt_update): writes frame->eye
+ * (the camera's eye), frame->planes (the inward normals of the four side
+ * planes of the view frustum and of the near plane, all through the eye),
+ * frame->nplanes (5, or 0 when frustum is 0: no culling) and frame->q =
+ * ((height_px / (2 tan(fovy / 2))) / tau_px)^2; the other fields are left
+ * as they are. The derivation is FP64 with one rounding to FP32 at the end:
+ * f = (target - eye) / |target - eye|; the up direction is replaced by +y
+ * (by +x when |f.y| >= 0.9) when |f . up / |up|| > 0.999; r = f x up / |f x
+ * up|; u = r x f; with t_y = tan(fovy / 2) and t_x = aspect t_y the planes
+ * are t_x f + r, t_x f - r, t_y f + u, t_y f - u and f. Every norm is
+ * sqrt((x x + y y) + z z) and every operation is rounded on its own.
+ * Errors: CBT_EINVAL (NULL pointers, tau_px not positive and finite, fovy
+ * outside (0, pi), aspect not positive, an empty viewport, eye = target, a
+ * zero up direction or one along the view's axis after the fallback,
+ * values that are not finite). Host only, synchronous. */
+int cbt_frame_from_camera(const cbt_camera* cam, float tau_px, int frustum, cbt_frame* frame);
+
 /* Per-frame counters (read with cbt_stats). */
 typedef struct {
     uint32_t live_before, live_after, free_before;

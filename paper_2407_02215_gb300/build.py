@@ -1,8 +1,9 @@
 """Builds the CUDA library libcbt.so in-tree for sm_103a (GB300).
 
-nvcc compiles the kernels with -fmad=false: the LOD test and the vertex
-evaluation must round every multiply and add separately so that they match
-the FP32/FP64 reference formula exactly.
+nvcc compiles the kernels with -fmad=false and the host code with
+-ffp-contract=off: the LOD test, the vertex evaluation and the camera
+derivation must round every multiply and add separately so that they match
+their formulas exactly.
 """
 from __future__ import annotations
 
@@ -16,10 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcbt.so")
 SOURCES = ["cbt_kernels.cu", "cbt_fused.cu", "cbt_reduce.cu", "cbt_index.cu", "cbt_api.cu", "cbt_static.cu",
-           "ingest.cpp"]
+           "ingest.cpp", "camera.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 
 

@@ -46,6 +46,7 @@ def load(path: str | None = None):
     lib.cbt_create.argtypes = [I32, P, P, P, P, P, I32, P, I32, I32, P, C.c_size_t, P,
                                C.POINTER(C.c_void_p)]
     lib.cbt_update.argtypes = [P, P, P]
+    lib.cbt_frame_from_camera.argtypes = [P, C.c_float, C.c_int, P]
     lib.cbt_live_count.argtypes = [P, C.POINTER(U32), P]
     lib.cbt_leaves.argtypes = [P, P, P, P, U32, C.POINTER(U32), P]
     lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
@@ -128,6 +129,38 @@ class Frame(C.Structure):
         ("disp_octaves", C.c_uint32),
         ("disp_seed", C.c_uint32),
     ]
+
+
+class Camera(C.Structure):
+    """Mirror of ``cbt_camera`` (include/cbt.h)."""
+
+    _fields_ = [
+        ("eye", C.c_double * 3),
+        ("target", C.c_double * 3),
+        ("up", C.c_double * 3),
+        ("fovy_rad", C.c_double),
+        ("aspect", C.c_double),
+        ("width_px", C.c_int32),
+        ("height_px", C.c_int32),
+    ]
+
+
+def frame_from_camera(eye, target, up, fovy_rad: float, aspect: float, width_px: int, height_px: int,
+                      tau_px: float, frustum: bool = True) -> dict:
+    """cbt_frame_from_camera: the frame's eye, FP32 planes [5, 3], plane
+    count and q from a camera (host only)."""
+    lib = load()
+    cam = Camera()
+    for i in range(3):
+        cam.eye[i], cam.target[i], cam.up[i] = float(eye[i]), float(target[i]), float(up[i])
+    cam.fovy_rad, cam.aspect = float(fovy_rad), float(aspect)
+    cam.width_px, cam.height_px = int(width_px), int(height_px)
+    f = Frame()
+    rc = lib.cbt_frame_from_camera(C.byref(cam), C.c_float(tau_px), 1 if frustum else 0, C.byref(f))
+    if rc:
+        raise CBTError(rc, "cbt_frame_from_camera")
+    return {"eye": np.array(f.eye[:], np.float64), "planes": np.array(f.planes[:], np.float32).reshape(5, 3),
+            "nplanes": int(f.nplanes), "q": np.float32(f.q)}
 
 
 STAT_FIELDS = ["live_before", "live_after", "free_before", "split_wishes", "merge_candidates",

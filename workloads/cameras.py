@@ -12,6 +12,7 @@ Nothing here is the method's arithmetic: it is the camera model feeding it.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -61,25 +62,45 @@ class FrameParams:
     disp_seed: int = 0
 
 
+# The camera model is written as scalar FP64 operations in a fixed order
+# (every norm sqrt((x x + y y) + z z), every operation rounded on its own),
+# so that cbt_frame_from_camera, which takes the same steps in C, gives the
+# same bits.
+def _norm3(v):
+    return math.sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2])
+
+
+def _cross3(a, b):
+    return [a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]]
+
+
 def camera_basis(cam: Camera):
-    f = np.asarray(cam.target, np.float64) - np.asarray(cam.eye, np.float64)
-    f = f / np.linalg.norm(f)
-    up = np.asarray(cam.up, np.float64)
-    if abs(np.dot(f, up / np.linalg.norm(up))) > 0.999:
-        up = np.array([0.0, 1.0, 0.0]) if abs(f[1]) < 0.9 else np.array([1.0, 0.0, 0.0])
-    r = np.cross(f, up)
-    r = r / np.linalg.norm(r)
-    u = np.cross(r, f)
-    return f, r, u
+    """Forward, right and up unit vectors (FP64 lists); the up direction
+    falls back to +y (+x when the view runs along y) when nearly parallel
+    to the view."""
+    e = [float(x) for x in cam.eye]
+    t = [float(x) for x in cam.target]
+    up = [float(x) for x in cam.up]
+    f = [t[c] - e[c] for c in range(3)]
+    fn = _norm3(f)
+    f = [x / fn for x in f]
+    un = _norm3(up)
+    if abs((f[0] * (up[0] / un) + f[1] * (up[1] / un)) + f[2] * (up[2] / un)) > 0.999:
+        up = [0.0, 1.0, 0.0] if abs(f[1]) < 0.9 else [1.0, 0.0, 0.0]
+    r = _cross3(f, up)
+    rn = _norm3(r)
+    r = [x / rn for x in r]
+    return f, r, _cross3(r, f)
 
 
 def frame_params(cam: Camera, tau_px: float, frustum: bool = True, **kw) -> FrameParams:
     f, r, u = camera_basis(cam)
-    ty = np.tan(cam.fovy_rad / 2.0)
-    tx = cam.aspect * ty
-    planes = np.stack([tx * f + r, tx * f - r, ty * f + u, ty * f - u, f]).astype(np.float32)
-    K = cam.height_px / (2.0 * ty)
-    q = np.float32((K / tau_px) ** 2)
+    ty = math.tan(float(cam.fovy_rad) / 2.0)
+    tx = float(cam.aspect) * ty
+    planes = np.array([[tx * f[c] + r[c] for c in range(3)], [tx * f[c] - r[c] for c in range(3)],
+                       [ty * f[c] + u[c] for c in range(3)], [ty * f[c] - u[c] for c in range(3)], f], np.float32)
+    kq = float(cam.height_px) / (2.0 * ty) / float(tau_px)
+    q = np.float32(kq * kq)
     return FrameParams(eye=np.asarray(cam.eye, np.float64).copy(), planes=planes,
                        nplanes=5 if frustum else 0, q=float(q), **kw)
 
