@@ -532,16 +532,22 @@ int cbt_compact(const uint32_t* d_bitfield, const uint32_t* d_sums, int32_t D, u
  * cudaMalloc/cudaFree would synchronize the device and stall the frame, or a
  * host application whose device memory all comes from its own allocator or a
  * graphics interop pool. This entry point allocates nothing; its scratch (a
- * tile ticket, a finished-tile counter and the look-back descriptors) is one
- * static device array of 33,024 bytes in this library, held by every GPU that
- * loads the library until the process exits. The paper has no counterpart to
- * this entry point.
+ * tile ticket, a finished-tile counter, an error word and the look-back
+ * descriptors) is one static device array of 33,024 bytes in this library,
+ * held by every GPU that loads the library until the process exits. The
+ * paper has no counterpart to this entry point.
  *   d_bitfield: DEVICE u32[max(1, 2^D / 32)], bit s % 32 of word s / 32 is slot
  *               s (bits at or above 2^D are ignored);
  *   D: 1 <= D <= 27 (the static scratch covers 4096 tiles of 1024 words);
- *   d_sums: DEVICE u32[2 * words], written in the layout of cbt_cbt;
+ *   d_sums: DEVICE u32[2 * words], written in the layout of cbt_cbt; its word
+ *           d_sums[0], which that layout leaves unused, receives the call's
+ *           device status: 0, or CBT_DERR_TIMEOUT when a bounded wait of the
+ *           kernel's look-back gave up (the tiles' prefixes, and so the list,
+ *           are then not to be trusted);
  *   d_live: DEVICE u32[2^D], receives the slots of the set bits, ascending;
- *   d_count: DEVICE u32, receives the number of set bits.
+ *   d_count: DEVICE u32, receives the number of set bits, or 0xFFFFFFFF when
+ *           d_sums[0] reports a timeout.
+ * Read d_sums[0] or d_count once the stream has reached the call.
  * The first call on a device looks up the scratch's device address (with
  * that device current); make that first call before any stream capture.
  * Every call clears the part of the scratch it uses before its kernel runs;

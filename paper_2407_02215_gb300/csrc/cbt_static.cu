@@ -14,6 +14,9 @@
 // that device; the first call should therefore come before any stream capture.
 // Every call clears the counters and the descriptors it will use before its
 // kernel runs; calls whose work overlaps on the GPU share the array and race.
+// A look-back wait that runs out sets the sticky error word in the scratch;
+// the last tile to finish copies it into the caller's sums[0] (a word the
+// sum-tree layout leaves unused) and then writes 0xFFFFFFFF as the count.
 #include <cstdint>
 #include <mutex>
 
@@ -122,14 +125,17 @@ __device__ uint32_t static_tile_prefix(unsigned long long* status, uint32_t tile
 }
 
 // One tile of kStaticTileWords words per block iteration: popcounts, the
-// tile's part of the sum tree, the live slots of its set bits in order; the
-// last tile to finish builds the levels above the tiles and the count.
+// tile's part of the sum tree, the live slots of its set bits in order
+// (each warp's 128 words as four rows of 32, a row's positions staged in
+// shared memory and stored coalesced); the last tile to finish builds the
+// levels above the tiles, the count and the error word.
 __global__ void __launch_bounds__(kThreads)
 k_reduce_compact_static(const uint32_t* bits, uint32_t W, uint32_t TW, uint32_t ntiles, uint32_t valid_bits,
                         uint32_t* sums, uint32_t* live, uint32_t* count, unsigned long long* scratch) {
     __shared__ uint32_t s_tile, s_last, s_excl;
     __shared__ uint32_t s_warp[kThreads / 32 + 1];
     __shared__ uint32_t s_lvl[2][kThreads];
+    __shared__ uint32_t s_rows[kThreads / 32][1024];
     unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch);
     unsigned int* done = reinterpret_cast<unsigned int*>(scratch + 1);
     unsigned int* err = reinterpret_cast<unsigned int*>(scratch + 2);
@@ -142,12 +148,11 @@ k_reduce_compact_static(const uint32_t* bits, uint32_t W, uint32_t TW, uint32_t 
         if (tile >= ntiles) break;
         const uint32_t w0 = tile * TW + threadIdx.x * 4u;
         const bool mine = threadIdx.x * 4u < TW;
-        uint32_t wv[4] = {0, 0, 0, 0}, pc[4] = {0, 0, 0, 0};
+        uint32_t pc[4] = {0, 0, 0, 0};
         if (mine)
             for (uint32_t k = 0; k < 4u && threadIdx.x * 4u + k < TW; ++k) {
                 uint32_t m = bits[w0 + k];
                 if (valid_bits < 32u) m &= (1u << valid_bits) - 1u;
-                wv[k] = m;
                 pc[k] = __popc(m);
             }
         if (mine) {
@@ -180,15 +185,35 @@ k_reduce_compact_static(const uint32_t* bits, uint32_t W, uint32_t TW, uint32_t 
         uint32_t tot;
         const uint32_t tex = static_block_scan(tsum, tot, s_warp);
         const uint32_t ex = static_tile_prefix(status, tile, tot, err, &s_excl);
-        uint32_t r = ex + tex;
-        if (mine)
-            for (uint32_t k = 0; k < 4u && threadIdx.x * 4u + k < TW; ++k) {
-                uint32_t m = wv[k];
-                while (m) {
-                    live[r++] = (w0 + k) * 32u + (uint32_t)(__ffs(m) - 1);
-                    m &= m - 1u;
-                }
+        // the warp's words [wb, wb + 128) in rows of 32, lane l on word wb +
+        // 32 k + l; its first output index is its first lane's prefix
+        const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+        uint32_t out = ex + __shfl_sync(0xFFFFFFFFu, tex, 0);
+        const uint32_t wb = tile * TW + warp * 128u;
+        uint32_t* row = s_rows[warp];
+#pragma unroll 1
+        for (uint32_t k = 0; k < 4u; ++k) {
+            const uint32_t wl = warp * 128u + k * 32u + lane;  // word within the tile
+            uint32_t m = wl < TW ? bits[wb + k * 32u + lane] : 0u;
+            if (valid_bits < 32u) m &= (1u << valid_bits) - 1u;
+            const uint32_t pc = __popc(m);
+            uint32_t inc = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                if ((int)lane >= o) inc += y;
             }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+            uint32_t o = inc - pc;
+            while (m) {
+                row[o++] = (wb + k * 32u + lane) * 32u + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1u;
+            }
+            __syncwarp();
+            for (uint32_t q = lane; q < total; q += 32u) live[out + q] = row[q];
+            __syncwarp();
+            out += total;
+        }
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) s_last = (atomicAdd(done, 1u) == ntiles - 1u) ? 1u : 0u;
@@ -201,7 +226,12 @@ k_reduce_compact_static(const uint32_t* bits, uint32_t W, uint32_t TW, uint32_t 
                 __threadfence();
                 __syncthreads();
             }
-            if (threadIdx.x == 0) *count = __ldcg(sums + 1);
+            if (threadIdx.x == 0) {
+                // every tile's look-back ended before its finish was counted
+                const unsigned int e = atomicOr(err, 0u);
+                sums[0] = e;
+                *count = e ? 0xFFFFFFFFu : __ldcg(sums + 1);
+            }
         }
     }
 }
