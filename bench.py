@@ -454,7 +454,43 @@ def bench_ours(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, frames, args.cpu_budget, [st["live_after"] for st in stats])
+    if not args.no_forms and world == 1:
+        del g
+        line.update(forms_summary(args))
     return line
+
+
+def forms_summary(args):
+    """The batched and served forms beside the plain per-instance launches
+    (the 256-instance batch population over 64 frames, equal work, final
+    states compared) and the served form's latency at one Poisson rate over
+    the 1,032-instance served population."""
+    import torch
+
+    from paper_2407_02215_gb300.serving import ServeLoop
+    specs4 = W.configs.config4()
+    r = forms_compare(specs4, 64, args.hbm_budget_gb)
+    batched = {"workload": "256 instances, H log-uniform 24..40k, pools 2^14..2^20, 64 frames",
+               "unit": UNIT, "plain": r["plain"]["value"], "batched": r["batched"]["value"],
+               "served_saturated": r["served_saturated"]["value"],
+               "speedup_batched_vs_plain": r["speedup_batched_vs_plain"],
+               "speedup_served_vs_plain": r["speedup_served_vs_plain"],
+               "identical_final_states": r["identical_final_states"], "tuned": r["batched"]["tuned"],
+               "plain_is": "one cbt_update per instance, one cbt_update_many call per frame"}
+    del specs4
+    specs5 = W.configs.config5()
+    loop = ServeLoop(specs5, hbm_budget_bytes=int(args.hbm_budget_gb * 2**30), inflight=2, max_batch=4096)
+    torch.cuda.synchronize()
+    loop.run(args.serve_rate, 0.5, seed=99)  # warm-up
+    s = loop.run(args.serve_rate, args.serve_seconds, seed=int(args.serve_rate))
+    served = {"workload": f"{len(loop.specs)} resident instances (1024 batch-like + 8 planets), "
+                          f"{loop.hbm_used / 2**30:.1f} GB of workspaces, Poisson arrivals",
+              "rate_hz": args.serve_rate, "seconds": args.serve_seconds, "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
+              "requests_per_s": s["requests_per_s"], "bisectors_per_s": s["bisectors_per_s"],
+              "mean_batch": s["mean_batch"], "tick_form": "per-step kernels, two overlapping streams"}
+    del loop
+    torch.cuda.synchronize()
+    return {"batched": batched, "served": served}
 
 
 def bench_reference(args):
@@ -481,77 +517,137 @@ def bench_reference(args):
     }
 
 
-def _sync_stats(gs):
-    return [g.stats() for g in gs]
+def _final_states(insts):
+    """Every instance's whole state: bitfield and sum tree, and the live
+    bisectors' slots, heap IDs and links."""
+    out = []
+    for g in insts:
+        bits, sums = g.cbt()
+        slots, heap, links = g.leaves()
+        out.append((bits, sums[1:], slots, heap, links))  # sums[0] is no node of the tree
+    return out
 
 
-def bench_batch(args):
-    """Batched form (256 uneven instances, 64 frames): the whole batch per
-    frame in one launch (fused) or one launch per step, whichever the online
-    autotuner picks (CUDA graph), against 256 plain per-instance updates of
-    the same frames; identical results."""
+def _same_states(a, b):
+    import torch
+    return len(a) == len(b) and all(all(torch.equal(x, y) for x, y in zip(sa, sb)) for sa, sb in zip(a, b))
+
+
+def forms_compare(specs, n_frames, hbm_budget_gb=120.0, serve=True, tune_rounds=2):
+    """The plain, batched and served forms on the same instances and frames,
+    with equal work: plain = one cbt_update per instance, issued by one
+    cbt_update_many call per frame; batched = the autotuned batch form
+    (CUDA graph); served = a saturated server with every instance's frames
+    queued at the start. Frames are packed beforehand and submitted back to
+    back. Each form starts from fresh instances; the final states of every
+    instance (bitfield, sum tree, live slots, heap IDs, links) are compared
+    with those of a counting pass that reads the live counts per frame."""
     import torch
 
     from paper_2407_02215_gb300 import CBT, Batch
-    specs = W.configs.config4(n_inst=args.instances, n_frames=args.frames)
-    torch.cuda.synchronize()
-    # plain: one cbt_update per instance per frame
-    plain = [CBT(s.mesh, s.D, s.max_depth) for s in specs]
-    torch.cuda.synchronize()
-    t_plain, bis_plain = 0.0, 0
+    from paper_2407_02215_gb300 import cbt as B
+    from paper_2407_02215_gb300.serving import ServeLoop
+    dev = torch.device("cuda")
+    n = len(specs)
+
+    def fresh():
+        gs = [CBT(s.mesh, s.D, s.max_depth, device=dev) for s in specs]
+        torch.cuda.synchronize()
+        return gs
+
+    packed = [B.pack_frames([s.frames[k] for s in specs], dev) for k in range(n_frames)]
+    # counting pass: the work (live bisectors at each frame's start) and the reference states
+    t0 = time.perf_counter()
+    cnt = fresh()
+    t_create = time.perf_counter() - t0
+    h = B.handles_of(cnt)
+    bis = 0
+    for k in range(n_frames):
+        B.update_many_packed(h, packed[k][0], n)
+        bis += sum(g.stats()["live_before"] for g in cnt)
+    ref = _final_states(cnt)
+    del cnt, h
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for k in range(args.frames):
+
+    def timed(step):
+        torch.cuda.synchronize()
         ev0.record()
-        for g, s in zip(plain, specs):
-            g.update(s.frames[k])
+        for k in range(n_frames):
+            step(k)
         ev1.record()
         torch.cuda.synchronize()
-        t_plain += ev0.elapsed_time(ev1) / 1e3
-        bis_plain += sum(st["live_before"] for st in _sync_stats(plain))
-    # batched: tune on a discarded copy, then time a fresh batch
-    tune = [CBT(s.mesh, s.D, s.max_depth) for s in specs]
+        return ev0.elapsed_time(ev1) / 1e3
+
+    plain = fresh()
+    h = B.handles_of(plain)
+    t_plain = timed(lambda k: B.update_many_packed(h, packed[k][0], n))
+    same_plain = _same_states(ref, _final_states(plain))
+    del plain, h
+    tune = fresh()
     bt = Batch(tune)
-    bt.autotune(2)  # 10 candidates x 2 rounds, chosen at the 21st frame
-    for k in range(min(args.frames, 21)):
-        bt.update([s.frames[k] for s in specs])
+    bt.autotune(tune_rounds)
+    for k in range(min(n_frames, 10 * tune_rounds + 1)):
+        bt.update_packed(packed[k][0])
     torch.cuda.synchronize()
     cfg = bt.config()
     del bt, tune
-    gs = [CBT(s.mesh, s.D, s.max_depth) for s in specs]
+    gs = fresh()
     batch = Batch(gs)
     if cfg["fused"]:
         batch.set_fused(True)
     else:
         batch.set_config(cfg["tile_words"], cfg["blocks_per_sm"])
     batch.set_graph(True)
-    # the frames are submitted back to back (no synchronisation between
-    # them, so the host packs frame k + 1 while the device runs frame k);
-    # the work is the plain run's, whose states are the same frame by frame
+    t_batch = timed(lambda k: batch.update_packed(packed[k][0]))
+    same_batch = _same_states(ref, _final_states(gs))
+    del batch, gs
+    out = {"instances": n, "frames": n_frames, "bisectors_per_frame": bis / n_frames,
+           "plain": {"value": bis / t_plain, "ms_per_frame": t_plain / n_frames * 1e3,
+                     "how": "one cbt_update per instance, one cbt_update_many call per frame"},
+           "batched": {"value": bis / t_batch, "ms_per_frame": t_batch / n_frames * 1e3, "tuned": cfg},
+           "speedup_batched_vs_plain": t_plain / t_batch, "create_s_per_set": t_create}
+    same = same_plain and same_batch
+    if serve:
+        loop = ServeLoop(specs, hbm_budget_bytes=int(hbm_budget_gb * 2**30), inflight=2, max_batch=4096)
+        torch.cuda.synchronize()
+        r = loop.run(1.0, 0.0, seed=1, per_instance=n_frames)
+        same_serve = len(loop.instances) == n and _same_states(ref, _final_states(loop.instances))
+        same = same and same_serve
+        out["served_saturated"] = {"value": bis / r["wall_s"], "wall_s": r["wall_s"], "ticks": r["ticks"],
+                                   "mean_batch": r["mean_batch"],
+                                   "how": "every instance's frames queued at the start; host wall clock"}
+        out["speedup_served_vs_plain"] = t_plain / r["wall_s"]
+        del loop
+    out["identical_final_states"] = same
+    out["identical_by_form"] = {"plain": same_plain, "batched": same_batch,
+                                **({"served": same_serve} if serve else {})}
+    del packed, ref
     torch.cuda.synchronize()
-    ev0.record()
-    for k in range(args.frames):
-        batch.update([s.frames[k] for s in specs])
-    ev1.record()
-    torch.cuda.synchronize()
-    t_batch = ev0.elapsed_time(ev1) / 1e3
-    bis_batch = bis_plain
-    same = all(a.live_count() == b.live_count() for a, b in zip(plain, gs))
-    return {"metric": METRIC + " [batched form]", "value": bis_batch / t_batch, "unit": UNIT,
-            "plain_value": bis_plain / t_plain, "speedup_vs_plain": (bis_batch / t_batch) / (bis_plain / t_plain),
-            "ms_per_frame_batched": t_batch / args.frames * 1e3, "ms_per_frame_plain": t_plain / args.frames * 1e3,
-            "identical_live_counts": same, "bisectors_per_frame": bis_batch / args.frames,
+    return out
+
+
+def bench_batch(args):
+    """Batched form (BASELINE config 4: 256 uneven instances, 64 frames)
+    against the plain per-instance launches and a saturated server, on the
+    same frames, with the final states compared."""
+    specs = W.configs.config4(n_inst=args.instances, n_frames=args.frames)
+    r = forms_compare(specs, args.frames, args.hbm_budget_gb)
+    return {"metric": METRIC + " [batched form]", "value": r["batched"]["value"], "unit": UNIT, **r,
             "config": {"workload": f"batch: {len(specs)} instances, H log-uniform 24..40k, pools 2^14..2^20, "
-                                   f"{args.frames} frames", "tuned": cfg}}
+                                   f"{args.frames} frames"}}
 
 
 def bench_serve(args):
-    """Served form: Poisson arrivals over resident instances at several
-    rates; p50/p99 latency beside throughput."""
+    """Served form (BASELINE config 5: 1024 batch-like instances and 8
+    planets): Poisson arrivals at several rates, p50/p99 latency beside
+    throughput, both tick forms; and the plain, batched and saturated-served
+    forms on the same population and frames (equal work, states compared)."""
     import torch
 
     from paper_2407_02215_gb300.serving import ServeLoop
     specs = W.configs.config5(n_inst=args.instances, n_planets=args.planets, n_frames=args.frames)
     rates = [float(r) for r in args.rates.split(",")]
+    t0 = time.perf_counter()
     forms = {}
     for name, fused in (("per_step_overlapped_ticks", False), ("fused_serial_ticks", True)):
         loop = ServeLoop(specs, hbm_budget_bytes=int(args.hbm_budget_gb * 2**30), inflight=2, max_batch=4096,
@@ -565,11 +661,16 @@ def bench_serve(args):
         admitted, rejected, used = len(loop.specs), len(loop.rejected), loop.hbm_used
         del loop
         torch.cuda.synchronize()
+    t_rates = time.perf_counter() - t0
+    cmp = forms_compare(specs, args.compare_frames, args.hbm_budget_gb)
     return {"metric": "served LOD-update requests: latency and throughput", "unit": "ms / bisectors/s",
             "admitted": admitted, "rejected": rejected,
             "hbm_used_gb": used / 2**30, "rates": forms["per_step_overlapped_ticks"], "forms": forms,
+            "same_work_forms": cmp, "rates_wall_s": t_rates,
             "config": {"workload": f"served: {len(specs)} instances ({args.instances} batch-like + "
-                                   f"{args.planets} planets), Poisson arrivals, HBM budget {args.hbm_budget_gb} GB"}}
+                                   f"{args.planets} planets), Poisson arrivals {args.duration} s per rate, "
+                                   f"HBM budget {args.hbm_budget_gb} GB; same-work forms over "
+                                   f"{args.compare_frames} frames"}}
 
 
 def bench_reduce(args):
@@ -811,13 +912,21 @@ def main():
     ap.add_argument("--workload", default="grid",
                     choices=["grid", "batch", "serve", "planet", "reduce", "dodeca", "waves", "terrain", "index"],
                     help="grid = the headline workload; the others are extra measurements")
-    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--instances", type=int, default=None,
+                    help="batch: 256 (config 4); serve: 1024 batch-like instances (config 5)")
     ap.add_argument("--planets", type=int, default=8)
     ap.add_argument("--frames", type=int, default=64)
+    ap.add_argument("--compare-frames", type=int, default=16)
     ap.add_argument("--rates", default="2000,5000,10000,20000")
-    ap.add_argument("--duration", type=float, default=5.0)
+    ap.add_argument("--duration", type=float, default=10.0)
     ap.add_argument("--hbm-budget-gb", type=float, default=120.0)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="grid line without the batched and served objects")
+    ap.add_argument("--serve-rate", type=float, default=10000.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     args = ap.parse_args()
+    if args.instances is None:
+        args.instances = 1024 if args.workload == "serve" else 256
     if args.workload != "grid":
         import paper_2407_02215_gb300 as P
         P.build_library()

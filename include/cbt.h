@@ -255,6 +255,14 @@ int cbt_attach_point_cache(cbt_state* st, void* memory, size_t bytes, cbt_stream
  * Asynchronous. */
 int cbt_update(cbt_state* st, const cbt_frame* frame, cbt_stream_t stream);
 
+/* n plain updates in one call: cbt_update(states[b], frames + b, stream)
+ * for b = 0 .. n-1 in order, each instance's frame launched on its own as
+ * cbt_update does (no batching), from a host loop in the library. Stops at
+ * the first error and returns it (the updates before it stay enqueued).
+ * Errors: those of cbt_update; CBT_EINVAL for NULL arrays or n < 0.
+ * Asynchronous. */
+int cbt_update_many(cbt_state* const* states, const cbt_frame* frames, int32_t n, cbt_stream_t stream);
+
 /* Device address of page-locked, mapped host memory (cudaHostAlloc'd or
  * registered; every pinned allocation is mapped under unified addressing),
  * for outputs that kernels write straight into host memory: e.g.

@@ -47,6 +47,7 @@ def load(path: str | None = None):
                                C.POINTER(C.c_void_p)]
     lib.cbt_update.argtypes = [P, P, P]
     lib.cbt_frame_from_camera.argtypes = [P, C.c_float, C.c_int, P]
+    lib.cbt_update_many.argtypes = [P, P, I32, P]
     lib.cbt_live_count.argtypes = [P, C.POINTER(U32), P]
     lib.cbt_leaves.argtypes = [P, P, P, P, U32, C.POINTER(U32), P]
     lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
@@ -470,6 +471,38 @@ class CBT:
         return {n: int(getattr(s, n)) for n in STAT_FIELDS}
 
 
+def handles_of(instances):
+    """The states' handles as a C array (for update_many_packed)."""
+    return (C.c_void_p * len(instances))(*[g.handle.value for g in instances])
+
+
+def pack_frames(fps, device, vertices_out=None):
+    """The frames as a C array of cbt_frame, and the device buffers they
+    point to (keep both alive while the frames are in use)."""
+    arr = (Frame * len(fps))()
+    keep = []
+    for b, fp in enumerate(fps):
+        vo = vertices_out[b] if vertices_out is not None else None
+        f, k = frame_struct(fp, device, vo)
+        arr[b] = f
+        keep.extend(k)
+    return arr, keep
+
+
+def update_many_packed(handles, arr, n: int, stream=None):
+    rc = load().cbt_update_many(handles, arr, n, _stream_ptr(stream))
+    if rc:
+        raise CBTError(rc, "cbt_update_many")
+
+
+def update_many(instances, fps, stream=None, vertices_out=None):
+    """cbt_update_many: one plain cbt_update per instance, issued from the
+    library's host loop in one call (frames fps[b] for instances[b])."""
+    arr, keep = pack_frames(fps, instances[0].device, vertices_out)
+    update_many_packed(handles_of(instances), arr, len(instances), stream)
+    del keep
+
+
 class Batch:
     """Several CBT instances updated by one launch per kernel and frame."""
 
@@ -506,6 +539,12 @@ class Batch:
             arr[b] = f
             keep.extend(k)
         self._keep = keep
+        rc = _lib.cbt_batch_update(self._h, arr, _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_batch_update")
+
+    def update_packed(self, arr, stream=None):
+        """One frame from frames packed by pack_frames."""
         rc = _lib.cbt_batch_update(self._h, arr, _stream_ptr(stream))
         if rc:
             raise CBTError(rc, "cbt_batch_update")

@@ -662,6 +662,15 @@ extern "C" int cbt_update(cbt_state* st, const cbt_frame* frame, cbt_stream_t st
     return batch_update(st->self, frame, reinterpret_cast<cudaStream_t>(stream));
 }
 
+extern "C" int cbt_update_many(cbt_state* const* states, const cbt_frame* frames, int32_t n, cbt_stream_t stream) {
+    if (!states || !frames || n < 0) return CBT_EINVAL;
+    for (int32_t b = 0; b < n; ++b) {
+        const int rc = cbt_update(states[b], frames + b, stream);
+        if (rc) return rc;
+    }
+    return CBT_OK;
+}
+
 extern "C" int cbt_live_count(cbt_state* st, uint32_t* h_count, cbt_stream_t stream) {
     if (!st || !h_count) return CBT_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -12,6 +12,7 @@ result is exactly the one it would get alone.
 """
 from __future__ import annotations
 
+import gc
 import time
 from collections import deque
 
@@ -51,7 +52,22 @@ class ServeLoop:
         self.max_batch = max_batch
         self.served = [0] * len(self.instances)  # frames applied per instance
 
-    def run(self, rate_hz: float, duration_s: float, seed: int = 0, max_requests: int | None = None):
+    def run(self, rate_hz: float, duration_s: float, seed: int = 0, max_requests: int | None = None,
+            per_instance: int | None = None):
+        """Serves Poisson arrivals at rate_hz for duration_s (or until
+        max_requests arrived); with per_instance, every instance instead has
+        that many requests queued at the start (a saturated server, equal work
+        per instance). Python's garbage collector is paused meanwhile (a
+        collection over the loop's objects stalls the host for milliseconds)."""
+        gc_was = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(rate_hz, duration_s, seed, max_requests, per_instance)
+        finally:
+            if gc_was:
+                gc.enable()
+
+    def _run(self, rate_hz, duration_s, seed, max_requests, per_instance):
         rng = np.random.default_rng(seed)
         n = len(self.instances)
         queues = [deque() for _ in range(n)]
@@ -62,6 +78,12 @@ class ServeLoop:
         arrivals = 0
         t0 = time.perf_counter()
         next_arr = t0 + rng.exponential(1.0 / rate_hz)
+        if per_instance is not None:
+            for b in range(n):
+                queues[b].extend([t0] * per_instance)
+                ready.add(b)
+            arrivals = max_requests = n * per_instance
+            next_arr = float("inf")
         stream_i = 0
         while True:
             now = time.perf_counter()
