@@ -876,6 +876,106 @@ def bench_index(args):
                                    "update, inputs resident", "frames_timed": int(ms.size)}}
 
 
+def _near_reference(heap, rows, ch, roots, radius_m, eye, project=None):
+    """FP64 vertices, relative to the eye, of the given rows whose heap IDs
+    have a vertex within radius_m of the eye: the oracle's exact integer
+    weights over 2^d times its FP64 root table (absolute), optionally moved
+    by `project` (absolute FP64 points [3, 3] -> points)."""
+    from oracle.oracle import decode_weights
+    out_rows, out_v = [], []
+    for r in rows:
+        j = int(heap[r])
+        d = j.bit_length() - 1 - ch
+        h = (j >> d) - (1 << ch)
+        p = (decode_weights(j, ch).astype(np.float64) / float(2 ** d)) @ roots[h]
+        if project is not None:
+            p = project(p)
+        v = p - eye[None, :]
+        if np.sqrt((v * v).sum(axis=1)).min() <= radius_m:
+            out_rows.append(r)
+            out_v.append(v)
+    return np.array(out_rows, np.int64), (np.stack(out_v) if out_v else np.zeros((0, 3, 3)))
+
+
+def bench_precision(args):
+    """Vertex error near the eye at the end of the planet descents, in mm,
+    against FP64 evaluations of the oracle's exact weights (Sec. 4: FP64
+    for planets; R10 fixed point; R13 sphere projection): the cube-sphere
+    descent (pool 2^22, 600 frames) in its fixed-point, FP64 and FP32 forms,
+    and the dodecahedron planet without and with its wave displacement (the
+    sphere form), within 100 m of the final eye (2 m above the surface)."""
+    import torch
+
+    from oracle import Oracle
+    from oracle import oracle as O
+    from paper_2407_02215_gb300 import CBT
+    out = {"metric": "vertex error near the eye at planet scale (max, mm)", "unit": "mm",
+           "radius_m": 100.0, "reference": "FP64 of the oracle's exact integer weights and FP64 roots"}
+    spec = W.configs.config3(n_frames=600)
+    g = CBT(spec.mesh, spec.D, spec.max_depth)
+    for fp in spec.frames:
+        g.update(fp)
+    eye = np.asarray(spec.frames[-1].eye, np.float64)
+    o = Oracle(spec.mesh, 12, spec.max_depth)
+    _, heap, _ = g.leaves()
+    heap = heap.cpu().numpy().view(np.uint64)
+    vf = g.vertices(eye, 1, 20).cpu().numpy().astype(np.float64)
+    dist = np.sqrt((vf * vf).sum(axis=2)).min(axis=1)
+    cand = np.flatnonzero(dist <= 101.0)
+    order = cand[np.argsort(dist[cand], kind="stable")]
+    cand = np.unique(np.concatenate([order[:10000], order[10000::max(1, (order.size - 10000) // 10000)]]))
+    rows, ref = _near_reference(heap, cand, o.ch, o.root_table(), 100.0, eye)
+    c3 = {"workload": "cube-sphere 1536 halfedges, R 6.371e6 m, pool 2^22, max depth 48, 600-frame descent to 2 m",
+          "live": int(heap.size), "within_100m": int((dist <= 100.0).sum()), "sampled": int(rows.size),
+          "sample": "the 10,000 nearest and 10,000 spread over the rest",
+          "nearest_m": float(np.sqrt((ref * ref).sum(axis=2)).min()) if rows.size else None}
+    for name, prec in (("fixed", 1), ("fp64", 2), ("fp32", 0)):
+        v = g.vertices(eye, prec, 20).cpu().numpy().astype(np.float64)[rows]
+        c3[name + "_max_mm"] = float(np.abs(v - ref).max() * 1e3) if rows.size else None
+    out["planet_cube_sphere"] = c3
+    del g
+    for key, spec in (("dodeca", W.configs.config_dodeca()), ("waves", W.configs.config_waves())):
+        g = CBT(spec.mesh, spec.D, spec.max_depth, point_cache=True)
+        vbuf = torch.empty((1 << spec.D, 3, 3), dtype=torch.float32, device="cuda")
+        for fp in spec.frames:
+            g.update(fp, vertices_out=vbuf)
+        torch.cuda.synchronize()
+        last = spec.frames[-1]
+        eye = np.asarray(last.eye, np.float64)
+        R = float(last.sphere_radius)
+        n = g.live_count()
+        vg = vbuf[:n].cpu().numpy().astype(np.float64)
+        _, heap, _ = g.leaves()
+        heap = heap.cpu().numpy().view(np.uint64)
+        o = Oracle(spec.mesh, 8, spec.max_depth)
+
+        def project(p, fp=last):
+            nrm = np.sqrt((p * p).sum(axis=1))
+            rad = np.full(3, R)
+            if fp.disp_amplitude:
+                for k in range(3):
+                    u = (p[k] / nrm[k]).astype(np.float32)
+                    hgt = np.float32(fp.disp_amplitude) * np.float32(
+                        O.fbm(u, fp.disp_frequency, fp.disp_octaves, fp.disp_seed))
+                    rad[k] = R + float(hgt)
+            return p * (rad / nrm)[:, None]
+
+        # the pool saturates short of the eye: the 5,000 nearest bisectors
+        dist = np.sqrt((vg * vg).sum(axis=2)).min(axis=1)
+        cand = np.argsort(dist, kind="stable")[:5000]
+        rows, ref = _near_reference(heap, cand, o.ch, o.root_table(), 1e30, eye, project)
+        e = np.abs(vg[rows] - ref)
+        dref = np.sqrt((ref * ref).sum(axis=2)).min(axis=1)
+        out[key] = {"workload": f"{spec.name}: dodecahedron planet, pool 2^{spec.D}, "
+                                f"{len(spec.frames)}-frame descent to 2 m, sphere form (FP64 projection)"
+                                + (", 2 m wave displacement" if last.disp_amplitude else ""),
+                    "live": int(n), "sampled": int(rows.size), "sample": "the 5,000 bisectors nearest the eye",
+                    "sphere_max_mm": float(e.max() * 1e3),
+                    "distance_m": [float(dref.min()), float(dref.max())]}
+        del g, vbuf
+    return out
+
+
 def bench_planet(args):
     """Planet descent (pool 2^22, max depth 48, fixed point): frame times."""
     import torch
@@ -910,7 +1010,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
     ap.add_argument("--workload", default="grid",
-                    choices=["grid", "batch", "serve", "planet", "reduce", "dodeca", "waves", "terrain", "index"],
+                    choices=["grid", "batch", "serve", "planet", "reduce", "dodeca", "waves", "terrain", "index",
+                             "precision"],
                     help="grid = the headline workload; the others are extra measurements")
     ap.add_argument("--instances", type=int, default=None,
                     help="batch: 256 (config 4); serve: 1024 batch-like instances (config 5)")
@@ -932,7 +1033,7 @@ def main():
         P.build_library()
         fn = {"batch": bench_batch, "serve": bench_serve, "planet": bench_planet,
               "reduce": bench_reduce, "dodeca": bench_dodeca, "waves": bench_waves,
-              "terrain": bench_terrain, "index": bench_index}[args.workload]
+              "terrain": bench_terrain, "index": bench_index, "precision": bench_precision}[args.workload]
         print(json.dumps(fn(args)))
         return
     if args.impl == "reference":

@@ -287,9 +287,11 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
         if (per_sm <= 0) rc = CBT_ECUDA;
         const uint32_t work = std::max({B->dev.Titems, B->dev.Twords, (B->dev.Trel + 255u) / 256u, 1u});
         B->fused_grid = static_cast<int>(std::min<uint32_t>(work, static_cast<uint32_t>(per_sm * B->sms)));
+        // the single-instance frame spreads classify, the walks and the rows
+        // of its export over the whole grid, so a small instance also gets
+        // every SM
         const int per_sm1 = n == 1 ? frame1_blocks_per_sm() : 0;
-        if (per_sm1 > 0)
-            B->fused_grid1 = static_cast<int>(std::min<uint32_t>(work, static_cast<uint32_t>(per_sm1 * B->sms)));
+        if (per_sm1 > 0) B->fused_grid1 = per_sm1 * B->sms;
     }
     if (rc) {
         if (B->h_fps) cudaFreeHost(B->h_fps);

@@ -109,3 +109,68 @@ def test_dodecahedron_planet_sphere_projection(P):
     vo = o.vertices(fp.eye, 3, 20, fp.sphere_radius)
     vg = vbuf[:n].cpu().numpy()
     assert np.array_equal(vg.view(np.uint32), vo.view(np.uint32))
+
+
+def near_eye_reference(rows_heap, ch, roots, eye, radius_m):
+    """Of the (row, heap ID) pairs given, those with a vertex within radius_m
+    of the eye, each with its vertices relative to the eye from the oracle's
+    exact integer weights (Alg. 2 / Eq. 1) and FP64 root table: w = W / 2^d
+    is exact in FP64 (W < 2^53), so each coordinate is within a few
+    nanometres of the exact point at Earth radius."""
+    from oracle.oracle import decode_weights
+    out = []
+    for row, j in rows_heap:
+        j = int(j)
+        d = j.bit_length() - 1 - ch
+        h = (j >> d) - (1 << ch)
+        Wt = decode_weights(j, ch).astype(np.float64) / float(2 ** d)  # rows: vertices, columns: root corners
+        v = Wt @ roots[h] - eye[None, :]
+        if np.sqrt((v * v).sum(axis=1)).min() <= radius_m:
+            out.append((row, v))
+    return out
+
+
+def test_planet_precision_near_the_eye(P):
+    """The precision form where it matters: the whole 600-frame descent on
+    the 2^22 pool (state equal to the stored oracle digest at the end), then
+    the bisectors with a vertex within 100 m of the final eye, 2 m above the
+    surface (a sample: the 10,000 nearest and 10,000 spread over the rest). Against the FP64 evaluation of the oracle's exact weights: fixed
+    point (R10) within 2^-19 m plus the final FP32 rounding, the FP64 form
+    within the same, FP32 root offsets off by a centimetre or more. The max
+    errors are printed in mm."""
+    if not os.path.exists(GOLD):
+        pytest.skip("planet_oracle.json not generated")
+    gold = json.load(open(GOLD))
+    spec = W.configs.config3(n_frames=gold["frames"], D=gold["D"])
+    g = P.CBT(spec.mesh, spec.D, spec.max_depth)
+    for fp in spec.frames:
+        g.update(fp)
+    assert g.stats()["error"] == 0
+    assert _digest(g) == gold["state_digest"][str(gold["frames"] - 1)]
+    eye = np.asarray(spec.frames[-1].eye, np.float64)
+    o = Oracle(spec.mesh, 12, spec.max_depth)  # only for its root table and ceil(log2 H)
+    roots, ch = o.root_table(), o.ch
+    _, heap, _ = g.leaves()
+    heap = heap.cpu().numpy().view(np.uint64)
+    vfix = g.vertices(eye, PREC_FIXED, 20).cpu().numpy().astype(np.float64)
+    dist = np.sqrt((vfix * vfix).sum(axis=2)).min(axis=1)
+    cand = np.flatnonzero(dist <= 101.0)
+    assert cand.size >= 100, f"only {cand.size} bisectors within 100 m of the eye"
+    # a sample of them: the 10,000 nearest and 10,000 spread over the rest
+    order = cand[np.argsort(dist[cand], kind="stable")]
+    cand = np.unique(np.concatenate([order[:10000], order[10000::max(1, (order.size - 10000) // 10000)]]))
+    near = near_eye_reference([(r, heap[r]) for r in cand], ch, roots, eye, 100.0)
+    assert len(near) >= 100
+    rows = np.array([r for r, _ in near])
+    ref = np.stack([v for _, v in near])
+    bound = 2.0**-19 + 2.0**-24 * np.abs(ref)
+    errs = {"within_100m": int((dist <= 100.0).sum()), "sampled": int(rows.size),
+            "nearest_m": float(np.sqrt((ref * ref).sum(axis=2)).min())}
+    for name, prec in (("fixed", PREC_FIXED), ("fp64", PREC_FP64), ("fp32", PREC_FP32)):
+        v = g.vertices(eye, prec, 20).cpu().numpy().astype(np.float64)[rows]
+        e = np.abs(v - ref)
+        errs[name + "_max_mm"] = float(e.max() * 1e3)
+        if name != "fp32":
+            assert (e <= bound).all(), name
+    print("planet vertex error within 100 m of the eye:", errs)
+    assert errs["fp32_max_mm"] >= 10.0

@@ -162,19 +162,28 @@ def flythrough_path(n_frames: int, seed: int, alt_hi=0.5, alt_lo=0.01, pitch_deg
 
 
 def descent_path(mesh, n_frames: int, seed: int, alt_hi=2e7, alt_lo=2.0):
-    """Planet descent: a seeded interior target on one coarse face; altitude
-    above that face's plane log-spaced alt_hi -> alt_lo; looking at
-    target + tangent * 10 * altitude; up = the face normal."""
+    """Planet descent onto the surface the method refines: a seeded interior
+    point of one root triangle (Vert h, Vert Next h, face centroid) of a
+    seeded coarse face is the target; the altitude above that triangle's
+    plane is log-spaced alt_hi -> alt_lo; looking at target + tangent * 10 *
+    altitude; up = the triangle's outward normal (a coarse face of a
+    cube-sphere is not planar, so its root triangles lie in different
+    planes)."""
     rng = np.random.default_rng(seed)
     f = int(rng.integers(mesh.F))
     off = int(mesh.face_sizes[:f].sum())
     idx = mesh.face_verts[off:off + int(mesh.face_sizes[f])]
     P = mesh.pos[idx]
-    w = rng.dirichlet(np.ones(len(idx)))
-    target = (w[:, None] * P).sum(0)
-    nrm = np.cross(P[1] - P[0], P[2] - P[0])
+    n = len(idx)
+    k = int(rng.integers(n))
+    a, b, c = P[k], P[(k + 1) % n], P.sum(0) / n
+    w = rng.dirichlet(np.ones(3))
+    target = w[0] * a + w[1] * b + w[2] * c
+    nrm = np.cross(b - a, c - a)
     nrm /= np.linalg.norm(nrm)
-    tang = P[1] - P[0]
+    if np.dot(nrm, target) < 0:
+        nrm = -nrm
+    tang = b - a
     tang -= nrm * np.dot(tang, nrm)
     tang /= np.linalg.norm(tang)
     cams = []
