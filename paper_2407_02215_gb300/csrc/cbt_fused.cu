@@ -1119,6 +1119,33 @@ __global__ void __launch_bounds__(kFThreads) k_wait_selftest(BatchGlobals* bg, i
 constexpr uint32_t kLocBits = 13, kLocMask = (1u << kLocBits) - 1u;  // offset of a new record within its tile
 constexpr uint32_t kMaxTiles1 = kFBuf / 2;  // scan tiles and word tiles the shared tables hold
 
+// Exclusive prefix sums of n <= kMaxTiles1 pairs over the block: thread x
+// takes the consecutive entries [x k, x k + k), k = ceil(n / threads), loads
+// them all at once (load(i) -> Pair), and after one block scan hands each
+// entry's exclusive prefix to store(i, Pair); returns the total.
+template <typename Load, typename Store>
+__device__ __forceinline__ Pair block_table(uint32_t n, Load load, Store store, Pair* s_warp) {
+    constexpr uint32_t kPer = kMaxTiles1 / kFThreads;
+    const uint32_t per = (n + kFThreads - 1u) / kFThreads;
+    const uint32_t i0 = threadIdx.x * per;
+    Pair v[kPer];
+    Pair loc{0, 0};
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        v[k] = (k < per && i0 + k < n) ? load(i0 + k) : Pair{0, 0};
+        loc = padd(loc, v[k]);
+    }
+    Pair tot;
+    Pair run = block_scan(loc, tot, s_warp);
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        if (k < per && i0 + k < n) store(i0 + k, run);
+        run = padd(run, v[k]);
+    }
+    __syncthreads();
+    return tot;
+}
+
 // A destination word (tile << kLocBits | offset) resolved through the
 // tiles' allocation offsets in shared memory.
 struct DestTiles {
@@ -1363,17 +1390,9 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
         return;
     }
     uint32_t* s_wpre = s_buf;
-    uint32_t carry = 0;
     const unsigned long long* wc = wish_counts(bt);
-    for (uint32_t t0 = 0; t0 < T; t0 += kFThreads) {
-        const uint32_t t = t0 + threadIdx.x;
-        const uint32_t v = t < T ? (uint32_t)__ldcg(wc + t) : 0u;
-        Pair tot;
-        const Pair ex = block_scan(Pair{v, 0u}, tot, s_warp);
-        if (t < T) s_wpre[t] = carry + ex.a;
-        carry += tot.a;
-    }
-    __syncthreads();
+    block_table(T, [&](uint32_t t) { return Pair{(uint32_t)__ldcg(wc + t), 0u}; },
+                [&](uint32_t t, Pair ex) { s_wpre[t] = ex.a; }, s_warp);
     const uint32_t n = __ldcg(&I.g->nwalk), F = c.F;
     const uint4* wl = walk_list_of(I);
     uint32_t* marks = chain_marks(I);
@@ -1639,19 +1658,13 @@ __device__ void phase_fill1(const BatchDev& bt, FCtx& c, bool all_granted, uint3
         __syncthreads();
         return;
     }
-    Pair carry{0, 0};
-    for (uint32_t t0 = 0; t0 < T; t0 += kFThreads) {
-        const uint32_t t = t0 + threadIdx.x;
-        const Pair v = t < T ? unpack_pair(__ldcg(bt.status + bt.Titems + t)) : Pair{0, 0};
-        Pair tot;
-        const Pair ex = block_scan(v, tot, s_warp);
-        if (t < T) {
-            s_cpre[t] = carry.a + ex.a;
-            s_apre[t] = carry.b + ex.b;
-        }
-        carry = padd(carry, tot);
-    }
-    __syncthreads();
+    const Pair carry = block_table(
+        T, [&](uint32_t t) { return unpack_pair(__ldcg(bt.status + bt.Titems + t)); },
+        [&](uint32_t t, Pair ex) {
+            s_cpre[t] = ex.a;
+            s_apre[t] = ex.b;
+        },
+        s_warp);
     const uint32_t C = carry.a;
     const uint64_t req = all_granted ? __ldcg(&I.g->rq_merge) + __ldcg(&I.g->rq_split)
                                      : (uint64_t)I.g->Mg + (uint64_t)I.g->Stot;
@@ -1712,24 +1725,23 @@ __device__ void phase_final1(const BatchDev& bt, FCtx& c, const uint32_t* s_tab,
     // ones being the tile's share of the first A zero bits
     const unsigned long long* tc = tile_counts(bt);
     const uint32_t A = __ldcg(&I.g->A), TS = 1u << tbits;
-    uint32_t carry = 0, carry0 = 0;
-    for (uint32_t t0 = 0; t0 < nt; t0 += kFThreads) {
-        const uint32_t t = t0 + threadIdx.x;
-        const unsigned long long w = t < nt ? __ldcg(tc + t) : 0ull;
-        const uint32_t old = (uint32_t)(w >> 32), clr = (uint32_t)w;
-        Pair tot;
-        const uint32_t ones_before = carry0 + block_scan(Pair{old, 0u}, tot, s_warp).a;
-        carry0 += tot.a;
-        const long long zb = (long long)t * TS - ones_before;  // zero bits before the tile at frame start
-        const long long set = min(max((long long)A - zb, 0ll), (long long)(TS - old));
-        const uint32_t v = t < nt ? old - clr + (uint32_t)set : 0u;
-        const Pair ex = block_scan(Pair{v, 0u}, tot, s_warp);
-        if (t < nt) s_tpre[t] = carry + ex.a;
-        carry += tot.a;
-    }
+    // pass 1: ones before each tile at frame start (into s_tpre), pass 2:
+    // the new counts from them, scanned in place
+    block_table(nt, [&](uint32_t t) { return Pair{(uint32_t)(__ldcg(tc + t) >> 32), 0u}; },
+                [&](uint32_t t, Pair ex) { s_tpre[t] = ex.a; }, s_warp);
+    const Pair tot = block_table(
+        nt,
+        [&](uint32_t t) {
+            const unsigned long long w = __ldcg(tc + t);
+            const uint32_t old = (uint32_t)(w >> 32), clr = (uint32_t)w;
+            const long long zb = (long long)t * TS - s_tpre[t];  // zero bits before the tile at frame start
+            const long long set = min(max((long long)A - zb, 0ll), (long long)(TS - old));
+            return Pair{old - clr + (uint32_t)set, 0u};
+        },
+        [&](uint32_t t, Pair ex) { s_tpre[t] = ex.a; }, s_warp);
     if (threadIdx.x == 0) s_tmp[0] = 0;
     __syncthreads();
-    const uint32_t Nn = carry;
+    const uint32_t Nn = tot.a;
     if (blockIdx.x == 0) {
         // node m (1 <= m < nt) covers tile nodes [m 2^k, (m + 1) 2^k) at 2^k
         // tiles per node of its level
