@@ -596,12 +596,16 @@ __device__ __forceinline__ void eval_vertices(const T W[9], int d, const FrameP&
 // vertices strictly on its negative side, where a vertex r is on the
 // negative side of plane n when (n.x r.x + n.y r.y) + n.z r.z < 0; it is
 // big when |v1 - v0|^2 q > |(v0 + v1)/2|^2.
-// The planes on whose negative side vertex r lies, as a bit mask.
-__device__ __forceinline__ uint32_t plane_mask(const float* r, const FrameP& fp) {
+// The planes among `among` (a bit mask) on whose negative side vertex r
+// lies, as a bit mask: a triangle is culled by a plane only if all three
+// vertices are, so a vertex need only be tested against the planes the
+// earlier ones failed (the same products, bit for bit, where they are made).
+__device__ __forceinline__ uint32_t plane_mask(const float* r, const FrameP& fp, uint32_t among = 31u) {
     uint32_t m = 0u;
 #pragma unroll
     for (uint32_t p = 0; p < 5u; ++p) {
         if (p >= fp.nplanes) break;
+        if (!((among >> p) & 1u)) continue;
         const float s = __fadd_rn(__fadd_rn(__fmul_rn(fp.planes[3 * p], r[0]), __fmul_rn(fp.planes[3 * p + 1], r[1])),
                                   __fmul_rn(fp.planes[3 * p + 2], r[2]));
         m |= (s < 0.0f ? 1u : 0u) << p;
@@ -620,7 +624,9 @@ __device__ __forceinline__ bool edge_big(const float* a, const float* b, float q
 }
 // bit0 visible, bit1 big.
 __device__ __forceinline__ uint32_t lod_test(const float r[9], const FrameP& fp) {
-    const uint32_t out = plane_mask(r, fp) & plane_mask(r + 3, fp) & plane_mask(r + 6, fp);
+    uint32_t out = plane_mask(r, fp);
+    if (out) out = plane_mask(r + 3, fp, out);
+    if (out) out = plane_mask(r + 6, fp, out);
     return (out == 0u ? 1u : 0u) | (edge_big(r, r + 3, fp.q) ? 2u : 0u);
 }
 

@@ -321,14 +321,18 @@ static __device__ bool find_group(const Inst& I, uint32_t s1, Group& g) {
 template <typename NV>
 __device__ __forceinline__ void wishes_from(const float r[9], bool odd, int d, uint32_t max_depth, const FrameP& fp,
                                             NV new_vertex, bool& split, bool& merge) {
-    const uint32_t m0 = plane_mask(r, fp), m1 = plane_mask(r + 3, fp), m2 = plane_mask(r + 6, fp);
+    // m01: the planes both r0 and r1 are behind (the parent's culling
+    // candidates too); r2 and the parent's new vertex are tested only there
+    const uint32_t m0 = plane_mask(r, fp);
+    const uint32_t m01 = m0 ? plane_mask(r + 3, fp, m0) : 0u;
+    const uint32_t m012 = m01 ? plane_mask(r + 6, fp, m01) : 0u;
     const bool big = edge_big(r, r + 3, fp.q);
-    split = (m0 & m1 & m2) == 0u && big && d < (int)max_depth;
+    split = m012 == 0u && big && d < (int)max_depth;
     merge = false;
     if (!split && d >= 1) {
         float nv[3];
         new_vertex(nv);
-        const bool pvis = (plane_mask(nv, fp) & m0 & m1) == 0u;
+        const bool pvis = (m01 ? plane_mask(nv, fp, m01) : 0u) == 0u;
         float a[3], b[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
