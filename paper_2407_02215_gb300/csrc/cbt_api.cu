@@ -274,6 +274,8 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
     d.status = reinterpret_cast<unsigned long long*>(region + B->L.status);
     std::vector<Inst> insts(n);
     for (uint32_t b = 0; b < n; ++b) insts[b] = states[b]->inst;
+    std::memset(&d.inst0, 0, sizeof(Inst));
+    if (n == 1) d.inst0 = insts[0];
     int rc = CBT_OK;
     if (cudaMemcpyAsync(region + B->L.inst, insts.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, s) ||
         cudaMemsetAsync(d.bg, 0, sizeof(BatchGlobals), s) ||
@@ -552,6 +554,7 @@ extern "C" int cbt_attach_point_cache(cbt_state* st, void* memory, size_t bytes,
         cudaStreamSynchronize(s) != cudaSuccess)
         return CBT_ECUDA;
     st->inst = I;
+    st->self->dev.inst0 = I;
     return CBT_OK;
 }
 

@@ -176,6 +176,7 @@ struct BatchDev {
     const Inst* inst;     // [B]
     const FrameP* fps;    // [B] in device memory, or null: fp0 for every instance
     FrameP fp0;
+    Inst inst0;           // B == 1: a copy of inst[0] (read from the launch's parameters)
     uint32_t B;
     uint32_t tw;          // word-tile size of the reduction and free-list kernels
     uint32_t* tile_base;  // [B+1]
@@ -237,7 +238,7 @@ __device__ __forceinline__ void set_err(Globals* g, uint32_t e) { atomicOr(&g->e
 // rows of M are barycentric), so only the first two columns are carried
 // and the third is 2^k minus them. W = 2^d M exactly while entries fit T
 // (T = u32 for d <= 31).
-struct DecTable {
+struct alignas(16) DecTable {
     uint16_t p[256][9];
 };
 
@@ -260,14 +261,17 @@ constexpr DecTable make_dec8() {
     return t;
 }
 
-__constant__ DecTable c_dec8 = make_dec8();
+// In global memory, not constant memory: the copy below reads it with a
+// different address in every lane, which the constant cache serializes.
+__device__ const DecTable g_dec8 = make_dec8();
 constexpr uint32_t kDecTabWords = 256u * 9u / 2u;  // the table in 32-bit words
 
-// Copies the eight-level table into shared memory (kDecTabWords words; call
-// with the whole block, then __syncthreads()).
+// Copies the eight-level table into shared memory (kDecTabWords words, s_tab
+// 16-byte aligned; call with the whole block, then __syncthreads()).
 __device__ __forceinline__ void load_dec6(uint32_t* s_tab) {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(&c_dec8.p[0][0]);
-    for (uint32_t k = threadIdx.x; k < kDecTabWords; k += blockDim.x) s_tab[k] = src[k];
+    const uint4* src = reinterpret_cast<const uint4*>(&g_dec8.p[0][0]);
+    for (uint32_t k = threadIdx.x; k < kDecTabWords / 4u; k += blockDim.x)
+        reinterpret_cast<uint4*>(s_tab)[k] = __ldg(src + k);
 }
 
 // One level on the first two columns, a[2 r + c] (c = 0, 1).

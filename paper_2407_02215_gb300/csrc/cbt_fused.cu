@@ -654,8 +654,9 @@ __device__ void free_list(const BatchDev& bt, FCtx& c, uint32_t* s_w, bool all_g
             }
             __syncthreads();
             uint64_t r = zeros_before + s_w[warp] + (inc - mine);
+            uint32_t* const freel = I.freel;  // in a register across the stores
             while (z && r < bound) {
-                I.freel[r] = w * 32u + (uint32_t)(__ffs(z) - 1);
+                freel[r] = w * 32u + (uint32_t)(__ffs(z) - 1);
                 ++r;
                 z &= z - 1u;
             }
@@ -936,11 +937,8 @@ __device__ void phase_compact(const BatchDev& bt, FCtx& c, const uint32_t* s_tab
 // evaluate), and the new ones are listed and evaluated densely by the block
 // (so that no warp idles beside one evaluating lane); otherwise the slot and
 // heap ID of the next round are loaded while the current one is evaluated.
-__device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_tab, uint32_t* s_list,
-                               uint32_t* s_n) {
-    ctx_tile(bt, bt.tile_base, 0, 1, c);
-    const Inst& I = c.I;
-    const FrameP& fp = c.fp;
+__device__ void vertices_of(const Inst& I, const FrameP& fp, const uint32_t* s_tab, uint32_t* s_list,
+                            uint32_t* s_n) {
     if (!fp.vout) return;
     const uint32_t n = min(__ldcg(I.sums + 1), fp.vcap);
     const uint32_t stride = gridDim.x * kFThreads;
@@ -991,11 +989,12 @@ __device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_ta
         evaluate(*s_n);
         return;
     }
-    // warp-uniform rounds of 32 consecutive rows, staged per warp in s_list
-    // (8 warps x 288 floats) and stored 16 bytes wide
+    // warp-uniform rounds of 32 consecutive rows (warp-major over the grid,
+    // so that rows of costly regions spread over the SMs), staged per warp in
+    // s_list (8 warps x 288 floats) and stored 16 bytes wide
     const uint32_t lane = threadIdx.x & 31u;
     float* stage = reinterpret_cast<float*>(s_list) + 288u * (threadIdx.x >> 5);
-    uint32_t w0 = blockIdx.x * kFThreads + (threadIdx.x & ~31u);
+    uint32_t w0 = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u;
     uint64_t j = w0 + lane < n ? I.heap[I.live[w0 + lane]] : 0ull;
     for (; w0 < n; w0 += stride) {
         const uint32_t i = w0 + lane;
@@ -1013,10 +1012,15 @@ __device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_ta
         j = jn;
     }
 }
+__device__ void phase_vertices(const BatchDev& bt, FCtx& c, const uint32_t* s_tab, uint32_t* s_list,
+                               uint32_t* s_n) {
+    ctx_tile(bt, bt.tile_base, 0, 1, c);
+    vertices_of(c.I, c.fp, s_tab, s_list, s_n);
+}
 
 __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame(BatchDev bt) {
     __shared__ FCtx s_c;
-    __shared__ uint32_t s_tab[kDecTabWords];
+    __shared__ __align__(16) uint32_t s_tab[kDecTabWords];
     __shared__ __align__(16) uint32_t s_buf[kFBuf];
     __shared__ Pair s_warp[kFThreads / 32 + 1];
     __shared__ uint32_t s_red[4 * (kFThreads / 32)];
@@ -1232,8 +1236,8 @@ __device__ __forceinline__ uint32_t scan_ipt1(uint32_t N) {
 // reads the live count itself. The chain-mark words of the live slots are
 // cleared unless the last frame (this kernel) left them 0.
 __device__ void phase_prep1(const BatchDev& bt, uint32_t tbits) {
-    const Inst& I = bt.inst[0];
-    const FrameP& fp = frame_of(bt, 0);
+    const Inst& I = bt.inst0;
+    const FrameP& fp = bt.fp0;
     const uint32_t N = __ldcg(I.sums + 1);
     const uint32_t nt = I.cap >> tbits;
     const uint32_t ipt = scan_ipt1(N), S = ipt * kFThreads, T = (N + S - 1u) / S;
@@ -1310,19 +1314,23 @@ __device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, ui
     if (threadIdx.x == 0) *s_n = 0;
     stats_reset(s_cnt);
     ctx_tile(bt, bt.tile_base, 0, 1, c);
-    const Inst& I = c.I;
-    const FrameP& fp = c.fp;
+    const Inst& I = bt.inst0;
+    const FrameP& fp = bt.fp0;
     const uint32_t N = c.N;
     const uint32_t S = kFThreads * bt.bg->scan_ipt;
     unsigned long long* wc = wish_counts(bt);
     const uint64_t key = splitmix64(((uint64_t)fp.seed << 32) | (uint64_t)fp.frame);
     const bool cache = vc_form(fp) && fp.vout;
+    // 32-item chunks, warp-major (chunk c to warp c mod (warps of the grid),
+    // warps numbered across the blocks first), so that the costly parts of
+    // the list (in slot order, i.e. clustered in space) spread over the SMs;
+    // the loop runs while the block's first warp has items
     const uint32_t stride = gridDim.x * kFThreads;
-    uint32_t i = blockIdx.x * kFThreads + threadIdx.x;
+    uint32_t i = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + (threadIdx.x & 31u);
     uint32_t sa = i < N ? I.live[i] : 0u;
     uint64_t ja = i < N ? I.heap[sa] : 0ull;
     uint32_t sb = i + stride < N ? I.live[i + stride] : 0u;
-    for (uint32_t base = blockIdx.x * kFThreads; base < N; base += stride, i += stride) {
+    for (uint32_t base = blockIdx.x * 32u; base < N; base += stride, i += stride) {
         const uint32_t sc = i + 2u * stride < N ? I.live[i + 2u * stride] : 0u;
         const uint64_t jb = i + stride < N ? I.heap[sb] : 0ull;
         bool split = false;
@@ -1380,8 +1388,8 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
                              uint32_t* s_tmp, uint32_t* s_n1) {
     stats_reset(s_cnt);
     ctx_tile(bt, bt.tile_base, 0, 1, c);
-    const Inst& I = c.I;
-    const FrameP& fp = c.fp;
+    const Inst& I = bt.inst0;
+    const FrameP& fp = bt.fp0;
     const uint32_t T = bt.bg->total_stiles, S = kFThreads * bt.bg->scan_ipt;
     if (threadIdx.x == 0) s_tmp[0] = s_tmp[1] = 0;
     if (T > kMaxTiles1) {  // the host keeps pools within the tables
@@ -1440,16 +1448,18 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
     };
     if (threadIdx.x == 0) *s_n1 = 0;
     __syncthreads();
-    // a block takes 256 consecutive entries per round (neighbouring entries
-    // walk neighbouring records, which its L1 then holds); a thread loads
-    // the entries of four rounds together
+    // a warp takes 32 consecutive entries per round (neighbouring entries
+    // walk neighbouring records, which its L1 then holds), warp-major over
+    // the grid so that every SM gets its share of a short list; a thread
+    // loads the entries of four rounds together
     const uint32_t stride = gridDim.x * kFThreads;
-    for (uint32_t c0 = blockIdx.x * kFThreads; c0 < n; c0 += 4u * stride) {  // block-uniform
+    const uint32_t mine = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + (threadIdx.x & 31u);
+    for (uint32_t c0 = 0; c0 + blockIdx.x * 32u < n; c0 += 4u * stride) {  // block-uniform
         uint32_t qq[4];
         uint4 e[4];
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t q = c0 + k * stride + threadIdx.x;
+            const uint32_t q = c0 + k * stride + mine;
             qq[k] = q < n ? q : kNull;
             e[k] = qq[k] != kNull ? wl[qq[k]] : make_uint4(0u, 0u, 0u, 0u);
         }
@@ -1526,11 +1536,11 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
     uint32_t* s_list = s_buf;          // local item indices to validate
     uint32_t* s_fate = s_buf + kFBuf / 2;  // their fates, by local item index
     if (T > kMaxTiles1 || S > kFBuf / 2) {  // the host keeps pools within the tables
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(bt.inst[0].g, kErrOverflow);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(bt.inst0.g, kErrOverflow);
         return;
     }
     if (all_granted && blockIdx.x == 0 && threadIdx.x == 0) {
-        Globals* g = bt.inst[0].g;
+        Globals* g = bt.inst0.g;
         g->stats[kStSplitGranted] = __ldcg(&g->stats[kStSplitWishes]);
         g->stats[kStMergeGranted] = __ldcg(&g->stats[kStMergeCand]);
     }
@@ -1538,7 +1548,7 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
         if (threadIdx.x == 0) *s_n = 0;
         stats_reset(s_cnt);
         ctx_tile(bt, bt.stile_base, t, T, c);
-        const Inst& I = c.I;
+        const Inst& I = bt.inst0;
         const uint32_t N = c.N;
         const uint32_t* marks = chain_marks(I);
         const uint32_t i0 = stile_first(c, ipt);
@@ -1650,7 +1660,7 @@ __device__ void phase_fill1(const BatchDev& bt, FCtx& c, bool all_granted, uint3
                             Pair* s_warp) {
     stats_reset(s_cnt);
     ctx_tile(bt, bt.tile_base, 0, 1, c);
-    const Inst& I = c.I;
+    const Inst& I = bt.inst0;
     const uint32_t T = bt.bg->total_stiles, S = kFThreads * bt.bg->scan_ipt;
     uint32_t* s_cpre = s_buf;
     uint32_t* s_apre = s_buf + kMaxTiles1;
@@ -1677,7 +1687,10 @@ __device__ void phase_fill1(const BatchDev& bt, FCtx& c, bool all_granted, uint3
     }
     const DestTiles dm{s_apre, min(carry.b, bound)};
     uint32_t relinked = 0;
-    for (uint32_t q = blockIdx.x * kFThreads + threadIdx.x; q < C; q += gridDim.x * kFThreads) {
+    // 32 records per warp, warp-major over the grid: with fewer records than
+    // threads, every SM still gets its share
+    for (uint32_t q = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + (threadIdx.x & 31u); q < C;
+         q += gridDim.x * kFThreads) {
         uint32_t lo = 0, hi = T;  // the last tile whose first record is at or before q
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
@@ -1699,24 +1712,17 @@ __device__ void phase_fill1(const BatchDev& bt, FCtx& c, bool all_granted, uint3
 // P6 (single instance). Every block computes each word tile's new count
 // from the tile counts of the frame (no bitfield read) and scans them into
 // shared memory: the new live count and each tile's first row. Block 0
-// writes the nodes above the tiles as differences of that scan; each word
-// tile's node and the nodes below it are rebuilt from its words (and the
-// count checked against them). Rows of the new live
-// list (Alg. 7 for every index) go to warps in chunks of at most 256: a warp
-// finds its first row's word from the scan and the tile's popcounts, then
-// reads the bitfield 32 words at a time, staging the set positions in
-// shared memory, and writes the chunk's live slots and, with `rows_out`,
-// their vertices.
-__device__ void phase_final1(const BatchDev& bt, FCtx& c, const uint32_t* s_tab, uint32_t* s_buf, float* s_vst,
-                             Pair* s_warp, uint32_t* s_tmp, uint32_t tbits, bool rows_out) {
+// writes the nodes above the tiles as differences of that scan; a warp per
+// word tile rebuilds the tile's node and the nodes below it from its words
+// (the count checked against the scan) and writes the tile's rows of the new
+// live list. The vertices follow in their own phase, over the whole list.
+__device__ void phase_final1(const BatchDev& bt, FCtx& c, uint32_t* s_buf, Pair* s_warp, uint32_t* s_tmp,
+                             uint32_t tbits) {
     ctx_tile(bt, bt.tile_base, 0, 1, c);
-    const Inst& I = c.I;
-    const FrameP& fp = c.fp;
+    const Inst& I = bt.inst0;
     const uint32_t W = I.W, TW = min(W, bt.tw), nt = I.cap >> tbits;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     uint32_t* s_tpre = s_buf;
-    uint32_t* s_rows = s_buf + kMaxTiles1 + 256u * warp;
-    float* vst = s_vst + 288u * warp;
     if (nt > kMaxTiles1 || TW > 64u) {  // the host keeps pools within the tables
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(I.g, kErrOverflow);
         return;
@@ -1756,133 +1762,79 @@ __device__ void phase_final1(const BatchDev& bt, FCtx& c, const uint32_t* s_tab,
             if (nt == 1u) I.sums[1] = Nn;
         }
     }
-    // word tiles: their levels below the tile node (TW <= 64: the levels of
-    // one warp, then the node, which the fill kept, over two warps)
-    for (uint32_t wt = blockIdx.x; wt < nt; wt += gridDim.x) {
-        const uint32_t w = wt * TW + threadIdx.x;
-        const bool mine = threadIdx.x < TW;
-        const uint32_t pc = mine ? __popc(__ldcg(I.bits + w)) : 0u;
-        if (mine && TW > 1u) I.sums[W + w] = pc;
-        uint32_t v = pc;
+    // word tiles, one warp each (TW <= 64 words: lane holds words lane and
+    // 32 + lane): the levels below the tile node (whose value, from the
+    // scan, is checked against the words' popcounts), then the tile's slice
+    // of the new live list (Alg. 7 for every index, in slot order): word by
+    // word, lane b tests bit b and the set ones take consecutive rows, so
+    // every store of the list is one contiguous run
+    // the instance's fields in registers (a store through a generic pointer
+    // would otherwise make the compiler reload them from shared memory)
+    uint32_t* const marks = chain_marks(I);
+    uint32_t* const live = I.live;
+    uint32_t* const sums = I.sums;
+    const uint32_t* const bits = I.bits;
+    const uint32_t cap = I.cap;
+    if (blockIdx.x == 0 && threadIdx.x == 0) I.g->marks_clean = 1u;  // read by the next frame
+    const uint32_t nwarps = gridDim.x * (kFThreads / 32u);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (uint32_t wt = warp * gridDim.x + blockIdx.x; wt < nt; wt += nwarps) {  // warp-major: tiles spread over SMs
+        const uint32_t w0 = wt * TW + lane, w1 = w0 + 32u;
+        const uint32_t x0 = lane < TW ? __ldcg(bits + w0) : 0u;
+        const uint32_t x1 = 32u + lane < TW ? __ldcg(bits + w1) : 0u;
+        uint32_t v0 = __popc(x0), v1 = __popc(x1);
+        if (TW > 1u) {
+            if (lane < TW) sums[W + w0] = v0;
+            if (32u + lane < TW) sums[W + w1] = v1;
+        }
 #pragma unroll
         for (uint32_t L = 1; L <= 5; ++L) {
-            v += __shfl_down_sync(0xFFFFFFFFu, v, 1u << (L - 1u));
-            if ((1u << L) < TW && mine && (threadIdx.x & ((1u << L) - 1u)) == 0u) I.sums[(W + w) >> L] = v;
-        }
-        if (lane == 0 && warp * 32u < TW) atomicAdd(&s_tmp[0], v);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const uint32_t node = (wt + 1u < nt ? s_tpre[wt + 1u] : Nn) - s_tpre[wt];
-            if (s_tmp[0] != node) set_err(I.g, kErrLink);
-            if (nt > 1u) I.sums[nt + wt] = node;  // (a single tile's node is the root, written above)
-            s_tmp[0] = 0;
-        }
-        __syncthreads();
-    }
-    // rows
-    uint32_t* marks = chain_marks(I);
-    if (blockIdx.x == 0 && threadIdx.x == 0) I.g->marks_clean = 1u;  // read by the next frame
-    const uint32_t nw = gridDim.x * (kFThreads / 32u);
-    uint32_t R = (Nn + nw - 1u) / nw;
-    R = max(32u, min(256u, (R + 31u) & ~31u));
-    const uint32_t nch = (Nn + R - 1u) / R;
-    for (uint32_t ch = blockIdx.x * (kFThreads / 32u) + warp; ch < nch; ch += nw) {
-        const uint32_t r0 = ch * R, r1 = min(Nn, r0 + R);
-        uint32_t lo = 0, hi = nt;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (s_tpre[mid] <= r0)
-                lo = mid + 1u;
-            else
-                hi = mid;
-        }
-        const uint32_t t = lo - 1u;
-        uint32_t rank = r0 - s_tpre[t];
-        uint32_t wcur = t * TW, skip = 0;
-        for (uint32_t w0 = t * TW; w0 < (t + 1u) * TW; w0 += 32u) {  // the word of set bit `rank` of the tile
-            const uint32_t wi = w0 + lane;
-            const uint32_t pc = wi < (t + 1u) * TW ? __popc(__ldcg(I.bits + wi)) : 0u;
-            uint32_t inc = pc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-                if ((int)lane >= o) inc += y;
+            v0 += __shfl_down_sync(0xFFFFFFFFu, v0, 1u << (L - 1u));
+            v1 += __shfl_down_sync(0xFFFFFFFFu, v1, 1u << (L - 1u));
+            if ((1u << L) < TW && (lane & ((1u << L) - 1u)) == 0u) {
+                if (lane < TW) sums[(W + w0) >> L] = v0;
+                if (32u + lane < TW) sums[(W + w1) >> L] = v1;
             }
-            const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            if (rank < total) {
-                const uint32_t L = (uint32_t)(__ffs(__ballot_sync(0xFFFFFFFFu, inc > rank)) - 1);
-                wcur = w0 + L;
-                skip = rank - __shfl_sync(0xFFFFFFFFu, inc - pc, L);
-                break;
-            }
-            rank -= total;
+        }
+        const uint32_t half0 = __shfl_sync(0xFFFFFFFFu, v0, 0), half1 = __shfl_sync(0xFFFFFFFFu, v1, 0);
+        const uint32_t r0 = s_tpre[wt];
+        const uint32_t node = (wt + 1u < nt ? s_tpre[wt + 1u] : Nn) - r0;
+        if (lane == 0) {
+            if (half0 + half1 != node) set_err(I.g, kErrLink);
+            if (nt > 1u) sums[nt + wt] = node;  // (a single tile's node is the root, written above)
         }
         uint32_t row = r0;
-        bool first = true;
-        while (row < r1) {
-            if (wcur >= W) {  // fewer set bits than the tile nodes count
-                if (lane == 0) set_err(I.g, kErrLink);
-                break;
+        const uint32_t n0 = min(TW, 32u);
+#pragma unroll 4
+        for (uint32_t i = 0; i < n0; ++i) {
+            const uint32_t x = __shfl_sync(0xFFFFFFFFu, x0, i);
+            const bool set = (x >> lane) & 1u;
+            const uint32_t r = row + __popc(x & lt_mask);
+            if (set && r < cap) {
+                const uint32_t sl = (wt * TW + i) * 32u + lane;
+                live[r] = sl;
+                marks[sl] = 0u;  // for the next frame's chain marks
             }
-            const uint32_t wi = wcur + lane;
-            uint32_t v = wi < W ? __ldcg(I.bits + wi) : 0u;
-            if (first && lane == 0)
-                for (uint32_t k = 0; k < skip; ++k) v &= v - 1u;
-            const uint32_t pc = __popc(v);
-            uint32_t inc = pc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-                if ((int)lane >= o) inc += y;
+            row += __popc(x);
+        }
+        for (uint32_t i = 0; i + 32u < TW; ++i) {
+            const uint32_t x = __shfl_sync(0xFFFFFFFFu, x1, i);
+            const bool set = (x >> lane) & 1u;
+            const uint32_t r = row + __popc(x & lt_mask);
+            if (set && r < cap) {
+                const uint32_t sl = (wt * TW + 32u + i) * 32u + lane;
+                live[r] = sl;
+                marks[sl] = 0u;
             }
-            const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-            const uint32_t need = r1 - row;
-            uint32_t o = inc - pc;
-            while (v && o < need) {
-                s_rows[o++] = wi * 32u + (uint32_t)(__ffs(v) - 1);
-                v &= v - 1u;
-            }
-            __syncwarp();
-            const uint32_t ne = min(total, need);
-            uint64_t jn = rows_out && lane < ne ? I.heap[s_rows[lane]] : 0ull;
-            for (uint32_t k0 = 0; k0 < ne; k0 += 32u) {
-                const uint32_t k = k0 + lane;
-                const bool valid = k < ne;
-                const uint32_t sl = valid ? s_rows[k] : 0u;
-                if (valid) {
-                    I.live[row + k] = sl;
-                    marks[sl] = 0u;  // for the next frame's chain marks
-                }
-                if (rows_out) {
-                    const uint64_t j = jn;
-                    jn = k + 32u < ne ? I.heap[s_rows[k + 32u]] : 0ull;
-                    const uint32_t r = row + k0;
-                    const uint32_t nv = fp.vcap > r ? min(min(32u, ne - k0), fp.vcap - r) : 0u;
-                    float x[9];
-                    bool ok = true;
-                    if (lane < nv) ok = vertex_eval(I, fp, j, s_tab, x);
-                    if (nv && __all_sync(0xFFFFFFFFu, ok)) {
-                        warp_rows_out(x, vst, fp.vout, r, nv);
-                    } else if (lane < nv && ok) {  // a row the decode refused stays unwritten
-                        float* out = fp.vout + 9ull * (r + lane);
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) out[q] = x[q];
-                    }
-                }
-            }
-            __syncwarp();
-            row += ne;
-            wcur += 32u;
-            first = false;
+            row += __popc(x);
         }
     }
 }
 
 __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(BatchDev bt, uint32_t tbits) {
     __shared__ FCtx s_c;
-    __shared__ uint32_t s_tab[kDecTabWords];
+    __shared__ __align__(16) uint32_t s_tab[kDecTabWords];
     __shared__ __align__(16) uint32_t s_buf[kFBuf];
-    __shared__ __align__(16) float s_vst[288 * (kFThreads / 32)];
     __shared__ Pair s_warp[kFThreads / 32 + 1];
     __shared__ uint32_t s_red[4 * (kFThreads / 32)];
     __shared__ uint32_t s_cnt[kBlockStats];
@@ -1907,7 +1859,7 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
     phase_walks1(bt, s_c, s_cnt, s_buf, s_warp, s_tmp, &s_n);
     sync();
     stamp(bt, 3);
-    const Globals* g = s_c.I.g;
+    const Globals* g = bt.inst0.g;
     const bool all_granted = __ldcg(&g->rq_merge) + __ldcg(&g->rq_split) <= (unsigned long long)s_c.F;
     if (!all_granted) {
         phase_gate(bt, s_c, s_cnt, s_red, s_warp, s_tmp, &s_n, reinterpret_cast<uint2*>(s_buf), true);
@@ -1920,12 +1872,11 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
     phase_fill1(bt, s_c, all_granted, s_cnt, s_buf, s_warp);
     sync();
     stamp(bt, 6);
-    const bool cached = vc_form(s_c.fp) && s_c.fp.vout;
-    phase_final1(bt, s_c, s_tab, s_buf, s_vst, s_warp, s_tmp, tbits, s_c.fp.vout && !cached);
-    if (cached) {
+    phase_final1(bt, s_c, s_buf, s_warp, s_tmp, tbits);
+    if (bt.fp0.vout) {
         sync();
         stamp(bt, 7);
-        phase_vertices(bt, s_c, s_tab, s_buf, &s_n);
+        vertices_of(bt.inst0, bt.fp0, s_tab, s_buf, &s_n);
     } else {
         stamp(bt, 7);
     }
@@ -1934,7 +1885,7 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
         if (bt.timing) atomicMax(&bt.bg->t[kFramePhases], global_ns());
         if (blockIdx.x == 0) {
             bt.bg->bar_epoch = epoch + nbar * gridDim.x;
-            if (ld_volatile(&bt.bg->abort)) set_err(bt.inst[0].g, kErrTimeout);
+            if (ld_volatile(&bt.bg->abort)) set_err(bt.inst0.g, kErrTimeout);
         }
     }
 }

@@ -133,7 +133,7 @@ __device__ __forceinline__ uint32_t live_n(const Inst& I, uint32_t cap) {
 
 __global__ void __launch_bounds__(kIThreads) k_index_insert(Inst I, const uint32_t* corner, IndexWs ws,
                                                             uint32_t cap) {
-    __shared__ uint32_t s_tab[kDecTabWords];
+    __shared__ __align__(16) uint32_t s_tab[kDecTabWords];
     load_dec6(s_tab);
     __syncthreads();
     const uint32_t N = live_n(I, cap);

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev bt) {
     __shared__ Inst s_I;
     __shared__ FrameP s_fp;
     __shared__ uint32_t s_cnt[kBlockStats];
-    __shared__ uint32_t s_tab[kDecTabWords];
+    __shared__ __align__(16) uint32_t s_tab[kDecTabWords];
     load_dec6(s_tab);
     const uint32_t T = ld_volatile(&bt.bg->total_tiles);
     for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_vertices(BatchDev bt) {
     __shared__ uint32_t s_b;
     __shared__ Inst s_I;
     __shared__ FrameP s_fp;
-    __shared__ uint32_t s_tab[kDecTabWords];
+    __shared__ __align__(16) uint32_t s_tab[kDecTabWords];
     __shared__ __align__(16) float s_stage[kThreads / 32][288];  // per warp: 32 rows of 9 floats
     load_dec6(s_tab);
     const uint32_t lane = threadIdx.x & 31u;
