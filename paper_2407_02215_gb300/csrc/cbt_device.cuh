@@ -100,7 +100,9 @@ struct Globals {
     uint32_t nwalk;  // single-instance frame: entries of the frame's walk list
     uint32_t marks_clean;  // 1 when the chain-mark words (chg) of the live slots are 0 (the
                            // single-instance frame leaves them so; the other frames clear this)
-    uint32_t pad[64 - 38];
+    uint32_t freel_full;   // 1 when freel lists every zero bit of the bitfield in slot order
+                           // (the single-instance frame leaves it so; the other frames clear this)
+    uint32_t pad[64 - 39];
 };
 static_assert(sizeof(Globals) == 256, "Globals must be 256 bytes");
 static_assert(10 + kStCount + 1 == 24, "pc_gen must sit at byte 96");
@@ -237,37 +239,54 @@ __device__ __forceinline__ void set_err(Globals* g, uint32_t e) { atomicOr(&g->e
 // entry of P_c is at most 2^8 (16 bits). Every row of W sums to 2^k (the
 // rows of M are barycentric), so only the first two columns are carried
 // and the third is 2^k minus them. W = 2^d M exactly while entries fit T
-// (T = u32 for d <= 31).
+// (T = u32 for d <= 31). The first r < 8 levels from the identity are the
+// first two columns of the r-level product, tabulated too (q: r-level
+// entries for the 2^r prefixes c at q[2^r - 2 + c]).
 struct alignas(16) DecTable {
     uint16_t p[256][9];
+    uint16_t q[256][6];  // 254 used
 };
+
+constexpr void dec_product(int c, int levels, uint32_t m[9]) {
+    for (int e = 0; e < 9; ++e) m[e] = (e % 4 == 0) ? 1u : 0u;
+    for (int k = levels - 1; k >= 0; --k) {
+        const int b = (c >> k) & 1;
+        uint32_t n[9] = {};
+        for (int col = 0; col < 3; ++col) {
+            n[6 + col] = m[col] + m[3 + col];
+            n[col] = 2u * (b ? m[6 + col] : m[col]);
+            n[3 + col] = 2u * (b ? m[3 + col] : m[6 + col]);
+        }
+        for (int e = 0; e < 9; ++e) m[e] = n[e];
+    }
+}
 
 constexpr DecTable make_dec8() {
     DecTable t{};
     for (int c = 0; c < 256; ++c) {
-        uint32_t m[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-        for (int k = 7; k >= 0; --k) {
-            const int b = (c >> k) & 1;
-            uint32_t n[9] = {};
-            for (int col = 0; col < 3; ++col) {
-                n[6 + col] = m[col] + m[3 + col];
-                n[col] = 2u * (b ? m[6 + col] : m[col]);
-                n[3 + col] = 2u * (b ? m[3 + col] : m[6 + col]);
-            }
-            for (int e = 0; e < 9; ++e) m[e] = n[e];
-        }
+        uint32_t m[9] = {};
+        dec_product(c, 8, m);
         for (int e = 0; e < 9; ++e) t.p[c][e] = static_cast<uint16_t>(m[e]);
     }
+    for (int r = 1; r < 8; ++r)
+        for (int c = 0; c < (1 << r); ++c) {
+            uint32_t m[9] = {};
+            dec_product(c, r, m);
+            for (int row = 0; row < 3; ++row)
+                for (int col = 0; col < 2; ++col)
+                    t.q[(1 << r) - 2 + c][2 * row + col] = static_cast<uint16_t>(m[3 * row + col]);
+        }
     return t;
 }
 
 // In global memory, not constant memory: the copy below reads it with a
 // different address in every lane, which the constant cache serializes.
 __device__ const DecTable g_dec8 = make_dec8();
-constexpr uint32_t kDecTabWords = 256u * 9u / 2u;  // the table in 32-bit words
+constexpr uint32_t kDecTabWords = sizeof(DecTable) / 4u;  // the table in 32-bit words
+static_assert(sizeof(DecTable) % 16u == 0u, "the table is copied 16 bytes at a time");
 
-// Copies the eight-level table into shared memory (kDecTabWords words, s_tab
-// 16-byte aligned; call with the whole block, then __syncthreads()).
+// Copies the tables into shared memory (kDecTabWords words, s_tab 16-byte
+// aligned; call with the whole block, then __syncthreads()).
 __device__ __forceinline__ void load_dec6(uint32_t* s_tab) {
     const uint4* src = reinterpret_cast<const uint4*>(&g_dec8.p[0][0]);
     for (uint32_t k = threadIdx.x; k < kDecTabWords / 4u; k += blockDim.x)
@@ -321,8 +340,13 @@ __device__ __forceinline__ void decode_weights(uint64_t j, int d, T W[9], T Wp[9
     if (d >= 1) {
         int lvl = d - 1;  // path bit applied next; the parent covers bits d-1 .. 1
         const int rem = (d - 1) & 7;
-#pragma unroll 1
-        for (int k = 0; k < rem; ++k, --lvl) dec_step<T>(a, (j >> lvl) & 1ull);
+        if (rem) {  // the first rem levels from the identity: one lookup
+            const uint32_t c = (uint32_t)((j >> (lvl - rem + 1)) & ((1ull << rem) - 1ull));
+            const uint16_t* Q = tab16 + 256u * 9u + 6u * ((1u << rem) - 2u + c);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a[k] = Q[k];
+            lvl -= rem;
+        }
 #pragma unroll 1
         for (; lvl >= 8; lvl -= 8) dec_chunk<T>(a, tab16 + 9u * (uint32_t)((j >> (lvl - 7)) & 255ull));
         dec_expand<T>(a, (T)1 << (d - 1), Wp);

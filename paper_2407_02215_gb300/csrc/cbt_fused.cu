@@ -198,6 +198,7 @@ __device__ void phase_prep(const BatchDev& bt, Pair* s_warp, uint32_t* s_tmp) {
                 g->C = 0;
                 g->done = 0;
                 g->marks_clean = 0;
+                g->freel_full = 0;
                 tiles = (N + kTileItems - 1u) / kTileItems;
                 stiles = (N + S - 1u) / S;
                 g->ntiles = tiles;
@@ -1293,25 +1294,25 @@ __device__ void phase_prep1(const BatchDev& bt, uint32_t tbits) {
     }
 }
 
-// Appends the block's walk entries to the frame's walk list (one reservation
-// per block and flush, coalesced copy). Call with the whole block.
-__device__ __forceinline__ void walks_out(const Inst& I, const uint4* s_list, uint32_t n, uint32_t* s_tmp) {
-    if (threadIdx.x == 0) s_tmp[0] = n ? atomicAdd(&I.g->nwalk, n) : 0u;
-    __syncthreads();
-    const uint32_t base = s_tmp[0];
-    uint4* wl = walk_list_of(I);
-    for (uint32_t q = threadIdx.x; q < n; q += kFThreads) wl[base + q] = s_list[q];
-    __syncthreads();
-}
-
 // P1 (single instance): the live list strided over the whole grid, the slot
 // and heap ID of the next rounds loaded while the current item is classified.
-// Walk entries (live index | split flag << 31, slot) are listed per block
-// and flushed to the frame's walk list; split wishes are counted per scan
-// tile (warp-aggregated, consecutive live indices share a tile).
-__device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, uint32_t* s_cnt, uint32_t* s_n,
-                                uint4* s_list, uint32_t* s_tmp) {
-    if (threadIdx.x == 0) *s_n = 0;
+// Walk entries (live index | split flag << 31, slot, heap ID) are listed per
+// warp and flushed to the frame's walk list; split wishes are counted per
+// scan tile (warp-aggregated, consecutive live indices share a tile).
+// A warp's walk buffer (kWarpWalks entries of the block's shared list) out
+// to the frame's walk list: one atomic for the range, then a coalesced copy.
+constexpr uint32_t kWarpWalks = kWalkCap1 / (kFThreads / 32);
+__device__ __forceinline__ void warp_walks_out(const Inst& I, const uint4* s_wl, uint32_t n) {
+    if (n == 0u) return;  // warp-uniform
+    uint32_t base = 0;
+    if ((threadIdx.x & 31u) == 0u) base = atomicAdd(&I.g->nwalk, n);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    uint4* wl = walk_list_of(I);
+    for (uint32_t q = threadIdx.x & 31u; q < n; q += 32u) wl[base + q] = s_wl[q];
+    __syncwarp();
+}
+
+__device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, uint32_t* s_cnt, uint4* s_list) {
     stats_reset(s_cnt);
     ctx_tile(bt, bt.tile_base, 0, 1, c);
     const Inst& I = bt.inst0;
@@ -1321,47 +1322,50 @@ __device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, ui
     unsigned long long* wc = wish_counts(bt);
     const uint64_t key = splitmix64(((uint64_t)fp.seed << 32) | (uint64_t)fp.frame);
     const bool cache = vc_form(fp) && fp.vout;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint4* s_wl = s_list + kWarpWalks * (threadIdx.x >> 5);  // the warp's walk buffer
+    uint32_t nwl = 0;                                           // its entries (warp-uniform)
     // 32-item chunks, warp-major (chunk c to warp c mod (warps of the grid),
     // warps numbered across the blocks first), so that the costly parts of
     // the list (in slot order, i.e. clustered in space) spread over the SMs;
-    // the loop runs while the block's first warp has items
+    // the warps run independently (no block barrier in the loop)
     const uint32_t stride = gridDim.x * kFThreads;
-    uint32_t i = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + (threadIdx.x & 31u);
+    uint32_t i = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + lane;
     uint32_t sa = i < N ? I.live[i] : 0u;
     uint64_t ja = i < N ? I.heap[sa] : 0ull;
     uint32_t sb = i + stride < N ? I.live[i + stride] : 0u;
-    for (uint32_t base = blockIdx.x * 32u; base < N; base += stride, i += stride) {
+    for (; i - lane < N; i += stride) {  // warp-uniform
         const uint32_t sc = i + 2u * stride < N ? I.live[i + 2u * stride] : 0u;
         const uint64_t jb = i + stride < N ? I.heap[sb] : 0ull;
-        bool split = false;
+        bool split = false, walk = false;
         if (i < N) {
             const uint32_t cmd = classify_item(I, fp, key, i, sa, ja, s_tab, s_cnt, cache);
             split = (cmd & kSplitWish) != 0u;
-            const bool group = (cmd & kMergeWish) && !(cmd & kHeapOdd);
-            if (split || group)
-                s_list[atomicAdd(s_n, 1u)] = make_uint4(i | (split ? 0x80000000u : 0u), sa, (uint32_t)ja,
-                                                        (uint32_t)(ja >> 32));
+            walk = split || ((cmd & kMergeWish) && !(cmd & kHeapOdd));
         }
+        const unsigned wm = __ballot_sync(0xFFFFFFFFu, walk);
+        if (walk)
+            s_wl[nwl + __popc(wm & ((1u << lane) - 1u))] =
+                make_uint4(i | (split ? 0x80000000u : 0u), sa, (uint32_t)ja, (uint32_t)(ja >> 32));
+        nwl += __popc(wm);
         {  // split wishes per scan tile
             const uint32_t t = i / S;
             const unsigned m = __match_any_sync(0xFFFFFFFFu, i < N ? t : kNull);
             const uint32_t n = __popc(__ballot_sync(0xFFFFFFFFu, split) & m);
-            if (n && (threadIdx.x & 31u) == (uint32_t)(__ffs(m) - 1)) atomicAdd(&wc[t], (unsigned long long)n);
+            if (n && lane == (uint32_t)(__ffs(m) - 1)) atomicAdd(&wc[t], (unsigned long long)n);
         }
         sa = sb;
         ja = jb;
         sb = sc;
-        __syncthreads();
-        const uint32_t n = *s_n;
-        __syncthreads();
-        if (n > kWalkCap1 - kFThreads) {  // block-uniform
-            walks_out(I, s_list, n, s_tmp);
-            if (threadIdx.x == 0) *s_n = 0;
-            __syncthreads();
+        __syncwarp();
+        if (nwl > kWarpWalks - 32u) {  // warp-uniform: room for the next round
+            warp_walks_out(I, s_wl, nwl);
+            nwl = 0;
         }
     }
+    __syncwarp();
+    warp_walks_out(I, s_wl, nwl);
     __syncthreads();
-    walks_out(I, s_list, *s_n, s_tmp);
     stats_flush(s_cnt, I.g, kStSplitWishes);
     __syncthreads();
 }
@@ -1551,21 +1555,40 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
         const Inst& I = bt.inst0;
         const uint32_t N = c.N;
         const uint32_t* marks = chain_marks(I);
-        const uint32_t i0 = stile_first(c, ipt);
-        const uint32_t e0 = threadIdx.x * ipt;
+        const uint32_t ts = c.lt * S;  // the tile's first live index
+        const uint32_t e0 = threadIdx.x * ipt, i0 = ts + e0;
         uint32_t sl[kMaxIpt], cm[kMaxIpt], f[kMaxIpt];
+        {  // slots and command words loaded coalesced (item ts + k 256 + tid)
+           // through shared memory, then taken ipt consecutive per thread
+            uint32_t* s_sl = s_buf;
+            uint32_t* s_cm = s_buf + kFBuf / 2;
+            uint32_t a[kMaxIpt];
 #pragma unroll
-        for (uint32_t k = 0; k < kMaxIpt; ++k) sl[k] = (k < ipt && i0 + k < N) ? I.live[i0 + k] : kNull;
-#pragma unroll
-        for (uint32_t k = 0; k < kMaxIpt; ++k) {
-            cm[k] = sl[k] != kNull ? *cmd_ptr(I, sl[k]) : 0u;
-            if (all_granted && sl[k] != kNull) {
-                const uint32_t mk = marks[sl[k]];
-                if (mk) {
-                    cm[k] |= mk;
-                    atomicOr(cmd_ptr(I, sl[k]), mk);
-                }
+            for (uint32_t k = 0; k < kMaxIpt; ++k) {
+                const uint32_t e = k * kFThreads + threadIdx.x;
+                a[k] = (k < ipt && ts + e < N) ? I.live[ts + e] : kNull;
             }
+#pragma unroll
+            for (uint32_t k = 0; k < kMaxIpt; ++k) {
+                if (k >= ipt) continue;
+                uint32_t m = a[k] != kNull ? *cmd_ptr(I, a[k]) : 0u;
+                if (all_granted && a[k] != kNull) {
+                    const uint32_t mk = marks[a[k]];
+                    if (mk) {
+                        m |= mk;
+                        atomicOr(cmd_ptr(I, a[k]), mk);
+                    }
+                }
+                s_sl[k * kFThreads + threadIdx.x] = a[k];
+                s_cm[k * kFThreads + threadIdx.x] = m;
+            }
+            __syncthreads();
+#pragma unroll
+            for (uint32_t k = 0; k < kMaxIpt; ++k) {
+                sl[k] = k < ipt ? s_sl[e0 + k] : kNull;
+                cm[k] = k < ipt ? s_cm[e0 + k] : 0u;
+            }
+            __syncthreads();  // s_buf is the lists' below
         }
         // groups to validate: when every request is granted, every recorded
         // group without split bits at its charged member; else the granted
@@ -1647,7 +1670,9 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
         stats_flush(s_cnt, I.g, kStSplitBis, kStMergeGroups, kStMergedBis);
         __syncthreads();
     }
-    free_list(bt, c, s_w, all_granted, tile_counts(bt));
+    // the last frame's final phase listed every zero bit of this frame's
+    // starting bitfield, unless another form of the frame ran since
+    if (!__ldcg(&bt.inst0.g->freel_full)) free_list(bt, c, s_w, all_granted, tile_counts(bt));
 }
 
 // P5 (single instance): every block scans the tiles' (changed, allocation)
@@ -1762,71 +1787,79 @@ __device__ void phase_final1(const BatchDev& bt, FCtx& c, uint32_t* s_buf, Pair*
             if (nt == 1u) I.sums[1] = Nn;
         }
     }
-    // word tiles, one warp each (TW <= 64 words: lane holds words lane and
-    // 32 + lane): the levels below the tile node (whose value, from the
-    // scan, is checked against the words' popcounts), then the tile's slice
-    // of the new live list (Alg. 7 for every index, in slot order): word by
-    // word, lane b tests bit b and the set ones take consecutive rows, so
-    // every store of the list is one contiguous run
+    // word tiles (TW <= 64 words: lane holds words lane and 32 + lane): the
+    // levels below the tile node (whose value, from the scan, is checked
+    // against the words' popcounts), then the tile's slice of the new live
+    // list (Alg. 7 for every index, in slot order): word by word, lane b
+    // tests bit b and the set ones take consecutive rows, so every store of
+    // the list is one contiguous run
     // the instance's fields in registers (a store through a generic pointer
     // would otherwise make the compiler reload them from shared memory)
     uint32_t* const marks = chain_marks(I);
     uint32_t* const live = I.live;
+    uint32_t* const freel = I.freel;
     uint32_t* const sums = I.sums;
     const uint32_t* const bits = I.bits;
     const uint32_t cap = I.cap;
-    if (blockIdx.x == 0 && threadIdx.x == 0) I.g->marks_clean = 1u;  // read by the next frame
+    const uint32_t vmask = cap < 32u ? (1u << cap) - 1u : 0xFFFFFFFFu;  // the slots of a word
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // read by the next frame
+        I.g->marks_clean = 1u;
+        I.g->freel_full = 1u;
+    }
     const uint32_t nwarps = gridDim.x * (kFThreads / 32u);
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (uint32_t wt = warp * gridDim.x + blockIdx.x; wt < nt; wt += nwarps) {  // warp-major: tiles spread over SMs
+    // a word tile in Q parts of UW words, one warp each (warp-major over the
+    // grid); every part reads the tile's words for its prefix, the first
+    // also rebuilds the tile's levels of the sum tree
+    const uint32_t Q = TW >= 64u ? 4u : TW >= 32u ? 2u : 1u, UW = TW / Q;
+    for (uint32_t u = warp * gridDim.x + blockIdx.x; u < nt * Q; u += nwarps) {
+        const uint32_t wt = u / Q, q = u % Q;
         const uint32_t w0 = wt * TW + lane, w1 = w0 + 32u;
         const uint32_t x0 = lane < TW ? __ldcg(bits + w0) : 0u;
         const uint32_t x1 = 32u + lane < TW ? __ldcg(bits + w1) : 0u;
+        const uint32_t r0 = s_tpre[wt];
         uint32_t v0 = __popc(x0), v1 = __popc(x1);
-        if (TW > 1u) {
-            if (lane < TW) sums[W + w0] = v0;
-            if (32u + lane < TW) sums[W + w1] = v1;
-        }
+        // ones in the tile before the part's first word q UW
+        const uint32_t pre = __reduce_add_sync(0xFFFFFFFFu, (lane < q * UW ? v0 : 0u) + (32u + lane < q * UW ? v1 : 0u));
+        if (q == 0u) {
+            if (TW > 1u) {
+                if (lane < TW) sums[W + w0] = v0;
+                if (32u + lane < TW) sums[W + w1] = v1;
+            }
 #pragma unroll
-        for (uint32_t L = 1; L <= 5; ++L) {
-            v0 += __shfl_down_sync(0xFFFFFFFFu, v0, 1u << (L - 1u));
-            v1 += __shfl_down_sync(0xFFFFFFFFu, v1, 1u << (L - 1u));
-            if ((1u << L) < TW && (lane & ((1u << L) - 1u)) == 0u) {
-                if (lane < TW) sums[(W + w0) >> L] = v0;
-                if (32u + lane < TW) sums[(W + w1) >> L] = v1;
+            for (uint32_t L = 1; L <= 5; ++L) {
+                v0 += __shfl_down_sync(0xFFFFFFFFu, v0, 1u << (L - 1u));
+                v1 += __shfl_down_sync(0xFFFFFFFFu, v1, 1u << (L - 1u));
+                if ((1u << L) < TW && (lane & ((1u << L) - 1u)) == 0u) {
+                    if (lane < TW) sums[(W + w0) >> L] = v0;
+                    if (32u + lane < TW) sums[(W + w1) >> L] = v1;
+                }
+            }
+            const uint32_t half0 = __shfl_sync(0xFFFFFFFFu, v0, 0), half1 = __shfl_sync(0xFFFFFFFFu, v1, 0);
+            const uint32_t node = (wt + 1u < nt ? s_tpre[wt + 1u] : Nn) - r0;
+            if (lane == 0) {
+                if (half0 + half1 != node) set_err(I.g, kErrLink);
+                if (nt > 1u) sums[nt + wt] = node;  // (a single tile's node is the root, written above)
             }
         }
-        const uint32_t half0 = __shfl_sync(0xFFFFFFFFu, v0, 0), half1 = __shfl_sync(0xFFFFFFFFu, v1, 0);
-        const uint32_t r0 = s_tpre[wt];
-        const uint32_t node = (wt + 1u < nt ? s_tpre[wt + 1u] : Nn) - r0;
-        if (lane == 0) {
-            if (half0 + half1 != node) set_err(I.g, kErrLink);
-            if (nt > 1u) sums[nt + wt] = node;  // (a single tile's node is the root, written above)
-        }
-        uint32_t row = r0;
-        const uint32_t n0 = min(TW, 32u);
+        // the part's rows of the live list and, from its zero bits, of the
+        // next frame's free list (Alg. 8 for every rank; every earlier tile
+        // holds 2^tbits slots)
+        uint32_t row = r0 + pre, zrow = wt * TS - r0 + (q * UW * 32u - pre);
 #pragma unroll 4
-        for (uint32_t i = 0; i < n0; ++i) {
-            const uint32_t x = __shfl_sync(0xFFFFFFFFu, x0, i);
-            const bool set = (x >> lane) & 1u;
-            const uint32_t r = row + __popc(x & lt_mask);
-            if (set && r < cap) {
-                const uint32_t sl = (wt * TW + i) * 32u + lane;
+        for (uint32_t i = q * UW; i < (q + 1u) * UW; ++i) {
+            const uint32_t x = __shfl_sync(0xFFFFFFFFu, i < 32u ? x0 : x1, i & 31u);
+            const uint32_t z = ~x & vmask;
+            const uint32_t sl = (wt * TW + i) * 32u + lane;
+            const uint32_t r = row + __popc(x & lt_mask), zr = zrow + __popc(z & lt_mask);
+            if (((x >> lane) & 1u) && r < cap) {
                 live[r] = sl;
                 marks[sl] = 0u;  // for the next frame's chain marks
+            } else if (((z >> lane) & 1u) && zr < cap) {
+                freel[zr] = sl;
             }
             row += __popc(x);
-        }
-        for (uint32_t i = 0; i + 32u < TW; ++i) {
-            const uint32_t x = __shfl_sync(0xFFFFFFFFu, x1, i);
-            const bool set = (x >> lane) & 1u;
-            const uint32_t r = row + __popc(x & lt_mask);
-            if (set && r < cap) {
-                const uint32_t sl = (wt * TW + 32u + i) * 32u + lane;
-                live[r] = sl;
-                marks[sl] = 0u;
-            }
-            row += __popc(x);
+            zrow += __popc(z);
         }
     }
 }
@@ -1853,7 +1886,7 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
     phase_prep1(bt, tbits);
     sync();
     stamp(bt, 1);
-    phase_classify1(bt, s_c, s_tab, s_cnt, &s_n, reinterpret_cast<uint4*>(s_buf), s_tmp);
+    phase_classify1(bt, s_c, s_tab, s_cnt, reinterpret_cast<uint4*>(s_buf));
     sync();
     stamp(bt, 2);
     phase_walks1(bt, s_c, s_cnt, s_buf, s_warp, s_tmp, &s_n);

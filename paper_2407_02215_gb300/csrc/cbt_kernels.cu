@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kThreads) k_prep(BatchDev bt, int frame_start)
                     g->Mg = 0;
                     g->done = 0;
                     g->marks_clean = 0;  // this frame writes its changed list over the chain-mark words
+                    g->freel_full = 0;   // and a free list of its allocations only
                     tiles = (N + kTileItems - 1u) / kTileItems;
                     g->ntiles = tiles;
                     stl = (N + kScanItems - 1u) / kScanItems;

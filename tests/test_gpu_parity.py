@@ -155,3 +155,29 @@ def test_deepest_heap_ids(CBT):
     vg = g.vertices(eye, PREC_FP64, 20).cpu().numpy()
     vo = o.vertices(eye, PREC_FP64, 20)
     assert np.array_equal(vg.view(np.uint32), vo.view(np.uint32))
+
+
+@pytest.mark.parametrize("D", [5, 9, 12])
+def test_forms_alternating_frame_by_frame(D):
+    """One instance whose execution form changes between frames (one launch,
+    one launch per step, one launch again ...): each form takes over the
+    state the other left, including what the one-launch frame carries from
+    one frame to the next (the cleared chain marks and the free list of every
+    zero bit), and every frame matches the oracle."""
+    import paper_2407_02215_gb300 as P
+    P.build_library()
+    forms = [True, True, False, True, False, False, True, True, True, False]
+
+    def make(*args, **kw):
+        return P.CBT(*args, **kw)
+    frames = [forced_params(MODE_RANDOM, seed=40 + D) for _ in range(3 * len(forms))]
+    m = W.meshes.cube_mesh()
+    g, o = make(m, D, D - 1), Oracle(m, D, D - 1)
+    for k, fp in enumerate(frames):
+        g.set_fused(forms[k % len(forms)])
+        g.update(fp)
+        so = o.update(fp)
+        sg = g.stats()
+        assert sg["error"] == 0, f"frame {k}: device error {sg['error']:#x}"
+        assert sg["allocated"] == so["allocated"], f"frame {k}"
+        assert_same_state(g, o, f"frame {k} ({'fused' if forms[k % len(forms)] else 'per step'})")
