@@ -1395,7 +1395,7 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
     const Inst& I = bt.inst0;
     const FrameP& fp = bt.fp0;
     const uint32_t T = bt.bg->total_stiles, S = kFThreads * bt.bg->scan_ipt;
-    if (threadIdx.x == 0) s_tmp[0] = s_tmp[1] = 0;
+    if (threadIdx.x == 0) s_tmp[0] = s_tmp[1] = s_tmp[2] = 0;
     if (T > kMaxTiles1) {  // the host keeps pools within the tables
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(I.g, kErrOverflow);
         __syncthreads();
@@ -1422,9 +1422,10 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
         if (sc) atomicAdd(&s_tmp[1], sc);
         count_stat(s_cnt, 0, mc != 0u);
     };
-    // the queued walks, evenly over the block's threads
+    // the queued walks over the block's threads, each taking the next one
+    // when its last is done (chain lengths differ; s_tmp[2] counts them out)
     auto walk_queue = [&](uint32_t cnt) {
-        for (uint32_t k = threadIdx.x; k < cnt; k += kFThreads) {
+        for (uint32_t k = atomicAdd(&s_tmp[2], 1u); k < cnt; k = atomicAdd(&s_tmp[2], 1u)) {
             const uint32_t q = s_q[k];
             const uint4 e = wl[q];
             const uint32_t i = e.x & 0x7FFFFFFFu, s = e.y;
@@ -1491,7 +1492,7 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
         if (cnt > kQCap - 4u * kFThreads) {  // block-uniform
             walk_queue(cnt);
             __syncthreads();
-            if (threadIdx.x == 0) *s_n1 = 0;
+            if (threadIdx.x == 0) *s_n1 = s_tmp[2] = 0;
             __syncthreads();
         }
     }

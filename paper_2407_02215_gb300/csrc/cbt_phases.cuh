@@ -944,10 +944,76 @@ static __device__ uint32_t fill_split(const Inst& I, uint32_t s, uint32_t cmd, u
     return relinked;
 }
 
+// One old edge of a merged child on the new mesh, taken whole: the
+// neighbour y across it (its edge facing the child, command word and
+// destination), then the parent's new neighbour there and that neighbour's
+// edge facing the parent (across_load and across_resolve for one edge).
+struct Edge1 {
+    uint32_t y, ep;
+    uint2 yc;
+    uint32_t slot, rev;
+};
+
+__device__ __forceinline__ void edge_load(const Inst& I, const uint4& rx, int E, Edge1& a) {
+    a.y = link_of(rx, E);
+    a.ep = (rx.w >> (2 * E)) & 3u;
+    a.yc = make_uint2(0u, 0u);
+    if (a.y != kNull && !bad_slot(I, a.y, kErrLink))
+        a.yc = I.cd[a.y];
+    else
+        a.y = kNull;
+}
+
+template <typename DM>
+__device__ __forceinline__ void edge_resolve(const Inst& I, Edge1& a, const DM& dm) {
+    a.slot = kNull;
+    a.rev = 3u;
+    if (a.y == kNull) return;
+    const int Ep = (int)a.ep;
+    const uint32_t ysb = a.yc.x & kSplitMask;
+    if (Ep > 2) {
+        set_err(I.g, kErrLink);
+        return;
+    }
+    if (ysb) {
+        const uint32_t yd = dm(a.yc.y);
+        uint32_t leaf, edge;
+        if (!family_leaf(ysb, Ep, kWhole, leaf, edge) || yd + leaf >= dm.A) {
+            set_err(I.g, kErrLink);
+            return;
+        }
+        a.slot = I.freel[yd + leaf];
+        a.rev = edge;
+    } else if (a.yc.x & kMerged) {
+        const uint32_t yd = dm(a.yc.y);
+        if (Ep != kT || yd >= dm.A) {
+            set_err(I.g, kErrLink);
+            return;
+        }
+        a.slot = I.freel[yd];
+        a.rev = (a.yc.x & kHeapOdd) ? (uint32_t)kNe : (uint32_t)kPe;
+    } else {
+        a.slot = a.y;
+        a.rev = (uint32_t)Ep;
+    }
+}
+
+// push_keep for one edge E taken whole.
+__device__ __forceinline__ uint32_t push_keep1(const Inst& I, const Edge1& a, uint32_t E, uint32_t ns, uint32_t ne) {
+    if (a.y == kNull || (a.yc.x & (kSplitMask | kMerged))) return 0u;
+    uint32_t* yr = reinterpret_cast<uint32_t*>(I.nb + a.y);
+    yr[a.ep] = ns;
+    atomicXor(yr + 3, (E ^ ne) << (2u * a.ep));
+    return 1u;
+}
+
 // Parents of a valid merge group (Alg. 4), written by its smallest member:
 // Next = across child 2p+1's Twin edge, Prev = across child 2p's Twin edge,
 // Twin = the other parent (Table 1 read backwards, Alg. 6). Members m0, m1
-// are the children of the smaller parent, m2, m3 of the other one.
+// are the children of the smaller parent, m2, m3 of the other one. Both
+// parents' reads go out in three rounds (the members' records, the
+// neighbours across their Twin edges, those neighbours' new records) before
+// any write, so that a group costs three dependent loads, not six.
 template <typename DM = DestPlain>
 static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 m, const DM& dm) {
     const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
@@ -957,37 +1023,45 @@ static __device__ uint32_t fill_merge(const Inst& I, uint32_t dest, const uint4 
         return 0u;
     }
     uint32_t ps[2] = {kNull, kNull};
+    uint64_t ju[2] = {0ull, 0ull};
+    uint4 ru[2], rv[2];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {  // unrolled loops keep ms and ps in registers
+    for (int k = 0; k < 2; ++k) {  // unrolled loops keep everything in registers
         if (k == np) break;
         ps[k] = I.freel[dest + (uint32_t)k];
+        const uint32_t u = ms[2 * k], v = ms[2 * k + 1];
+        if (bad_slot(I, u, kErrLink) || bad_slot(I, v, kErrLink)) return 0u;
+        ju[k] = I.heap[u];
+        ru[k] = I.nb[u];
+        rv[k] = I.nb[v];
+    }
+    Edge1 xa[2], xb[2];  // across child 2p's and child 2p+1's Twin edges
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (k == np) break;
         if (bad_slot(I, ps[k], kErrOverflow)) return 0u;
+        const bool odd = (ju[k] & 1ull) != 0ull;  // u is child 2p+1
+        edge_load(I, odd ? rv[k] : ru[k], kT, xa[k]);
+        edge_load(I, odd ? ru[k] : rv[k], kT, xb[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (k == np) break;
+        edge_resolve(I, xb[k], dm);
+        edge_resolve(I, xa[k], dm);
     }
     uint32_t relinked = 0;
 #pragma unroll
-    for (int pk = 0; pk < 2; ++pk) {
-        if (pk == np) break;
-        const uint32_t u = ms[2 * pk], v = ms[2 * pk + 1];
-        if (bad_slot(I, u, kErrLink) || bad_slot(I, v, kErrLink)) return relinked;
-        const uint64_t ju = I.heap[u];
-        const uint32_t a = (ju & 1ull) ? v : u;   // child 2p
-        const uint32_t c1 = (ju & 1ull) ? u : v;  // child 2p+1
-        const bool modd = (*cmd_ptr(I, a) & kDepthOdd) != 0u;
-        Across xa, xb;
-        const uint4 ra = I.nb[a], rb = I.nb[c1];
-        across_load(I, rb, xb);
-        across_load(I, ra, xa);
-        across_resolve(I, xb, kT, false, modd, dm);
-        across_resolve(I, xa, kT, false, modd, dm);
-        relinked += push_keep(I, xb, kT, ps[pk], (uint32_t)kNe);
-        relinked += push_keep(I, xa, kT, ps[pk], (uint32_t)kPe);
-        const uint32_t tw = np == 2 ? ps[1 - pk] : kNull;
+    for (int k = 0; k < 2; ++k) {
+        if (k == np) break;
+        relinked += push_keep1(I, xb[k], (uint32_t)kT, ps[k], (uint32_t)kNe);
+        relinked += push_keep1(I, xa[k], (uint32_t)kT, ps[k], (uint32_t)kPe);
+        const uint32_t tw = np == 2 ? ps[1 - k] : kNull;
         const uint32_t rvT = np == 2 ? (uint32_t)kT : 3u;
-        I.nb[ps[pk]] = make_uint4(tw, xb.slot[kT][0], xa.slot[kT][0],
-                                  rvT | (xb.rev[kT][0] << 2) | (xa.rev[kT][0] << 4));
-        I.heap[ps[pk]] = ju >> 1;
-        *cmd_ptr(I, ps[pk]) = 0u;  // a new record: no cached vertices
-        dm.set(I, ps[pk]);
+        I.nb[ps[k]] = make_uint4(tw, xb[k].slot, xa[k].slot, rvT | (xb[k].rev << 2) | (xa[k].rev << 4));
+        I.heap[ps[k]] = ju[k] >> 1;
+        *cmd_ptr(I, ps[k]) = 0u;  // a new record: no cached vertices
+        dm.set(I, ps[k]);
     }
     return relinked;
 }
