@@ -318,6 +318,16 @@ int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_workspace, siz
 /* Number of live bisectors (CBT root). Synchronous. */
 int cbt_live_count(cbt_state* st, uint32_t* h_count, cbt_stream_t stream);
 
+/* The same count, enqueued on `stream` after the work already there: a
+ * 4-byte copy into `count`, which is DEVICE memory or page-locked HOST memory
+ * (4-byte aligned, caller-owned); nothing is synchronised, so the caller
+ * waits on the stream or an event recorded after it before reading. With it
+ * a frame's export can be copied to the host (its size known from the
+ * count) while the next frame computes. CBT_EINVAL for NULL or misaligned
+ * pointers, CBT_ECUDA when the copy cannot be enqueued. Section 3.1: the
+ * count is the CBT's root. */
+int cbt_live_count_async(cbt_state* st, uint32_t* count, cbt_stream_t stream);
+
 /* Copies the live bisectors, ascending slot order, into caller device
  * buffers: d_slots[N], d_heap[N], d_links[N][3] as (Twin, Next, Prev).
  * Any output may be NULL. cap = capacity of the outputs in bisectors;

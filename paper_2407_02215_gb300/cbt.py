@@ -49,6 +49,7 @@ def load(path: str | None = None):
     lib.cbt_frame_from_camera.argtypes = [P, C.c_float, C.c_int, P]
     lib.cbt_update_many.argtypes = [P, P, I32, P]
     lib.cbt_live_count.argtypes = [P, C.POINTER(U32), P]
+    lib.cbt_live_count_async.argtypes = [P, P, P]
     lib.cbt_leaves.argtypes = [P, P, P, P, U32, C.POINTER(U32), P]
     lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
     lib.cbt_host_device_pointer.argtypes = [P, C.POINTER(P)]
@@ -387,6 +388,15 @@ class CBT:
         if rc:
             raise CBTError(rc, "cbt_live_count")
         return int(n.value)
+
+    def live_count_async(self, out, stream=None):
+        """Enqueues the live count into out[0] (a 4-byte CUDA tensor, or a
+        pinned host tensor) on the stream, without synchronising."""
+        if out.element_size() != 4 or not (out.is_cuda or out.is_pinned()):
+            raise ValueError("out: a 4-byte CUDA or pinned host tensor")
+        rc = _lib.cbt_live_count_async(self._h, C.c_void_p(out.data_ptr()), _stream_ptr(stream))
+        if rc:
+            raise CBTError(rc, "cbt_live_count_async")
 
     def leaves(self, stream=None):
         n = self.live_count(stream)

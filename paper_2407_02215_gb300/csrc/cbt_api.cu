@@ -56,7 +56,7 @@ struct Layout {
 
 // A batch region for instances with the given pool sizes and halfedge counts.
 struct BatchLayout {
-    size_t inst, fps, bg, tile_base, ctile_base, stile_base, wtile_base, vtile_base, rel_base, status, total;
+    size_t inst, fps, bg, tile_base, ctile_base, stile_base, wtile_base, vtile_base, rel_base, status, tpre, total;
     uint32_t Titems, TwordsMax, Trel;
 };
 
@@ -83,6 +83,7 @@ BatchLayout batch_layout(uint32_t n, const uint32_t* cap, const uint32_t* W, con
     L.vtile_base = take(4u * (n + 1u));
     L.rel_base = take(4u * (n + 1u));
     L.status = take(8u * (2u * static_cast<size_t>(L.Titems) + L.TwordsMax));
+    L.tpre = take(4u * 2u * static_cast<size_t>(L.TwordsMax));
     L.total = off;
     return L;
 }
@@ -272,6 +273,7 @@ int batch_build(cbt_state* const* states, uint32_t n, char* region, cudaStream_t
     d.rel_base = reinterpret_cast<const uint32_t*>(region + B->L.rel_base);
     d.bg = reinterpret_cast<BatchGlobals*>(region + B->L.bg);
     d.status = reinterpret_cast<unsigned long long*>(region + B->L.status);
+    d.tpre = reinterpret_cast<uint32_t*>(region + B->L.tpre);
     std::vector<Inst> insts(n);
     for (uint32_t b = 0; b < n; ++b) insts[b] = states[b]->inst;
     std::memset(&d.inst0, 0, sizeof(Inst));
@@ -682,6 +684,12 @@ extern "C" int cbt_live_count(cbt_state* st, uint32_t* h_count, cbt_stream_t str
     if (cudaMemcpyAsync(h_count, st->inst.sums + 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return CBT_ECUDA;
     return cudaStreamSynchronize(s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
+}
+
+extern "C" int cbt_live_count_async(cbt_state* st, uint32_t* count, cbt_stream_t stream) {
+    if (!st || !count || (reinterpret_cast<uintptr_t>(count) & 3u)) return CBT_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return cudaMemcpyAsync(count, st->inst.sums + 1, 4, cudaMemcpyDefault, s) == cudaSuccess ? CBT_OK : CBT_ECUDA;
 }
 
 extern "C" int cbt_leaves(cbt_state* st, uint32_t* d_slots, uint64_t* d_heap, uint32_t* d_links,

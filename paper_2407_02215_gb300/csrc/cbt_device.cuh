@@ -192,6 +192,8 @@ struct BatchDev {
     uint32_t Titems, Twords, Trel;
     uint32_t* nout;              // optional [B]: live count at frame start per instance
     uint32_t timing;             // one-launch frame: record phase boundaries
+    uint32_t* tpre;              // single-instance frame: [2][Twords] ones before each word tile of
+                                 // the next frame's starting bitfield, by frame parity
 };
 
 constexpr int kThreads = 256;
@@ -291,6 +293,24 @@ __device__ __forceinline__ void load_dec6(uint32_t* s_tab) {
     const uint4* src = reinterpret_cast<const uint4*>(&g_dec8.p[0][0]);
     for (uint32_t k = threadIdx.x; k < kDecTabWords / 4u; k += blockDim.x)
         reinterpret_cast<uint4*>(s_tab)[k] = __ldg(src + k);
+}
+// The same copy in two halves (blocks of 256 threads): the loads into
+// registers, then the stores, so that other loads can go out in between.
+constexpr uint32_t kDecVecs = kDecTabWords / 4u;
+__device__ __forceinline__ void dec_fetch(uint4 (&r)[kDecVecs / 256u + 1u]) {
+    const uint4* src = reinterpret_cast<const uint4*>(&g_dec8.p[0][0]);
+#pragma unroll
+    for (uint32_t k = 0; k < kDecVecs / 256u + 1u; ++k) {
+        const uint32_t i = threadIdx.x + 256u * k;
+        r[k] = i < kDecVecs ? __ldg(src + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+__device__ __forceinline__ void dec_store(uint32_t* s_tab, const uint4 (&r)[kDecVecs / 256u + 1u]) {
+#pragma unroll
+    for (uint32_t k = 0; k < kDecVecs / 256u + 1u; ++k) {
+        const uint32_t i = threadIdx.x + 256u * k;
+        if (i < kDecVecs) reinterpret_cast<uint4*>(s_tab)[i] = r[k];
+    }
 }
 
 // One level on the first two columns, a[2 r + c] (c = 0, 1).

@@ -1403,10 +1403,28 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
     }
     uint32_t* s_wpre = s_buf;
     const unsigned long long* wc = wish_counts(bt);
-    block_table(T, [&](uint32_t t) { return Pair{(uint32_t)__ldcg(wc + t), 0u}; },
-                [&](uint32_t t, Pair ex) { s_wpre[t] = ex.a; }, s_warp);
     const uint32_t n = __ldcg(&I.g->nwalk), F = c.F;
     const uint4* wl = walk_list_of(I);
+    // a warp takes 32 consecutive entries per round (neighbouring entries
+    // walk neighbouring records, which its L1 then holds), warp-major over
+    // the grid so that every SM gets its share of a short list; a thread
+    // loads the entries of four rounds together, the first four before the
+    // table of split wishes below is built
+    const uint32_t stride = gridDim.x * kFThreads;
+    const uint32_t mine = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + (threadIdx.x & 31u);
+    uint32_t qq[4];
+    uint4 e[4];
+    auto fetch = [&](uint32_t c0) {
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t q = c0 + k * stride + mine;
+            qq[k] = q < n ? q : kNull;
+            e[k] = qq[k] != kNull ? wl[qq[k]] : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    fetch(0u);
+    block_table(T, [&](uint32_t t) { return Pair{(uint32_t)__ldcg(wc + t), 0u}; },
+                [&](uint32_t t, Pair ex) { s_wpre[t] = ex.a; }, s_warp);
     uint32_t* marks = chain_marks(I);
     uint32_t* s_q = s_buf + kMaxTiles1;  // list indices of the block's walks to do
     constexpr uint32_t kQCap = kFBuf - kMaxTiles1;
@@ -1453,21 +1471,8 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
     };
     if (threadIdx.x == 0) *s_n1 = 0;
     __syncthreads();
-    // a warp takes 32 consecutive entries per round (neighbouring entries
-    // walk neighbouring records, which its L1 then holds), warp-major over
-    // the grid so that every SM gets its share of a short list; a thread
-    // loads the entries of four rounds together
-    const uint32_t stride = gridDim.x * kFThreads;
-    const uint32_t mine = ((threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32u + (threadIdx.x & 31u);
     for (uint32_t c0 = 0; c0 + blockIdx.x * 32u < n; c0 += 4u * stride) {  // block-uniform
-        uint32_t qq[4];
-        uint4 e[4];
-#pragma unroll
-        for (uint32_t k = 0; k < 4; ++k) {
-            const uint32_t q = c0 + k * stride + mine;
-            qq[k] = q < n ? q : kNull;
-            e[k] = qq[k] != kNull ? wl[qq[k]] : make_uint4(0u, 0u, 0u, 0u);
-        }
+        if (c0) fetch(c0);
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
             if (qq[k] == kNull) continue;
@@ -1534,8 +1539,8 @@ __device__ __forceinline__ uint32_t fate_group_granted(const Inst& I, uint32_t i
 // request was granted, the chain marks are ORed into the command words (the
 // fill reads them there). Then the free list. Group validations run from a
 // list (dependent loads), their fates returned through shared memory.
-__device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint32_t tbits, uint32_t* s_cnt,
-                             Pair* s_warp, uint32_t* s_w, uint32_t* s_n, uint32_t* s_buf) {
+__device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, bool carried, uint32_t tbits,
+                             uint32_t* s_cnt, Pair* s_warp, uint32_t* s_w, uint32_t* s_n, uint32_t* s_buf) {
     const uint32_t T = bt.bg->total_stiles, ipt = bt.bg->scan_ipt;
     const uint32_t S = kFThreads * ipt;
     uint32_t* s_list = s_buf;          // local item indices to validate
@@ -1673,7 +1678,7 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, uint
     }
     // the last frame's final phase listed every zero bit of this frame's
     // starting bitfield, unless another form of the frame ran since
-    if (!__ldcg(&bt.inst0.g->freel_full)) free_list(bt, c, s_w, all_granted, tile_counts(bt));
+    if (!carried) free_list(bt, c, s_w, all_granted, tile_counts(bt));
 }
 
 // P5 (single instance): every block scans the tiles' (changed, allocation)
@@ -1743,7 +1748,7 @@ __device__ void phase_fill1(const BatchDev& bt, FCtx& c, bool all_granted, uint3
 // (the count checked against the scan) and writes the tile's rows of the new
 // live list. The vertices follow in their own phase, over the whole list.
 __device__ void phase_final1(const BatchDev& bt, FCtx& c, uint32_t* s_buf, Pair* s_warp, uint32_t* s_tmp,
-                             uint32_t tbits) {
+                             uint32_t tbits, bool carried) {
     ctx_tile(bt, bt.tile_base, 0, 1, c);
     const Inst& I = bt.inst0;
     const uint32_t W = I.W, TW = min(W, bt.tw), nt = I.cap >> tbits;
@@ -1757,20 +1762,29 @@ __device__ void phase_final1(const BatchDev& bt, FCtx& c, uint32_t* s_buf, Pair*
     // ones being the tile's share of the first A zero bits
     const unsigned long long* tc = tile_counts(bt);
     const uint32_t A = __ldcg(&I.g->A), TS = 1u << tbits;
-    // pass 1: ones before each tile at frame start (into s_tpre), pass 2:
-    // the new counts from them, scanned in place
-    block_table(nt, [&](uint32_t t) { return Pair{(uint32_t)(__ldcg(tc + t) >> 32), 0u}; },
-                [&](uint32_t t, Pair ex) { s_tpre[t] = ex.a; }, s_warp);
+    // the ones before each tile at frame start: kept by the last frame's
+    // final phase (`carried`: the last frame was this kernel) in the buffer of
+    // this frame's parity, else scanned here from the tile counts (into
+    // s_tpre); then the new counts from them, scanned in place, and kept for
+    // the next frame in the other buffer
+    const uint32_t par = bt.fp0.frame & 1u;
+    const uint32_t* tpre_in = bt.tpre + par * bt.Twords;
+    uint32_t* tpre_out = bt.tpre + (par ^ 1u) * bt.Twords;
+    if (!carried)
+        block_table(nt, [&](uint32_t t) { return Pair{(uint32_t)(__ldcg(tc + t) >> 32), 0u}; },
+                    [&](uint32_t t, Pair ex) { s_tpre[t] = ex.a; }, s_warp);
     const Pair tot = block_table(
         nt,
         [&](uint32_t t) {
             const unsigned long long w = __ldcg(tc + t);
             const uint32_t old = (uint32_t)(w >> 32), clr = (uint32_t)w;
-            const long long zb = (long long)t * TS - s_tpre[t];  // zero bits before the tile at frame start
+            const uint32_t before = carried ? __ldcg(tpre_in + t) : s_tpre[t];
+            const long long zb = (long long)t * TS - before;  // zero bits before the tile at frame start
             const long long set = min(max((long long)A - zb, 0ll), (long long)(TS - old));
             return Pair{old - clr + (uint32_t)set, 0u};
         },
         [&](uint32_t t, Pair ex) { s_tpre[t] = ex.a; }, s_warp);
+    for (uint32_t t = blockIdx.x + threadIdx.x * gridDim.x; t < nt; t += kFThreads * gridDim.x) tpre_out[t] = s_tpre[t];
     if (threadIdx.x == 0) s_tmp[0] = 0;
     __syncthreads();
     const uint32_t Nn = tot.a;
@@ -1882,9 +1896,16 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
         grid_sync(bt.bg, epoch, nbar);
     };
     stamp(bt, 0);
-    load_dec6(s_tab);
+    // read before any block can reach the final phase, which sets it
+    const bool carried = __ldcg(&bt.inst0.g->freel_full) != 0u;
+    // the decode tables are fetched now and stored after prep's own loads
+    // have gone out
+    static_assert(kFThreads == 256, "dec_fetch splits the table over 256 threads");
+    uint4 tab[kDecVecs / 256u + 1u];
+    dec_fetch(tab);
     if (threadIdx.x == 0) s_c.b = kNull;
     phase_prep1(bt, tbits);
+    dec_store(s_tab, tab);
     sync();
     stamp(bt, 1);
     phase_classify1(bt, s_c, s_tab, s_cnt, reinterpret_cast<uint4*>(s_buf));
@@ -1900,13 +1921,13 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
         sync();
     }
     stamp(bt, 4);
-    phase_alloc1(bt, s_c, all_granted, tbits, s_cnt, s_warp, s_w, &s_n, s_buf);
+    phase_alloc1(bt, s_c, all_granted, carried, tbits, s_cnt, s_warp, s_w, &s_n, s_buf);
     sync();
     stamp(bt, 5);
     phase_fill1(bt, s_c, all_granted, s_cnt, s_buf, s_warp);
     sync();
     stamp(bt, 6);
-    phase_final1(bt, s_c, s_buf, s_warp, s_tmp, tbits);
+    phase_final1(bt, s_c, s_buf, s_warp, s_tmp, tbits, carried);
     if (bt.fp0.vout) {
         sync();
         stamp(bt, 7);

@@ -61,3 +61,35 @@ def test_vertices_to_host(P):
         g.vertices_to_host(dv, small, hn)
     assert int(hn[0]) == g.live_count()
     assert np.array_equal(dv[:16].cpu().numpy().view(np.uint32), small.numpy().view(np.uint32))
+
+
+def test_live_count_async_into_pinned_and_device_memory(P):
+    """cbt_live_count_async enqueues the count behind the frame on the same
+    stream: after a stream synchronisation the pinned word and the device
+    word hold the count cbt_live_count returns, frame after frame; and the
+    rows a second stream then copies out equal the device export."""
+    import torch
+    spec = W.configs.config2(n_frames=12, nx=30)
+    g = P.CBT(spec.mesh, 17, spec.max_depth)
+    s, side = torch.cuda.Stream(), torch.cuda.Stream()
+    dv = torch.empty((1 << 17, 3, 3), dtype=torch.float32, device="cuda")
+    hv = torch.empty((1 << 17, 3, 3), dtype=torch.float32, pin_memory=True)
+    hn = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+    dn = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for fp in spec.frames:
+        with torch.cuda.stream(s):
+            g.update(fp, stream=s, vertices_out=dv)
+            g.live_count_async(hn, stream=s)
+            g.live_count_async(dn, stream=s)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        ev.synchronize()
+        n = int(hn[0])
+        with torch.cuda.stream(side):
+            side.wait_event(ev)
+            hv[:n].copy_(dv[:n], non_blocking=True)
+        side.synchronize()
+        assert n == g.live_count() == int(dn.cpu()[0])
+        assert np.array_equal(dv[:n].cpu().numpy().view(np.uint32), hv[:n].numpy().view(np.uint32))
+    with pytest.raises(ValueError):
+        g.live_count_async(torch.zeros(1, dtype=torch.int32))  # neither CUDA nor pinned
