@@ -1075,7 +1075,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="grid line without the batched and served objects")
     ap.add_argument("--serve-rate", type=float, default=10000.0)
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.instances is None:
         args.instances = 1024 if args.workload == "serve" else 256
