@@ -458,6 +458,9 @@ __device__ uint32_t crossing_mg(const BatchDev& bt, const FCtx& c, uint32_t F, u
 // granted while their running total fits F, splits while Mg plus theirs
 // does (R6 reading); granted splits mark their chains (command form of
 // Alg. 3).
+// kOne: the single-instance frame, whose descriptor is in the launch
+// parameters (a copy in shared memory is reloaded after every store).
+template <bool kOne = false>
 __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_t* s_red, Pair* s_warp,
                            uint32_t* s_tmp, uint32_t* s_n, uint2* s_list, bool always_recorded = false) {
     const uint32_t T = bt.bg->total_stiles, ipt = bt.bg->scan_ipt;
@@ -465,7 +468,7 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         if (threadIdx.x == 0) *s_n = 0;
         stats_reset(s_cnt);
         ctx_tile(bt, bt.stile_base, t, T, c);
-        const Inst& I = c.I;
+        const Inst& I = kOne ? bt.inst0 : c.I;
         const uint32_t N = c.N, F = c.F;
         const uint32_t i0 = stile_first(c, ipt);
         uint32_t sl[kMaxIpt], w[kMaxIpt];
@@ -1917,7 +1920,7 @@ __global__ void __launch_bounds__(kFThreads, CBT_FRAME_MIN_BLOCKS) k_frame1(Batc
     const Globals* g = bt.inst0.g;
     const bool all_granted = __ldcg(&g->rq_merge) + __ldcg(&g->rq_split) <= (unsigned long long)s_c.F;
     if (!all_granted) {
-        phase_gate(bt, s_c, s_cnt, s_red, s_warp, s_tmp, &s_n, reinterpret_cast<uint2*>(s_buf), true);
+        phase_gate<true>(bt, s_c, s_cnt, s_red, s_warp, s_tmp, &s_n, reinterpret_cast<uint2*>(s_buf), true);
         sync();
     }
     stamp(bt, 4);
