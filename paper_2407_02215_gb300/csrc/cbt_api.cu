@@ -49,7 +49,7 @@ uint32_t item_tiles(uint32_t cap) { return (cap + kTileItems - 1u) / kTileItems;
 
 // Per-instance arrays.
 struct Layout {
-    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, root64, rel, corner, batch,
+    size_t globals, heap, nb, cd, bits, sums, live, freel, scan, grp, chg, chgr, vc, root64, rel, corner, rbnd, batch,
         total;
     uint32_t cap, W, ch;
 };
@@ -117,6 +117,7 @@ bool make_layout(int32_t H, int32_t D, Layout& L) {
     L.root64 = take(72u * h);
     L.rel = take(72u * h);
     L.corner = take(12u * h);
+    L.rbnd = take(4u * ((h + 31u) / 32u));
     const uint32_t Hh = static_cast<uint32_t>(H);
     const BatchLayout B = batch_layout(1, &L.cap, &L.W, &Hh);
     L.batch = take(B.total);
@@ -618,7 +619,9 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     std::vector<int32_t> ints(3u * h);
     std::vector<double> hpos(3u * h);
     std::vector<uint32_t> corner(3u * h);
+    std::vector<uint32_t> rbnd((h + 31u) / 32u, 0u);
     for (size_t k = 0; k < h; ++k) {
+        if (twin[k] < 0) rbnd[k >> 5] |= 1u << (k & 31u);
         ints[k] = twin[k];
         ints[h + k] = next[k];
         ints[2u * h + k] = prev[k];
@@ -635,6 +638,8 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
     cudaMemcpyAsync(d_ints, ints.data(), 12u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d_hpos, hpos.data(), 24u * h, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(st->corner, corner.data(), 12u * h, cudaMemcpyHostToDevice, s);
+    I.rbnd = reinterpret_cast<const uint32_t*>(b + L.rbnd);
+    cudaMemcpyAsync(const_cast<uint32_t*>(I.rbnd), rbnd.data(), 4u * rbnd.size(), cudaMemcpyHostToDevice, s);
     const int grid = static_cast<int>(std::min<uint32_t>((std::max(L.W, static_cast<uint32_t>(H)) + 255u) / 256u,
                                                          static_cast<uint32_t>(st->sms) * 4u));
     launch_init(I, d_ints, d_ints + h, d_ints + 2u * h, d_hpos, std::max(1, grid), s);

@@ -129,6 +129,7 @@ struct Inst {
     uint32_t cap, W, D, H, ch, max_depth;
     uint32_t ntiles_items;  // ceil(cap / kTileItems)
     uint32_t pad_;
+    const uint32_t* rbnd;   // bit h: halfedge h has no Twin (mesh boundary), [ceil(H / 32)]
 };
 
 struct FrameP {

@@ -1098,12 +1098,13 @@ __global__ void __launch_bounds__(kFThreads) k_wait_selftest(BatchGlobals* bg, i
 //                words of the live slots and the tile counters cleared
 //   P1 classify  wishes (Sec. 3.3 GenerateCommands), balanced over the grid;
 //                the items that need a walk appended to the frame's walk
-//                list; split wishes counted per scan tile
+//                list; per scan tile the split wishes' lower-bound costs
 //   P2 walks     the walk list spread evenly over the grid. A split wish's
 //                chain (command form of Alg. 3) is walked, recorded and
 //                marked (into the chain-mark words) unless the split wishes
-//                before its scan tile already cost more than the free slots
-//                at 2 each, so that the gate denies it whatever its cost. A
+//                before its scan tile and itself already cost more than the
+//                free slots at their lower bounds, so that the gate denies
+//                it whatever its cost. A
 //                merge wish with an even heap ID walks its Alg. 4 group while
 //                it can be a merge candidate with this wish its smallest
 //                member, which then records it with its merge cost. Per scan
@@ -1174,7 +1175,8 @@ struct DestTiles {
 __device__ __forceinline__ unsigned long long* tile_counts(const BatchDev& bt) {
     return bt.status + 2u * bt.Titems;
 }
-// Per scan tile: the split wishes (P1), then the allocation sums (P4).
+// Per scan tile: the split wishes' lower-bound costs (P1), then the
+// allocation sums (P4).
 __device__ __forceinline__ unsigned long long* wish_counts(const BatchDev& bt) { return bt.status + bt.Titems; }
 // The chain marks of P2 (one word per slot; the per-step frame's list of
 // changed items uses the same array).
@@ -1183,6 +1185,11 @@ __device__ __forceinline__ uint32_t* chain_marks(const Inst& I) { return I.chg; 
 // per entry {live index | split flag << 31, slot, heap ID low, high}.
 __device__ __forceinline__ uint4* walk_list_of(const Inst& I) { return I.chgr; }
 constexpr uint32_t kWalkCap1 = kFBuf / 4;  // uint4 entries of the block's list
+// The x word of a walk entry: the live index, bit 31 for a split wish, bit
+// 30 for a split wish under a root whose halfedge has a Twin, so that it has
+// one too (its chain then costs at least 4: itself and the Twin's pair,
+// Alg. 3); else the chain can cost 2.
+constexpr uint32_t kWalkSplit = 0x80000000u, kWalkInterior = 0x40000000u, kWalkIndex = 0x3FFFFFFFu;
 
 // Alg. 4 group of s1 (heap ID j1, a merge wish) on the frame-start state,
 // walked only while s1 can be its smallest member and every member wishes
@@ -1340,22 +1347,29 @@ __device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, ui
     for (; i - lane < N; i += stride) {  // warp-uniform
         const uint32_t sc = i + 2u * stride < N ? I.live[i + 2u * stride] : 0u;
         const uint64_t jb = i + stride < N ? I.heap[sb] : 0ull;
-        bool split = false, walk = false;
+        bool split = false, walk = false, interior = false;
         if (i < N) {
             const uint32_t cmd = classify_item(I, fp, key, i, sa, ja, s_tab, s_cnt, cache);
             split = (cmd & kSplitWish) != 0u;
             walk = split || ((cmd & kMergeWish) && !(cmd & kHeapOdd));
+            // every bisector under a root whose halfedge has a Twin has one
+            // (its refinement edge is inside the root triangle, on an edge
+            // to the face's centroid, or on that halfedge)
+            const int d = depth_of(ja, I.ch);
+            const uint32_t h = d >= 0 ? (uint32_t)((ja >> d) - (1ull << I.ch)) : kNull;
+            interior = split && h < I.H && !((__ldg(I.rbnd + (h >> 5)) >> (h & 31u)) & 1u);
         }
         const unsigned wm = __ballot_sync(0xFFFFFFFFu, walk);
         if (walk)
             s_wl[nwl + __popc(wm & ((1u << lane) - 1u))] =
-                make_uint4(i | (split ? 0x80000000u : 0u), sa, (uint32_t)ja, (uint32_t)(ja >> 32));
+                make_uint4(i | (split ? kWalkSplit : 0u) | (interior ? kWalkInterior : 0u), sa, (uint32_t)ja,
+                           (uint32_t)(ja >> 32));
         nwl += __popc(wm);
-        {  // split wishes per scan tile
+        {  // the split wishes' lower-bound costs per scan tile
             const uint32_t t = i / S;
             const unsigned m = __match_any_sync(0xFFFFFFFFu, i < N ? t : kNull);
-            const uint32_t n = __popc(__ballot_sync(0xFFFFFFFFu, split) & m);
-            if (n && lane == (uint32_t)(__ffs(m) - 1)) atomicAdd(&wc[t], (unsigned long long)n);
+            const uint32_t lb = __reduce_add_sync(m, split ? (interior ? 4u : 2u) : 0u);
+            if (lb && lane == (uint32_t)(__ffs(m) - 1)) atomicAdd(&wc[t], (unsigned long long)lb);
         }
         sa = sb;
         ja = jb;
@@ -1374,16 +1388,17 @@ __device__ void phase_classify1(const BatchDev& bt, FCtx& c, uint32_t* s_tab, ui
 }
 
 // P2 (single instance): the frame's walk list over the whole grid. s_wpre
-// (shared) gets the split wishes before each scan tile. A block first takes
+// (shared) gets the split wishes' lower-bound costs before each scan tile
+// (4 with a Twin, else 2). A block first takes
 // its share of the entries and settles the splits past the bound below; the
 // walks left are queued and spread evenly over the block's threads. Per
 // entry:
-//   - a split wish: unless 2 (wishes before its scan tile + 1) > F, its
+//   - a split wish: unless those costs plus its own bound exceed F, its
 //     chain is walked on the frame-start links, checked, its first members
 //     recorded in grp[i] and marked in the chain-mark words; its scan word
 //     the chain's allocation count (or 3d + 4 under the paper's gate, set by
-//     classify); past that bound the gate denies it whatever its cost (every
-//     cost is at least 2), and 2 stands in;
+//     classify); past that bound the gate denies it whatever its cost, and
+//     its bound stands in;
 //   - a merge wish with an even heap ID: its Alg. 4 group, walked while the
 //     wish can be its smallest member and every member wishes to merge (a
 //     merge candidate); then it records the members and kGrpMin, and the
@@ -1449,10 +1464,10 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
         for (uint32_t k = atomicAdd(&s_tmp[2], 1u); k < cnt; k = atomicAdd(&s_tmp[2], 1u)) {
             const uint32_t q = s_q[k];
             const uint4 e = wl[q];
-            const uint32_t i = e.x & 0x7FFFFFFFu, s = e.y;
+            const uint32_t i = e.x & kWalkIndex, s = e.y;
             const uint64_t j = (uint64_t)e.z | ((uint64_t)e.w << 32);
             uint32_t mc = 0, sc = 0;
-            if (e.x & 0x80000000u) {
+            if (e.x & kWalkSplit) {
                 const int d = depth_of(j, I.ch);
                 uint4 rec;
                 bool more;
@@ -1479,15 +1494,20 @@ __device__ void phase_walks1(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint3
 #pragma unroll
         for (uint32_t k = 0; k < 4; ++k) {
             if (qq[k] == kNull) continue;
-            const uint32_t i = e[k].x & 0x7FFFFFFFu;
+            const uint32_t i = e[k].x & kWalkIndex;
             const uint32_t t = i / S;
-            // a split is denied whatever its cost when the wishes before its
-            // scan tile cost more than F at 2 each
-            const bool skip = (e[k].x & 0x80000000u) &&
-                              2ull * ((unsigned long long)s_wpre[min(t, T - 1u)] + 1ull) > (unsigned long long)F;
+            // a split is denied whatever its cost when the lower bounds of
+            // the split wishes before its scan tile and of its own exceed F
+            const bool skip =
+                (e[k].x & kWalkSplit) && (unsigned long long)s_wpre[min(t, T - 1u)] +
+                                                 ((e[k].x & kWalkInterior) ? 4ull : 2ull) > (unsigned long long)F;
             if (skip) {
+                // its bound stands in for its cost: every split after it in
+                // the gate's order is then denied on these costs as on the
+                // true ones, and the requested total still exceeds F
                 const uint64_t j = (uint64_t)e[k].z | ((uint64_t)e[k].w << 32);
-                const uint32_t sc = fp.gate == 1 ? 3u * (uint32_t)depth_of(j, I.ch) + 4u : 2u;
+                const uint32_t sc = fp.gate == 1 ? 3u * (uint32_t)depth_of(j, I.ch) + 4u
+                                                 : ((e[k].x & kWalkInterior) ? 4u : 2u);
                 if (fp.gate != 1) I.scan[i] = sc;
                 account(t, 0u, sc);
             } else {

@@ -313,3 +313,37 @@ def test_list_frames_with_chains_and_quads():
                            gate=GATE_PAPER if k % 5 == 4 else GATE_CHAIN)
         check_frame(o, fp, frame)
         frame += 1
+
+
+def test_split_cost_lower_bounds():
+    """The bounds the single-instance frame skips chain walks with: a split
+    wish under a root whose halfedge has a Twin has a Twin itself (its
+    refinement edge lies inside the root triangle, on an edge to the face's
+    centroid, or on that halfedge) and costs at least 4 under the chain gate
+    (its own pair, plus the Twin's pair when they form a diamond, else at
+    least 3 for a coarser Twin and more down the chain); under a boundary
+    halfedge it can cost 2. On the pinned runs every split wish keeps to
+    these bounds (the restated chain, which the frames above match against
+    the oracle), the Twin exists wherever the root's does, and both kinds of
+    root occur."""
+    seen = {2: 0, 4: 0}
+    for name, make in MESHES:
+        mesh = make()
+        o = Oracle(mesh, D=7, max_depth=9)
+        root_twin = o.halfedges["twin"]
+        for frame, fp in enumerate(_frames(7 * 31 + mesh.H)):
+            st = Start(o)
+            split, _ = wishes(st, fp, frame)
+            for s in st.live:
+                if not split[s]:
+                    continue
+                h = (st.heap[s] >> st.depth(s)) - (1 << st.ch)
+                members, diamond = chain(st, s)
+                cost = 2 + 3 * (len(members) - int(diamond)) + 2 * int(diamond)
+                bound = 4 if root_twin[h] >= 0 else 2
+                if bound == 4:
+                    assert st.twin[s] != NULL, (name, frame, s)
+                assert cost >= bound, (name, frame, s, cost)
+                seen[bound] += 1
+            o.update(fp)
+    assert seen[2] > 0 and seen[4] > 0
