@@ -1568,6 +1568,7 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, bool
     const uint32_t S = kFThreads * ipt;
     uint32_t* s_list = s_buf;          // local item indices to validate
     uint32_t* s_fate = s_buf + kFBuf / 2;  // their fates, by local item index
+    __shared__ uint32_t s_first;
     if (T > kMaxTiles1 || S > kFBuf / 2) {  // the host keeps pools within the tables
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(bt.inst0.g, kErrOverflow);
         return;
@@ -1617,6 +1618,7 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, bool
                 sl[k] = k < ipt ? s_sl[e0 + k] : kNull;
                 cm[k] = k < ipt ? s_cm[e0 + k] : 0u;
             }
+            if (threadIdx.x == 0) s_first = s_sl[0];  // the tile's first slot
             __syncthreads();  // s_buf is the lists' below
         }
         // groups to validate: when every request is granted, every recorded
@@ -1654,9 +1656,11 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, bool
         // histogram over the word tiles from the one holding the tile's first
         // slot (slots ascend with the live index); others go straight out
         uint32_t* s_hist = s_buf + kFBuf / 2;
-        const uint32_t hbase = (I.cap + I.live[c.lt * S]) >> tbits, nt = I.cap >> tbits;
+        uint32_t* s_ml = s_buf;  // the tile's merges: local index << 13 | allocation offset
+        const uint32_t hbase = (I.cap + s_first) >> tbits, nt = I.cap >> tbits;
         unsigned long long* tc = tile_counts(bt);
         s_hist[threadIdx.x] = 0u;
+        if (threadIdx.x == 0) *s_n = 0;
         __syncthreads();
         auto cleared = [&](uint32_t slot) {
             const uint32_t node = (I.cap + slot) >> tbits;
@@ -1672,26 +1676,33 @@ __device__ void phase_alloc1(const BatchDev& bt, FCtx& c, bool all_granted, bool
             if (!na) continue;
             const uint32_t dw = (t << kLocBits) | arun;
             I.chgr[t * S + crun] = make_uint4(i0 + k, sl[k], cm[k], dw);
-            // alloc_apply, with the clears counted
+            // alloc_apply, with the clears counted; a merge is listed and
+            // applied below, one per thread
             if (!(f[k] & 8u)) {
                 *dest_ptr(I, sl[k]) = dw;
                 count_stat(s_cnt, 0, true);
                 cleared(sl[k]);
             } else {
-                const uint4 m = I.grp[i0 + k];
-                const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (ms[q] == kNull || bad_slot(I, ms[q], kErrLink)) continue;
-                    atomicOr(cmd_ptr(I, ms[q]), kMerged);
-                    *dest_ptr(I, ms[q]) = dw + (q < 2 ? 0u : 1u);
-                    cleared(ms[q]);
-                }
-                atomicAdd(&s_cnt[2], m.z == kNull ? 2u : 4u);
-                count_stat(s_cnt, 1, true);
+                s_ml[atomicAdd(s_n, 1u)] = ((e0 + k) << kLocBits) | arun;
             }
             ++crun;
             arun += na;
+        }
+        __syncthreads();
+        const uint32_t nm = *s_n;
+        for (uint32_t q = threadIdx.x; q < nm; q += kFThreads) {
+            const uint32_t e = s_ml[q] >> kLocBits, dw = (t << kLocBits) | (s_ml[q] & kLocMask);
+            const uint4 m = I.grp[ts + e];
+            const uint32_t ms[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (ms[r] == kNull || bad_slot(I, ms[r], kErrLink)) continue;
+                atomicOr(cmd_ptr(I, ms[r]), kMerged);
+                *dest_ptr(I, ms[r]) = dw + (r < 2 ? 0u : 1u);
+                cleared(ms[r]);
+            }
+            atomicAdd(&s_cnt[2], m.z == kNull ? 2u : 4u);
+            count_stat(s_cnt, 1, true);
         }
         __syncthreads();
         if (s_hist[threadIdx.x] && hbase + threadIdx.x - nt < nt)
