@@ -181,3 +181,30 @@ def test_forms_alternating_frame_by_frame(D):
         assert sg["error"] == 0, f"frame {k}: device error {sg['error']:#x}"
         assert sg["allocated"] == so["allocated"], f"frame {k}"
         assert_same_state(g, o, f"frame {k} ({'fused' if forms[k % len(forms)] else 'per step'})")
+
+
+def test_single_instance_above_the_one_launch_tables():
+    """A single instance whose pool (2^23 slots) exceeds the single-instance
+    frame's tables runs the batch frame (its phase names say so), and every
+    frame equals the oracle: forced splits to depth 9, random requests, then
+    merges."""
+    import paper_2407_02215_gb300 as P
+    P.build_library()
+    m = W.meshes.cube_mesh()
+    D, md = 23, 12
+    g, o = P.CBT(m, D, md), Oracle(m, D, md)
+    g.set_fused(True)
+    g.set_timing(True)
+    frames = [forced_params(MODE_FORCE_SPLIT) for _ in range(9)]
+    frames += [forced_params(MODE_RANDOM, seed=23) for _ in range(6)]
+    frames += [forced_params(MODE_FORCE_MERGE) for _ in range(3)]
+    for k, fp in enumerate(frames):
+        g.update(fp)
+        so = o.update(fp)
+        sg = g.stats()
+        assert sg["error"] == 0, f"frame {k}: device error {sg['error']:#x}"
+        for key in ("live_after", "split_granted", "merge_granted", "allocated"):
+            assert sg[key] == so[key], f"frame {k}: {key} gpu {sg[key]} oracle {so[key]}"
+        if k % 3 == 2 or k == len(frames) - 1:
+            assert_same_state(g, o, f"frame {k}")
+    assert "gate_sum" in g.kernel_times()  # a phase of the batch frame
