@@ -491,6 +491,7 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
         Pair tot;
         const Pair tex = block_scan(loc, tot, s_warp);
         Pair run = padd(before, tex);
+        uint32_t gmask = 0, nmg = 0;  // the thread's granted splits (by k), granted merges
 #pragma unroll
         for (uint32_t k = 0; k < kMaxIpt; ++k) {
             const uint32_t mc = (w[k] >> 24) & kMergeCostMask, sc = w[k] & 0xFFFFFFu;
@@ -498,16 +499,25 @@ __device__ void phase_gate(const BatchDev& bt, FCtx& c, uint32_t* s_cnt, uint32_
             if (sl[k] == kNull) continue;
             const bool mgrant = mc > 0u && run.a <= F;
             if (mc) atomicOr(cmd_ptr(I, sl[k]), mgrant ? (kCand | kMergeGrant) : kCand);
-            count_stat(s_cnt, 0, mgrant);
-            // a split wish, and only a split wish, has a nonzero split cost;
-            // bit 31 of the list's live index: its chain continues past the
-            // recorded members
-            const bool sgrant = sc > 0u && (uint64_t)Mg + (uint64_t)run.b <= F;
-            if (sgrant) s_list[atomicAdd(s_n, 1u)] = make_uint2((i0 + k) | (w[k] & kScanMore), sl[k]);
-            count_stat(s_cnt, 1, sgrant);
+            nmg += mgrant ? 1u : 0u;
+            // a split wish, and only a split wish, has a nonzero split cost
+            if (sc > 0u && (uint64_t)Mg + (uint64_t)run.b <= F) gmask |= 1u << k;
+        }
+        // the granted splits listed in thread order (bit 31 of the list's
+        // live index: its chain continues past the recorded members), the
+        // counts added once per warp
+        Pair ntot;
+        const Pair gex = block_scan(Pair{(uint32_t)__popc(gmask), nmg}, ntot, s_warp);
+        uint32_t q = gex.a;
+#pragma unroll
+        for (uint32_t k = 0; k < kMaxIpt; ++k)
+            if ((gmask >> k) & 1u) s_list[q++] = make_uint2((i0 + k) | (w[k] & kScanMore), sl[k]);
+        if (threadIdx.x == 0) {
+            s_cnt[0] += ntot.b;
+            s_cnt[1] += ntot.a;
         }
         __syncthreads();
-        const uint32_t n = *s_n;
+        const uint32_t n = ntot.a;
         // the paper's gate charges 3d + 4 without a walk (the single-instance
         // frame walks, and records, every chain that can be granted); the
         // records of four grants are loaded before their marks go out
