@@ -1102,38 +1102,47 @@ __global__ void __launch_bounds__(kFThreads) k_wait_selftest(BatchGlobals* bg, i
 // ===================================================== one instance, fewer phases
 //
 // k_frame1: the frame of a single instance (a batch of one), with the same
-// results as k_frame in six phases, or five when the frame's requests all
-// fit the free slots:
-//   P0 prep      frame counters; the camera-relative roots; the chain-mark
-//                words of the live slots and the tile counters cleared
-//   P1 classify  wishes (Sec. 3.3 GenerateCommands), balanced over the grid;
-//                the items that need a walk appended to the frame's walk
-//                list; per scan tile the split wishes' lower-bound costs
+// results as k_frame in seven phases, or six when the frame's requests all
+// fit the free slots or nothing is exported:
+//   P0 prep      frame counters; the camera-relative roots; the word-tile
+//                counts copied; the chain-mark words of the live slots and
+//                the tile counters cleared (the marks only when the last
+//                frame was not this kernel, which leaves them clear)
+//   P1 classify  wishes (Sec. 3.3 GenerateCommands), in 32-item chunks dealt
+//                warp-major over the grid; the items that need a walk
+//                appended to the frame's walk list; per scan tile the split
+//                wishes' lower-bound costs
 //   P2 walks     the walk list spread evenly over the grid. A split wish's
 //                chain (command form of Alg. 3) is walked, recorded and
 //                marked (into the chain-mark words) unless the split wishes
 //                before its scan tile and itself already cost more than the
 //                free slots at their lower bounds, so that the gate denies
-//                it whatever its cost. A
-//                merge wish with an even heap ID walks its Alg. 4 group while
-//                it can be a merge candidate with this wish its smallest
-//                member, which then records it with its merge cost. Per scan
-//                tile the (merge, split) cost sums, per frame their totals.
+//                it whatever its cost. A merge wish with an even heap ID
+//                walks its Alg. 4 group while it can be a merge candidate
+//                with this wish its smallest member, which then records it
+//                with its merge cost. Per scan tile the (merge, split) cost
+//                sums, per frame their totals.
 //   P3 gate      (when the totals exceed the free slots F) grants in the
 //                order of the R6 reading and chain marking into the command
 //                words; otherwise every request is granted and the chain-mark
 //                words hold the marks
 //   P4 alloc     fates, their tile-local allocation prefix (a destination
 //                word holds the tile and the offset within it), the fill
-//                records per tile, the bits cleared per word tile, the free
-//                list
+//                records per tile, the bits cleared per word tile; the free
+//                list only when the last frame was not this kernel
 //   P5 fill      the tiles' record and allocation offsets in shared memory;
 //                new records, links and bits
 //   P6 final     every word tile's new count (frame-start count, clears, and
 //                its share of the first A zero bits), hence the sum tree;
-//                the new live list read off the bitfield by warps over equal
-//                row ranges, with the vertex export (FP32, fixed point, FP64)
-//   P7 vertices  sphere and displaced forms: the export from the cache of P1
+//                per 16-word part of a word tile (one warp), its rows of the
+//                new live list and, from its zero bits, of the next frame's
+//                free list (every zero bit in slot order)
+//   P7 vertices  the export of the new list (FP32, fixed point, FP64
+//                evaluated; sphere and displaced forms copied from the cache
+//                of P1), 32 rows per warp, warp-major
+// The instance descriptor and the frame parameters are read from the launch
+// parameters (a copy in shared memory would be reloaded after every store
+// through a generic pointer).
 
 constexpr uint32_t kLocBits = 13, kLocMask = (1u << kLocBits) - 1u;  // offset of a new record within its tile
 constexpr uint32_t kMaxTiles1 = kFBuf / 2;  // scan tiles and word tiles the shared tables hold
