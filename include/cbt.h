@@ -283,6 +283,15 @@ int cbt_host_device_pointer(void* h_ptr, void** d_ptr);
 int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, float* h_vertices, uint32_t cap,
                          uint32_t* h_count, cbt_stream_t stream);
 
+/* Rows [0, rows) of a frame's vertex export (float[rows][3][3] at
+ * d_vertices, DEVICE memory) copied into h_vertices (page-locked HOST
+ * memory, at least rows rows) by the copy engine on `stream`, nothing
+ * synchronised: rows is the live count, e.g. from cbt_live_count_async once
+ * the caller has waited for it. With two export buffers a frame's rows go
+ * out while the next frame computes. CBT_EINVAL for NULL pointers, CBT_ECUDA
+ * when the copy cannot be enqueued; rows = 0 enqueues nothing. */
+int cbt_vertices_to_host_async(const float* d_vertices, float* h_vertices, uint32_t rows, cbt_stream_t stream);
+
 /* Indexed export of the live bisectors, the input of a visibility buffer
  * (the paper exports its triangulation into one, Sec. 4). Corners that are
  * the same point of the subdivided surface share one vertex: a corner's

@@ -7,4 +7,4 @@ library has not been built.
 """
 from .build import build as build_library  # noqa: F401
 from .cbt import (CBT, CBT_NULL, Batch, CBTError, Server, halfedges_from_faces, load,  # noqa: F401
-                  sum_reduce, compact, update_many, workspace_bytes)
+                  sum_reduce, compact, update_many, vertices_to_host_async, workspace_bytes)

@@ -50,6 +50,7 @@ def load(path: str | None = None):
     lib.cbt_update_many.argtypes = [P, P, I32, P]
     lib.cbt_live_count.argtypes = [P, C.POINTER(U32), P]
     lib.cbt_live_count_async.argtypes = [P, P, P]
+    lib.cbt_vertices_to_host_async.argtypes = [P, P, U32, P]
     lib.cbt_leaves.argtypes = [P, P, P, P, U32, C.POINTER(U32), P]
     lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
     lib.cbt_host_device_pointer.argtypes = [P, C.POINTER(P)]
@@ -503,6 +504,20 @@ def update_many_packed(handles, arr, n: int, stream=None):
     rc = load().cbt_update_many(handles, arr, n, _stream_ptr(stream))
     if rc:
         raise CBTError(rc, "cbt_update_many")
+
+
+def vertices_to_host_async(d_vertices, h_vertices, rows: int, stream=None):
+    """cbt_vertices_to_host_async: the first `rows` rows of a vertex export
+    (CUDA tensor) into a pinned host tensor by the copy engine, on the
+    stream, without synchronising."""
+    if not d_vertices.is_cuda or not h_vertices.is_pinned():
+        raise ValueError("d_vertices: a CUDA tensor; h_vertices: a pinned host tensor")
+    if rows > min(d_vertices.shape[0], h_vertices.shape[0]):
+        raise ValueError("rows beyond the buffers")
+    rc = load().cbt_vertices_to_host_async(C.c_void_p(d_vertices.data_ptr()), C.c_void_p(h_vertices.data_ptr()),
+                                           int(rows), _stream_ptr(stream))
+    if rc:
+        raise CBTError(rc, "cbt_vertices_to_host_async")
 
 
 def update_many(instances, fps, stream=None, vertices_out=None):

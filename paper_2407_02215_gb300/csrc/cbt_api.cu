@@ -767,6 +767,16 @@ extern "C" int cbt_vertices_to_host(cbt_state* st, const float* d_vertices, floa
     return *h_count > cap ? CBT_ENOMEM : CBT_OK;
 }
 
+extern "C" int cbt_vertices_to_host_async(const float* d_vertices, float* h_vertices, uint32_t rows,
+                                          cbt_stream_t stream) {
+    if (!d_vertices || !h_vertices) return CBT_EINVAL;
+    if (rows == 0u) return CBT_OK;
+    return cudaMemcpyAsync(h_vertices, d_vertices, 36ull * rows, cudaMemcpyDeviceToHost,
+                           reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? CBT_OK
+               : CBT_ECUDA;
+}
+
 extern "C" size_t cbt_index_workspace_bytes(uint32_t max_live) { return index_workspace_bytes(max_live); }
 
 extern "C" int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_workspace, size_t bytes,

@@ -67,7 +67,8 @@ def test_live_count_async_into_pinned_and_device_memory(P):
     """cbt_live_count_async enqueues the count behind the frame on the same
     stream: after a stream synchronisation the pinned word and the device
     word hold the count cbt_live_count returns, frame after frame; and the
-    rows a second stream then copies out equal the device export."""
+    rows cbt_vertices_to_host_async then copies out on a second stream equal
+    the device export."""
     import torch
     spec = W.configs.config2(n_frames=12, nx=30)
     g = P.CBT(spec.mesh, 17, spec.max_depth)
@@ -85,9 +86,9 @@ def test_live_count_async_into_pinned_and_device_memory(P):
             ev.record(s)
         ev.synchronize()
         n = int(hn[0])
-        with torch.cuda.stream(side):
-            side.wait_event(ev)
-            hv[:n].copy_(dv[:n], non_blocking=True)
+        side.wait_event(ev)
+        hv.fill_(float("nan"))
+        P.vertices_to_host_async(dv, hv, n, stream=side)  # cbt_vertices_to_host_async
         side.synchronize()
         assert n == g.live_count() == int(dn.cpu()[0])
         assert np.array_equal(dv[:n].cpu().numpy().view(np.uint32), hv[:n].numpy().view(np.uint32))
