@@ -298,13 +298,18 @@ int cbt_vertices_to_host_async(const float* d_vertices, float* h_vertices, uint3
  * identity is its exact weight row (Eq. 1) in lowest terms over the global
  * mesh vertices and face centroids of its root, so shared corners match
  * across bisectors, roots and faces and the indexed mesh is watertight.
+ * Corners at a mesh vertex or face centroid are matched by that global
+ * point; the others lie inside a root edge or triangle, where the conforming
+ * bisection (Sec. 2.3) puts the bisectors sharing the point in one fan,
+ * walked through the neighbour links.
  * Vertices are numbered in order of first occurrence over (live index,
  * corner); triangle i is live bisector i (ascending slot, as cbt_leaves).
  *   d_tri_vertices: DEVICE float[N][3][3], the per-bisector vertices of the
  *           current live list (cbt_update's vertices_out or cbt_vertices);
  *           may be NULL when d_vertices is NULL;
- *   d_workspace: DEVICE scratch of cbt_index_workspace_bytes(triangles_cap)
- *           bytes at least, caller-owned, 256-byte aligned;
+ *   d_workspace: DEVICE scratch of cbt_index_workspace_bytes(st,
+ *           triangles_cap) bytes at least (4 bytes per pool slot, per global
+ *           point and, twice, per corner), caller-owned, 256-byte aligned;
  *   d_vertices: DEVICE float[vertices_cap][3] or NULL: each vertex's
  *           position, copied from its first occurrence;
  *   d_indices: DEVICE u32[triangles_cap][3];
@@ -317,9 +322,12 @@ int cbt_vertices_to_host_async(const float* d_vertices, float* h_vertices, uint3
  * d_tri_vertices; a workspace not 256-byte aligned or an output not aligned
  * to its element), CBT_ENOMEM (N > triangles_cap, workspace too small, or
  * more vertices than vertices_cap: the counts are still returned),
- * CBT_EDEVICE (two identities with one 64-bit hash: reported, never merged),
- * CBT_ECUDA. Five launches on `stream`; synchronous (returns the counts). */
-size_t cbt_index_workspace_bytes(uint32_t max_live);
+ * CBT_EDEVICE (a live bisector whose heap ID names no root of the mesh, or
+ * neighbour links that do not close a fan: a link without its way back, a
+ * fan that does not return to its start or passes 64 bisectors), CBT_ECUDA.
+ * Five launches on `stream`; synchronous (returns the counts).
+ * cbt_index_workspace_bytes returns 0 for a NULL state. */
+size_t cbt_index_workspace_bytes(const cbt_state* st, uint32_t max_live);
 int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_workspace, size_t bytes, float* d_vertices,
               uint32_t vertices_cap, uint32_t* d_indices, uint32_t triangles_cap, uint64_t* d_heap,
               uint32_t* h_nvertices, uint32_t* h_ntriangles, cbt_stream_t stream);

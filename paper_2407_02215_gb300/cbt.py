@@ -55,7 +55,7 @@ def load(path: str | None = None):
     lib.cbt_vertices.argtypes = [P, P, P, U32, I32, U32, C.POINTER(U32), P]
     lib.cbt_host_device_pointer.argtypes = [P, C.POINTER(P)]
     lib.cbt_vertices_to_host.argtypes = [P, P, P, U32, P, P]
-    lib.cbt_index_workspace_bytes.argtypes = [U32]
+    lib.cbt_index_workspace_bytes.argtypes = [C.c_void_p, U32]
     lib.cbt_index_workspace_bytes.restype = C.c_size_t
     lib.cbt_index.argtypes = [P, P, P, C.c_size_t, P, U32, P, U32, P, C.POINTER(U32), C.POINTER(U32), P]
     lib.cbt_cbt.argtypes = [P, P, P, P]
@@ -436,7 +436,8 @@ class CBT:
 
     def index_workspace(self, max_live: int):
         """Device scratch for index() with up to max_live live bisectors."""
-        return torch.empty(int(_lib.cbt_index_workspace_bytes(int(max_live))), dtype=torch.uint8, device=self.device)
+        return torch.empty(int(_lib.cbt_index_workspace_bytes(self._h, int(max_live))), dtype=torch.uint8,
+                           device=self.device)
 
     def index(self, tri_vertices=None, workspace=None, out=None, stream=None):
         """Indexed export (cbt_index): (vertices [nv, 3] or None, indices

@@ -205,6 +205,8 @@ struct cbt_batch {
 struct cbt_state {
     Inst inst;
     uint32_t* corner;  // [H][3] global points of the root corners: vert[h], vert[next h], V + face[h]
+    uint32_t npts;     // global points: 1 + the largest in corner
+    uint32_t* h_ix = nullptr;  // pinned counts of the last cbt_index (made by its first call)
     void* workspace;
     size_t bytes;
     int sms;
@@ -631,6 +633,7 @@ extern "C" int cbt_create(int32_t H, const int32_t* twin, const int32_t* next, c
         corner[3u * k + 2u] = static_cast<uint32_t>(V) + static_cast<uint32_t>(face[k]);
     }
     st->corner = reinterpret_cast<uint32_t*>(b + L.corner);
+    st->npts = h ? 1u + *std::max_element(corner.begin(), corner.end()) : 0u;
     int32_t* d_ints = reinterpret_cast<int32_t*>(b + L.rel);
     double* d_hpos = reinterpret_cast<double*>(b + L.rel + align256(12u * h));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -777,19 +780,25 @@ extern "C" int cbt_vertices_to_host_async(const float* d_vertices, float* h_vert
                : CBT_ECUDA;
 }
 
-extern "C" size_t cbt_index_workspace_bytes(uint32_t max_live) { return index_workspace_bytes(max_live); }
+extern "C" size_t cbt_index_workspace_bytes(const cbt_state* st, uint32_t max_live) {
+    return st ? index_workspace_bytes(max_live, st->inst.cap, st->npts) : 0u;
+}
 
 extern "C" int cbt_index(cbt_state* st, const float* d_tri_vertices, void* d_workspace, size_t bytes,
                          float* d_vertices, uint32_t vertices_cap, uint32_t* d_indices, uint32_t triangles_cap,
                          uint64_t* d_heap, uint32_t* h_nvertices, uint32_t* h_ntriangles, cbt_stream_t stream) {
     if (!st || !d_workspace || !d_indices || (d_vertices && !d_tri_vertices)) return CBT_EINVAL;
-    // the workspace holds 64-bit words and 32-byte identities; the outputs their element types
+    // the workspace is carved in 256-byte aligned arrays; the outputs are aligned to their element types
     if ((reinterpret_cast<uintptr_t>(d_workspace) & 255u) || (reinterpret_cast<uintptr_t>(d_indices) & 3u) ||
         (reinterpret_cast<uintptr_t>(d_heap) & 7u) || (reinterpret_cast<uintptr_t>(d_vertices) & 3u) ||
         (reinterpret_cast<uintptr_t>(d_tri_vertices) & 3u))
         return CBT_EINVAL;
-    return launch_index(st->inst, st->corner, triangles_cap, d_workspace, bytes, d_tri_vertices, d_vertices,
-                        vertices_cap, d_indices, d_heap, st->sms, reinterpret_cast<cudaStream_t>(stream),
+    if (!st->h_ix && cudaMallocHost(reinterpret_cast<void**>(&st->h_ix), 16u) != cudaSuccess) {
+        st->h_ix = nullptr;
+        return CBT_ECUDA;
+    }
+    return launch_index(st->inst, st->corner, st->npts, triangles_cap, d_workspace, bytes, d_tri_vertices, d_vertices,
+                        vertices_cap, d_indices, d_heap, st->sms, reinterpret_cast<cudaStream_t>(stream), st->h_ix,
                         h_nvertices, h_ntriangles);
 }
 
@@ -831,6 +840,7 @@ extern "C" int cbt_stats(cbt_state* st, cbt_frame_stats* out, cbt_stream_t strea
 
 extern "C" void cbt_destroy(cbt_state* st) {
     if (!st) return;
+    if (st->h_ix) cudaFreeHost(st->h_ix);
     batch_free(st->self);
     delete st;
 }

@@ -23,10 +23,10 @@ void launch_vertices(const BatchDev& bt, int grid, cudaStream_t s);
 int launch_rows_to_host(const uint32_t* count, const float* src, float* dst, uint32_t cap, uint32_t* h_count,
                         int sms, cudaStream_t s);
 // Indexed export (cbt_index.cu).
-size_t index_workspace_bytes(uint32_t max_live);
-int launch_index(const Inst& I, const uint32_t* corner, uint32_t cap, void* workspace, size_t bytes,
+size_t index_workspace_bytes(uint32_t max_live, uint32_t pool, uint32_t npts);
+int launch_index(const Inst& I, const uint32_t* corner, uint32_t npts, uint32_t cap, void* workspace, size_t bytes,
                  const float* tri, float* verts, uint32_t vcap, uint32_t* idx, uint64_t* ids, int sms,
-                 cudaStream_t s, uint32_t* h_nvert, uint32_t* h_ntri);
+                 cudaStream_t s, uint32_t* h_cnt, uint32_t* h_nvert, uint32_t* h_ntri);
 // The one-launch frame (cbt_fused.cu): blocks of it resident per SM, and its
 // cooperative launch over `grid` blocks.
 int frame_blocks_per_sm();
