@@ -50,7 +50,8 @@ def test_grid_flythrough_indexed(P, terrain):
 def test_planet_indexed_deep(P):
     """Sphere form on the dodecahedron planet under a camera that descends
     looking straight down with a 2 degree view, so that refinement goes
-    deeper than 31 levels (64-bit weights in the identities)."""
+    deeper than 31 levels (64-bit weights in the oracle's identities, path
+    bits past 32 in the root-corner test)."""
     from workloads.cameras import PREC_SPHERE, frame_params, sphere_descent_path
     R = 6.371e6
     mesh = W.meshes.dodecahedron_mesh(R)

@@ -148,6 +148,78 @@ def test_decode_deep_exact():
     assert (Wm.astype(object).sum(axis=1) == 1 << 60).all()
 
 
+def test_root_corners_follow_the_path_bits():
+    """Brute force over every path to depth 10: a corner's row has a single
+    nonzero weight (the corner is a root corner) exactly when Eq. 1 carried
+    it down unchanged: corner 0 when the bits below the first are all 0,
+    corner 1 when they are all 1 (the first bit picking root corner 0 / 2,
+    or 1 / 2), corner 2 only at depth 0."""
+    ch = 2
+    for d in range(0, 11):
+        for path in range(1 << d):
+            j = (4 << d) + path
+            Wm = decode_weights(j, ch).astype(np.int64)
+            for v in range(3):
+                nz = np.flatnonzero(Wm[v])
+                if d == 0:
+                    want = v
+                elif v == 2:
+                    want = None
+                else:
+                    low = path & ((1 << (d - 1)) - 1)
+                    first = (path >> (d - 1)) & 1
+                    if v == 0:
+                        want = (2 if first else 0) if low == 0 else None
+                    else:
+                        want = (1 if first else 2) if low == (1 << (d - 1)) - 1 else None
+                if want is None:
+                    assert nz.size >= 2, (d, path, v)
+                else:
+                    assert nz.tolist() == [want], (d, path, v)
+
+
+def test_split_turns_the_vertex_order_over():
+    """Each split halves the area and reverses the vertex order: the weight
+    matrix of a depth-d bisector has determinant (-1)^d 4^d."""
+    rng = np.random.default_rng(3)
+    ch = 2
+    for d in list(range(0, 8)) + [int(x) for x in rng.integers(8, 21, 30)]:
+        path = int(rng.integers(0, 1 << d)) if d else 0
+        m = [[int(x) for x in row] for row in decode_weights((4 << d) + path, ch)]
+        det = (m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+               + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]))
+        assert det == (-1) ** d * 4 ** d, (d, path, det)
+
+
+@pytest.mark.parametrize("mesh_name", ["cube", "grid"])
+def test_edge_kinds_give_the_depth_parity(mesh_name):
+    """In the conforming bisection a refinement edge (Twin) at depth d is
+    shared with a refinement edge at depth d or a Next / Prev edge at depth
+    d - 1: across every link of a randomly refined state the two depths
+    differ by at most one, and their parities agree exactly when both edges
+    are refinement edges or both are not."""
+    m = W.meshes.cube_mesh() if mesh_name == "cube" else W.meshes.grid_mesh(5, 4, tri_frac=0.3, seed=8)
+    o = Oracle(m, 14, 13)
+    _random_refine(o, 6, 11)
+    slots, heap, links = o.leaves()
+    row = {int(s): i for i, s in enumerate(slots)}
+    depth = [int(j).bit_length() - 1 - o.ch for j in heap]
+    seen = 0
+    for i, s in enumerate(slots):
+        for x in range(3):
+            u = int(links[i, x])
+            if u == 0xFFFFFFFF:
+                continue
+            k = row[u]
+            back = [e for e in range(3) if int(links[k, e]) == int(s)]
+            assert len(back) == 1
+            e = back[0]
+            assert abs(depth[i] - depth[k]) <= 1
+            assert ((depth[i] - depth[k]) % 2 == 0) == ((x == 0) == (e == 0))
+            seen += 1
+    assert seen > 250
+
+
 # ------------------------------------------------------- hash and LOD
 
 def test_splitmix64_published_vector():
