@@ -1,8 +1,9 @@
 """Indexed export (cbt_index, R15 reading): the vertex buffer, index buffer
 and triangle heap IDs equal the oracle's indexed form of the same state,
 bit for bit (plain grid, displaced terrain, sphere-form planet with depths
-beyond 31, closed cube); at full size the index buffer obeys the Euler
-characteristic of the surface and numbers vertices by first occurrence."""
+beyond 31, closed cube, two triangles sharing only a vertex); at full size
+the index buffer obeys the Euler characteristic of the surface and numbers
+vertices by first occurrence."""
 import numpy as np
 import pytest
 
@@ -77,6 +78,22 @@ def test_closed_cube_indexed(P):
     fp.eye = np.array([2.0, 1.0, 0.5])
     v, idx = _index_pair(g, o, fp, 16)
     assert idx.shape[0] == 24 * 2 ** 10 and v.shape[0] == 2 + 12 * 2 ** 10
+
+
+def test_pinched_vertex_indexed(P):
+    """Two triangles meeting only at a vertex (no shared edge): the corners
+    at that vertex are matched by their global point although no neighbour
+    link joins the two sides; the indexed form equals the oracle's after
+    random refinement of both sides."""
+    from workloads.cameras import MODE_RANDOM
+    m = W.meshes._mesh("bowtie", [[0, 1, 2], [0, 3, 4]],
+                       [(0, 0, 0), (1, 0, 0), (1, 1, 0), (-1, 0, 0), (-1, -1, 0)])
+    frames = [forced_params(MODE_RANDOM, seed=90 + k) for k in range(8)]
+    g, o = run_pair(m, 12, 10, frames[:-1], P.CBT, Oracle, check_every=7)
+    fp = frames[-1]
+    fp.eye = np.array([0.3, -0.2, 1.0])
+    v, idx = _index_pair(g, o, fp, 12)
+    assert v.shape[0] == idx.max() + 1
 
 
 def test_full_size_grid_index_properties(P):

@@ -599,6 +599,29 @@ def test_indexed_export_euler_open_and_geometry():
     assert np.unique(q, axis=0).shape[0] == V
 
 
+def test_indexed_export_pinched_vertex():
+    """Two triangles that meet only at a vertex (a bowtie: no edge shared):
+    the shared mesh vertex stays one index however far either side is
+    refined, so V - E + F stays 1 (E = (3F + B) / 2, every root edge a
+    border), and that index's corners lie on both triangles' sides."""
+    m = W.meshes._mesh("bowtie", [[0, 1, 2], [0, 3, 4]],
+                       [(0, 0, 0), (1, 0, 0), (1, 1, 0), (-1, 0, 0), (-1, -1, 0)])
+    o = Oracle(m, 12, 10)
+    for k in range(4):
+        _random_refine(o, 2, 90 + 3 * k)
+        _, idx, _ = o.export_indexed()
+        F = idx.shape[0]
+        B = int((o.leaves()[2] == 0xFFFFFFFF).sum())
+        V = int(idx.max()) + 1
+        assert V - (3 * F + B) // 2 + F == 1
+    pos = o.vertices_f64().reshape(-1, 3)
+    flat = idx.reshape(-1)
+    at0 = np.flatnonzero(np.abs(pos).max(axis=1) == 0.0)
+    assert at0.size >= 2 and np.unique(flat[at0]).size == 1
+    side = np.sign(o.vertices_f64().sum(axis=1)[at0 // 3, 0])
+    assert (side > 0).any() and (side < 0).any()
+
+
 @pytest.mark.parametrize("form", ["plain", "sphere"])
 def test_zero_amplitude_displacement_is_the_plain_update(form):
     """R14 reduces to the undisplaced update when the amplitude is zero (the
