@@ -34,6 +34,8 @@ def test_workspace_bytes_and_errors():
     assert P.workspace_bytes(2, 16) == 0       # H < 3
     assert P.workspace_bytes(24, 4) == 0       # 2^D < H
     assert P.workspace_bytes(24, 31) == 0      # D > 30
+    # the indexed export's scratch needs a state (its pool and global points)
+    assert P.load().cbt_index_workspace_bytes(None, 100) == 0
 
 
 def test_host_ingest_matches_paper_table():
