@@ -308,6 +308,36 @@ def test_uniform_refinement_closed_form():
         o.update(forced_params(MODE_FORCE_MERGE))
         assert o.live_count == 24 * 2**d
     assert _leafset(o) == [32 + h for h in range(24)]
+    # the merged roots are linked as the halfedges were (slots may differ)
+    slots, heap, links = o.leaves()
+    root_of = {int(s): int(j) - 32 for s, j in zip(slots, heap)}
+    he = o.halfedges
+    for s, j, ln in zip(slots, heap, links):
+        h = int(j) - 32
+        assert [root_of[int(x)] for x in ln] == [int(he["twin"][h]), int(he["next"][h]), int(he["prev"][h])]
+
+
+@pytest.mark.parametrize("mesh_name", ["fig1", "grid"])
+def test_split_then_merge_restores_the_root_links(mesh_name):
+    """Open meshes (border halfedges have no Twin): uniform refinement to
+    depth 6 and forced merging back leave the H roots linked exactly as the
+    halfedge operators, border links null."""
+    m = W.meshes.fig1_mesh() if mesh_name == "fig1" else W.meshes.grid_mesh(3, 2, tri_frac=0.3, seed=1)
+    o = Oracle(m, D=14, max_depth=8)
+    H, base = m.H, 1 << o.ch
+    for _ in range(6):
+        o.update(forced_params(MODE_FORCE_SPLIT))
+    assert o.live_count == H * 64
+    for _ in range(6):
+        o.update(forced_params(MODE_FORCE_MERGE))
+    slots, heap, links = o.leaves()
+    assert sorted(int(j) for j in heap) == [base + h for h in range(H)]
+    root_of = {int(s): int(j) - base for s, j in zip(slots, heap)}
+    root_of[0xFFFFFFFF] = -1
+    he = o.halfedges
+    for j, ln in zip(heap, links):
+        h = int(j) - base
+        assert [root_of[int(x)] for x in ln] == [int(he["twin"][h]), int(he["next"][h]), int(he["prev"][h])]
 
 
 def test_max_allocation_bound():
